@@ -1,0 +1,360 @@
+"""Pins of the CPU oracle to things other than itself (CPU only).
+
+Each check is chosen so that a plausible slip in the oracle (a dropped term,
+a wrong sign, a transposed gradient, a missing density factor, a wrong
+element size h) fails at least one of them:
+  * closed forms of single tetrahedra, evaluated with 50-digit decimals;
+  * per-term invariants that follow from sum_a grad N_a = 0 and from linearity;
+  * textbook special cases: the consistent P1 mass matrix for the Galerkin
+    convection, barycentric gradients from an independent linear solve;
+  * global identities: divergence theorem on the cube, discrete
+    divergence of a constant pressure, rotation/translation/renumbering
+    invariance;
+  * derivatives: complex step against central differences, the element
+    Jacobian VJP against the full complex-step Jacobian and the dot-product
+    identity.
+"""
+import decimal
+from decimal import Decimal as D
+
+import numpy as np
+import pytest
+
+import meshgen as mg
+import oracle
+
+decimal.getcontext().prec = 50
+SQ5 = D(5).sqrt()
+QA = (D(5) + 3 * SQ5) / 20
+QB = (D(5) - SQ5) / 20
+REF_DN = [(-1, -1, -1), (1, 0, 0), (0, 1, 0), (0, 0, 1)]
+
+
+def ref_tet(s=1.0):
+    return np.array([[0, 0, 0], [s, 0, 0], [0, s, 0], [0, 0, s]], float)
+
+
+def closed_form_shear(rho, mu, s, q, c1=4, c2=2):
+    """Tet X0=0, Xk=s e_k; u = (y, 1, 0), p = q x, no eddy viscosity.
+    grad u has the single entry du/dy = 1, so (u.grad)u = (1, 0, 0) and the
+    strong residual is (rho + q, 0, 0); h = s, V = s^3/6, grad N_a = e/s,
+    u at Gauss point g: (y_g, 1, 0) with y_g = s*A if g == 2 else s*B,
+    p_bar = q s / 4."""
+    rho, mu, s, q = D(rho), D(mu), D(s), D(q)
+    V = s ** 3 / 6
+    h = s
+    pbar = q * s / 4
+    taus, ys = [], []
+    for g in range(4):
+        y = s * (QA if g == 2 else QB)
+        ys.append(y)
+        taus.append(1 / (c1 * mu / h ** 2 + c2 * rho * (y * y + 1).sqrt() / h))
+    F = [[D(0)] * 4 for _ in range(4)]
+    for a in range(4):
+        dN = [D(c) / s for c in REF_DN[a]]
+        supg = sum(taus[g] * rho * (ys[g] * dN[0] + dN[1]) * (rho + q) for g in range(4))
+        F[a][0] = -V * rho / 4 - V * mu * dN[1] + V * pbar * dN[0] - V / 4 * supg
+        F[a][1] = V * pbar * dN[1]
+        F[a][2] = V * pbar * dN[2]
+        F[a][3] = -V / 4 * sum(taus) * dN[0] * (rho + q)
+    return np.array([[float(x) for x in row] for row in F])
+
+
+def shear_inputs(s, q):
+    X = ref_tet(s)
+    U = np.zeros((4, 4))
+    U[:, 0] = X[:, 1]          # u = y
+    U[:, 1] = 1.0              # v = 1
+    U[:, 3] = q * X[:, 0]      # p = q x
+    return X, U
+
+
+@pytest.mark.parametrize("rho,mu,s,q", [(1.0, 1e-2, 1.0, 0.0), (2.5, 0.3, 0.37, -1.7),
+                                        (0.8, 1e-4, 3.0, 0.5), (1.0, 1e-2, 1e-2, 2.0)])
+def test_closed_form_shear_tet(rho, mu, s, q):
+    X, U = shear_inputs(s, q)
+    F = oracle.element(X, U, rho, mu)
+    ref = closed_form_shear(rho, mu, s, q)
+    scale = np.abs(ref).max()
+    assert np.abs(F - ref).max() <= 1e-14 * scale
+
+
+@pytest.mark.parametrize("mu,s", [(1e-2, 1.0), (0.7, 0.25)])
+def test_closed_form_pressure_only(mu, s):
+    """u = 0, p = 1 at node 1: F_a,i = V p_bar dN_a/dx_i with p_bar = 1/4,
+    tau = h^2/(c1 mu), F_a,4 = -(V/4) * 4 tau dN_a/dx."""
+    X = ref_tet(s)
+    U = np.zeros((4, 4))
+    U[1, 3] = 1.0
+    F = oracle.element(X, U, 1.0, mu)
+    sd = D(s)
+    V, tau = sd ** 3 / 6, sd ** 2 / (4 * D(mu))
+    for a in range(4):
+        dN = [D(c) / sd for c in REF_DN[a]]
+        for i in range(3):
+            assert abs(D(F[a, i]) - V / 4 * dN[i]) <= D("1e-15") * V / sd
+        exp4 = -V * tau * dN[0] / sd          # grad p = (1/s, 0, 0)
+        assert abs(D(F[a, 3]) - exp4) <= D("1e-14") * V * tau / sd ** 2
+
+
+def test_closed_form_viscous_linear_velocity():
+    """rho = 0, u_x = y: only the viscous term survives:
+    F_0,x = +mu/6, F_2,x = -mu/6 on the unit reference tet."""
+    mu = 1e-2
+    X = ref_tet()
+    U = np.zeros((4, 4))
+    U[:, 0] = X[:, 1]
+    F = oracle.element(X, U, 0.0, mu)
+    exp = np.zeros((4, 4))
+    exp[0, 0], exp[2, 0] = mu / 6, -mu / 6
+    assert np.abs(F - exp).max() < 1e-17
+
+
+@pytest.mark.parametrize("s,cv,rho", [(1.0, 0.07, 1.0), (0.2, 0.1, 2.0)])
+def test_closed_form_vreman(s, cv, rho):
+    """u = (y, x, 0): alpha has entries alpha_12 = alpha_21 = 1, so
+    beta = h^2 diag(1, 1, 0), B = h^4, A = 2 and nu_t = c h^2 / sqrt(2)."""
+    mu = 1e-3
+    X = ref_tet(s)
+    U = np.zeros((4, 4))
+    U[:, 0] = X[:, 1]
+    U[:, 1] = X[:, 0]
+    F = oracle.element(X, U, rho, mu, c_vreman=cv, terms=oracle.T_VISC)
+    mu_eff = mu + rho * cv * s * s / np.sqrt(2.0)
+    V = s ** 3 / 6
+    dN = np.array(REF_DN, float) / s
+    exp = np.zeros((4, 4))
+    exp[:, 0] = -V * mu_eff * dN[:, 1]
+    exp[:, 1] = -V * mu_eff * dN[:, 0]
+    assert np.abs(F - exp).max() <= 1e-14 * np.abs(exp).max()
+    # pure shear has no Vreman viscosity (B = 0)
+    U2 = np.zeros((4, 4))
+    U2[:, 0] = X[:, 1]
+    F2 = oracle.element(X, U2, rho, mu, c_vreman=cv, terms=oracle.T_VISC)
+    assert np.abs(F2[:, 0] + V * mu * dN[:, 1]).max() <= 1e-15 * V * mu / s
+
+
+def random_tet(rng):
+    while True:
+        X = rng.normal(size=(4, 3))
+        e = X[1:] - X[0]
+        if np.linalg.det(e.T) > 0.2:
+            return X
+
+
+def bary_grad(X):
+    """Gradients of barycentric coordinates by an independent linear solve:
+    [1 x y z] c = delta -> grad N_a = c[1:, a]."""
+    A = np.hstack([np.ones((4, 1)), X])
+    C = np.linalg.solve(A, np.eye(4))
+    return C[1:].T  # [a][j]
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_term_invariants_random_tets(seed):
+    rng = np.random.default_rng(100 + seed)
+    X = random_tet(rng)
+    U = rng.normal(size=(4, 4))
+    rho, mu = 1.3, 0.05
+    dN = bary_grad(X)
+    V = abs(np.linalg.det((X[1:] - X[0]).T)) / 6
+    G = U[:, :3].T @ dN           # G[i][j] = du_i/dx_j
+    div = np.trace(G)
+    Fs = {t: oracle.element(X, U, rho, mu, c_vreman=0.0, terms=t)
+          for t in (oracle.T_CONV, oracle.T_VISC, oracle.T_PRES, oracle.T_SUPG, oracle.T_CONT,
+                    oracle.T_PSPG)}
+    tol = 1e-13 * (1 + np.abs(U).max()) ** 2
+    # sum_a grad N_a = 0: these terms sum to zero over the element's nodes
+    for t in (oracle.T_VISC, oracle.T_PRES, oracle.T_SUPG, oracle.T_PSPG):
+        assert np.abs(Fs[t].sum(axis=0)).max() < tol
+    # Galerkin continuity sums to -V div u
+    assert abs(Fs[oracle.T_CONT][:, 3].sum() + V * div) < tol
+    # term supports: momentum terms leave column 4 alone and vice versa
+    for t in (oracle.T_CONV, oracle.T_VISC, oracle.T_PRES, oracle.T_SUPG):
+        assert np.all(Fs[t][:, 3] == 0)
+    for t in (oracle.T_CONT, oracle.T_PSPG):
+        assert np.all(Fs[t][:, :3] == 0)
+    # textbook forms from the independent gradients
+    M = V * (np.ones((4, 4)) + np.eye(4)) / 20.0          # P1 consistent mass matrix
+    conv = -rho * M @ (U[:, :3] @ G.T)                    # -rho sum_b M_ab (G u_b)
+    assert np.abs(Fs[oracle.T_CONV][:, :3] - conv).max() < tol
+    visc = -V * mu * dN @ G.T                             # -V mu G grad N_a
+    assert np.abs(Fs[oracle.T_VISC][:, :3] - visc).max() < tol
+    pres = V * U[:, 3].mean() * dN                        # V p_bar grad N_a
+    assert np.abs(Fs[oracle.T_PRES][:, :3] - pres).max() < tol
+    assert np.abs(Fs[oracle.T_CONT][:, 3] + V * div / 4).max() < tol
+    # the full RHS is the sum of its terms
+    full = oracle.element(X, U, rho, mu)
+    assert np.abs(full - sum(Fs.values())).max() < tol
+
+
+def test_element_even_permutation_and_rigid_motion():
+    rng = np.random.default_rng(7)
+    X = random_tet(rng)
+    U = rng.normal(size=(4, 4))
+    for cv in (0.0, 0.07):
+        F = oracle.element(X, U, 1.0, 1e-2, c_vreman=cv)
+        for perm in ([1, 2, 0, 3], [2, 0, 1, 3], [1, 0, 3, 2], [3, 2, 1, 0], [0, 2, 3, 1]):
+            Fp = oracle.element(X[perm], U[perm], 1.0, 1e-2, c_vreman=cv)
+            assert np.abs(Fp - F[perm]).max() < 1e-13 * np.abs(F).max()
+        # rotation + translation: momentum rotates, continuity invariant
+        Q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+        if np.linalg.det(Q) < 0:
+            Q[:, 0] *= -1
+        Xr = X @ Q.T + np.array([0.3, -1.2, 2.0])
+        Ur = U.copy()
+        Ur[:, :3] = U[:, :3] @ Q.T
+        Fr = oracle.element(Xr, Ur, 1.0, 1e-2, c_vreman=cv)
+        assert np.abs(Fr[:, :3] - F[:, :3] @ Q.T).max() < 1e-12 * np.abs(F).max()
+        assert np.abs(Fr[:, 3] - F[:, 3]).max() < 1e-12 * np.abs(F).max()
+
+
+def test_linearity_in_pressure():
+    rng = np.random.default_rng(3)
+    X = random_tet(rng)
+    U = rng.normal(size=(4, 4))
+    p1, p2 = rng.normal(size=4), rng.normal(size=4)
+
+    def f(p):
+        W = U.copy()
+        W[:, 3] = p
+        return oracle.element(X, W, 1.0, 1e-2, c_vreman=0.07)
+    d = f(p1 + p2) - f(p1) - f(p2) + f(np.zeros(4))
+    assert np.abs(d).max() < 1e-13 * np.abs(f(p1)).max()
+
+
+def test_inverted_tet_rejected():
+    X = ref_tet()[[0, 2, 1, 3]]
+    with pytest.raises(ValueError):
+        oracle.element(X, np.zeros((4, 4)), 1.0, 1e-2)
+
+
+@pytest.fixture(scope="module")
+def mesh6():
+    coords, conn, _, _ = mg.box_mesh(6, 0.1)
+    up = mg.fields(coords)
+    return coords, conn, up
+
+
+def boundary_faces(conn):
+    f = np.concatenate([conn[[1, 2, 3]], conn[[0, 2, 3]], conn[[0, 1, 3]], conn[[0, 1, 2]]], axis=1)
+    fs = np.sort(f.T, axis=1)
+    uf, counts = np.unique(fs, axis=0, return_counts=True)
+    return uf[counts == 1]
+
+
+def outward_area_normals(coords, faces):
+    P = coords[:, faces]  # [3][F][3]
+    n = np.cross((P[:, :, 1] - P[:, :, 0]).T, (P[:, :, 2] - P[:, :, 0]).T) / 2.0  # [F][3]
+    centre = P.mean(axis=2).T
+    sign = np.sign(np.sum(n * (centre - 0.5), axis=1))
+    return n * sign[:, None]
+
+
+def test_global_divergence_theorem(mesh6):
+    """sum over nodes of the continuity RHS = -int div u = -oint u.n
+    (the stabilisation part sums to zero element by element)."""
+    coords, conn, up = mesh6
+    rhs = oracle.assemble(coords, conn, up, 1.0, 1e-2)
+    faces = boundary_faces(conn)
+    nA = outward_area_normals(coords, faces)
+    umean = up[:3, faces].mean(axis=2).T            # [F][3]
+    flux = np.sum(nA * umean)
+    assert abs(rhs[3].sum() + flux) < 1e-13 * (1 + abs(flux))
+
+
+def test_constant_fields(mesh6):
+    coords, conn, _ = mesh6
+    N = coords.shape[1]
+    # constant velocity, zero pressure: no gradients, no residual -> RHS = 0
+    up = np.zeros((4, N))
+    up[:3] = np.array([0.3, -2.0, 1.1])[:, None]
+    rhs = oracle.assemble(coords, conn, up, 1.0, 1e-2, c_vreman=0.07)
+    assert np.abs(rhs).max() < 1e-16
+    # zero velocity, constant pressure p0: momentum RHS = p0 oint N_a n
+    # (zero at interior nodes), continuity RHS = 0
+    p0 = 1.7
+    up = np.zeros((4, N))
+    up[3] = p0
+    rhs = oracle.assemble(coords, conn, up, 1.0, 1e-2)
+    faces = boundary_faces(conn)
+    nA = outward_area_normals(coords, faces)
+    expect = np.zeros((3, N))
+    for k in range(3):
+        np.add.at(expect.T, faces[:, k], p0 * nA / 3.0)
+    assert np.abs(rhs[:3] - expect).max() < 1e-15
+    assert np.abs(rhs[3]).max() < 1e-16
+
+
+def test_global_invariances(mesh6):
+    coords, conn, up = mesh6
+    N, E = coords.shape[1], conn.shape[1]
+    rhs = oracle.assemble(coords, conn, up, 1.0, 1e-2, c_vreman=0.07)
+    scale = np.abs(rhs).max()
+    # node renumbering
+    order = mg.random_order(N)
+    c2, cn2, up2 = mg.renumber(order, coords, conn, up)
+    rhs2 = oracle.assemble(c2, cn2, up2, 1.0, 1e-2, c_vreman=0.07)
+    assert np.abs(rhs2 - rhs[:, order]).max() < 1e-14 * scale
+    # element order
+    perm = np.random.default_rng(0).permutation(E)
+    rhs3 = oracle.assemble(coords, conn[:, perm], up, 1.0, 1e-2, c_vreman=0.07)
+    assert np.abs(rhs3 - rhs).max() < 1e-14 * scale
+    # element slices add up
+    half = oracle.assemble(coords, conn, up, 1.0, 1e-2, c_vreman=0.07, e0=0, e1=E // 3)
+    rest = oracle.assemble(coords, conn, up, 1.0, 1e-2, c_vreman=0.07, e0=E // 3, e1=E)
+    assert np.abs(half + rest - rhs).max() < 1e-14 * scale
+    # rigid rotation of the whole problem
+    Q, _ = np.linalg.qr(np.random.default_rng(1).normal(size=(3, 3)))
+    if np.linalg.det(Q) < 0:
+        Q[:, 0] *= -1
+    upr = up.copy()
+    upr[:3] = Q @ up[:3]
+    rr = oracle.assemble(Q @ coords, conn, upr, 1.0, 1e-2, c_vreman=0.07)
+    assert np.abs(rr[:3] - Q @ rhs[:3]).max() < 1e-13 * scale
+    assert np.abs(rr[3] - rhs[3]).max() < 1e-13 * scale
+
+
+def test_complex_step_matches_central_differences(mesh6):
+    coords, conn, up = mesh6
+    d = mg.normal(up.shape, seed=mg.SEED_DIRS)
+    for cv in (0.0, 0.07):
+        s = 1e-30
+        jv = oracle.assemble_complex(coords, conn, up + 1j * s * d, 1.0, 1e-2, c_vreman=cv).imag / s
+        eps = 1e-6
+        fd = (oracle.assemble(coords, conn, up + eps * d, 1.0, 1e-2, c_vreman=cv) -
+              oracle.assemble(coords, conn, up - eps * d, 1.0, 1e-2, c_vreman=cv)) / (2 * eps)
+        assert np.linalg.norm(jv - fd) <= 1e-7 * np.linalg.norm(jv)
+        # the complex evaluation's real part is the real RHS
+        re = oracle.assemble_complex(coords, conn, up + 1j * s * d, 1.0, 1e-2, c_vreman=cv).real
+        assert np.abs(re - oracle.assemble(coords, conn, up, 1.0, 1e-2, c_vreman=cv)).max() < 1e-15
+
+
+def test_vjp_against_full_complex_step_jacobian():
+    coords, conn, _, _ = mg.box_mesh(2, 0.1)
+    up = mg.fields(coords)
+    N = coords.shape[1]
+    w = mg.normal((4, N), seed=mg.SEED_COT)
+    for cv in (0.0, 0.07):
+        s = 1e-30
+        J = np.empty((4 * N, 4 * N))
+        for col in range(4 * N):
+            e = np.zeros(4 * N)
+            e[col] = s
+            J[:, col] = (oracle.assemble_complex(coords, conn, up + 1j * e.reshape(4, N), 1.0,
+                                                 1e-2, c_vreman=cv).imag / s).ravel()
+        ref = (J.T @ w.ravel()).reshape(4, N)
+        g = oracle.vjp(coords, conn, up, w, 1.0, 1e-2, c_vreman=cv)
+        assert np.linalg.norm(g - ref) <= 1e-13 * np.linalg.norm(ref)
+
+
+def test_vjp_dot_product_identity(mesh6):
+    coords, conn, up = mesh6
+    N = coords.shape[1]
+    w = mg.normal((4, N), seed=mg.SEED_COT)
+    v = mg.normal((4, N), seed=mg.SEED_DIRS)
+    s = 1e-30
+    jv = oracle.assemble_complex(coords, conn, up + 1j * s * v, 1.0, 1e-4).imag / s
+    g = oracle.vjp(coords, conn, up, w, 1.0, 1e-4)
+    lhs, rhs = np.sum(w * jv), np.sum(g * v)
+    assert abs(lhs - rhs) <= 1e-12 * np.sqrt(np.sum(w * w) * np.sum(jv * jv))
