@@ -1,0 +1,485 @@
+#!/usr/bin/env python3
+"""Benchmark of the tetrahedral Navier-Stokes RHS assembly on one GB300.
+
+One step = one pass of the whole hot path over the workload: the FP64 RHS
+assembly (zeroing + gather + element arithmetic + scatter) followed by its
+adjoint (vector-Jacobian product) on the same nodal fields.
+
+Workload (stands in for the paper's 32M-tet Bolund LES mesh, Sec. III-A,
+which is not available): unit cube of 256^3 hexes split into 6 Kuhn tets
+each (100,663,296 tets, 16,974,593 nodes), interior nodes jittered by
++-0.1 h, RCM node order, rho = 1, mu = 1e-4, velocity = Taylor-Green +
+N(0, 1e-2) noise + m*d with m ~ U(0, 10) and d uniform on the sphere,
+pressure ~ U(-1, 1), seeded and synthetic.
+
+Prints one JSON line (rank 0). --impl reference times the CPU oracle
+instead (bounded sample, host cores).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import meshgen as mg  # noqa: E402
+
+METRIC = "tets assembled/sec + FP64 TF/s (fraction of roofline), FP32 & adjoint vs plain FP64"
+UNIT = "tets/s"
+
+# Algorithmic FP64 operations per tet of the kernels' formulation
+# (add/sub/mul = 1, fused multiply-add = 2, sqrt/reciprocal/cube root = 1),
+# counted by instantiating the element code with a counting scalar
+# (tests/test_flop_count.py keeps these numbers in step with the source).
+FLOPS_PER_TET = {"fwd": 571, "vjp": 1170}
+FLOPS_PER_TET_VREMAN = {"fwd": 640, "vjp": 1315}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=256, help="hexes per cube edge")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision lines")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--sample-fwd", type=int, default=1 << 20,
+                    help="oracle forward elements per host process")
+    ap.add_argument("--sample-vjp", type=int, default=1 << 16,
+                    help="oracle adjoint elements per host process")
+    return ap.parse_args()
+
+
+def workload(n: int):
+    return mg.paper_scale(n=n, order="rcm")
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle baseline (fork-based pool, started before any CUDA call).
+
+_W = None
+
+
+def _compact(e0, e1):
+    conn = _W.conn[:, e0:e1]
+    nodes, inv = np.unique(conn, return_inverse=True)
+    return (np.ascontiguousarray(_W.coords[:, nodes]), inv.reshape(conn.shape).astype(np.int32),
+            np.ascontiguousarray(_W.up[:, nodes]))
+
+
+def _oracle_slice(args):
+    import oracle
+    e0, e1, kind, seed = args
+    coords, conn, up = _compact(e0, e1)
+    if kind == "fwd":
+        t = time.perf_counter()
+        oracle.assemble(coords, conn, up, _W.rho, _W.mu, c_vreman=_W.c_vreman)
+        return time.perf_counter() - t
+    cot = mg.normal(up.shape, seed=seed)
+    t = time.perf_counter()
+    oracle.vjp(coords, conn, up, cot, _W.rho, _W.mu, c_vreman=_W.c_vreman)
+    return time.perf_counter() - t
+
+
+def cpu_oracle_rates(w, procs: int, n_fwd: int, n_vjp: int, repeats: int = 1):
+    """Oracle tets/s for the forward and the adjoint, `procs` processes each
+    over its own slice of consecutive elements (nodes compacted per slice).
+    Returns (fwd_rate, vjp_rate, step_rate, wall_times)."""
+    import oracle
+    oracle.build()
+    global _W
+    _W = w
+    E = w.n_elems
+    procs = max(1, procs)
+    n_fwd = min(n_fwd, E // procs)
+    n_vjp = min(n_vjp, E // procs)
+    ctx = mp.get_context("fork")
+    walls = []
+    with ctx.Pool(procs) as pool:
+        for _ in range(repeats):
+            t0 = time.perf_counter()
+            pool.map(_oracle_slice, [(i * n_fwd, (i + 1) * n_fwd, "fwd", 0) for i in range(procs)])
+            t1 = time.perf_counter()
+            pool.map(_oracle_slice, [(i * n_vjp, (i + 1) * n_vjp, "vjp", mg.SEED_COT)
+                                     for i in range(procs)])
+            t2 = time.perf_counter()
+            walls.append((t1 - t0, t2 - t1))
+    tf = statistics.median(x[0] for x in walls)
+    tv = statistics.median(x[1] for x in walls)
+    fwd_rate = procs * n_fwd / tf
+    vjp_rate = procs * n_vjp / tv
+    step_rate = 1.0 / (1.0 / fwd_rate + 1.0 / vjp_rate)
+    sample = (f"{procs} host processes, each over its own {n_fwd} (forward) and {n_vjp} "
+              f"(adjoint) consecutive elements of the {w.name} mesh, nodes compacted per slice; "
+              f"rate = elements / wall time, step rate = 1/(1/fwd + 1/adjoint)")
+    return fwd_rate, vjp_rate, step_rate, sample, walls
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+# ---------------------------------------------------------------------------
+# Clock sampling during the timed region.
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: str):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", gpu_index], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    w = workload(args.n)
+    procs = host_cores()
+    cpu_oracle_rates(w, procs, args.sample_fwd, args.sample_vjp, repeats=max(1, args.warmup))
+    fwd, vjp, step, sample, walls = cpu_oracle_rates(w, procs, args.sample_fwd, args.sample_vjp,
+                                                     repeats=args.steps)
+    ms = 1e3 * w.n_elems / step
+    line = {"metric": METRIC, "value": step, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": w.name, "n_tets": w.n_elems, "n_nodes": w.n_nodes,
+                       "rho": w.rho, "mu": w.mu, "step": "fp64 forward + adjoint",
+                       "sample": sample},
+            "cpu_baseline": {"value": step, "unit": UNIT, "cores": procs, "kind": "oracle",
+                             "sample": sample, "fwd_tets_per_s": fwd, "vjp_tets_per_s": vjp},
+            "e2e": {"value": step, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    world, rank, local = dist_env()
+    w = workload(args.n)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        procs = host_cores()
+        fwd, vjp, step, sample, _ = cpu_oracle_rates(w, procs, args.sample_fwd, args.sample_vjp)
+        cpu = {"value": step, "unit": UNIT, "cores": procs, "kind": "oracle", "sample": sample,
+               "fwd_tets_per_s": fwd, "vjp_tets_per_s": vjp}
+
+    import torch
+    import paper_2403_08777_gb300 as ns
+    from paper_2403_08777_gb300 import _abi
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    lib = ns.load_library()
+
+    coords = torch.from_numpy(w.coords).to(dev)
+    conn = torch.from_numpy(w.conn).to(dev)
+    up = torch.from_numpy(w.up).to(dev)
+    cot_h = mg.normal((4, w.n_nodes), seed=mg.SEED_COT)
+    cot = torch.from_numpy(cot_h).to(dev)
+    mesh = ns.Mesh(coords, conn)
+    del coords, conn
+    p = ns.Params(rho=w.rho, mu=w.mu, c_vreman=w.c_vreman)
+    rhs = torch.empty((4, w.n_nodes), dtype=torch.float64, device=dev)
+    grad = torch.empty_like(rhs)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def step(evs=None):
+        if evs is not None:
+            evs[0].record(stream)
+        mesh.assemble(up, p, out=rhs)
+        if evs is not None:
+            evs[1].record(stream)
+        mesh.assemble_vjp(up, cot, p, out=grad)
+        if evs is not None:
+            evs[2].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+
+    gpu_index = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local]
+    sampler = ClockSampler(gpu_index)
+    time.sleep(0.3)
+    per = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize(dev)
+    t_wall = time.perf_counter()
+    start.record(stream)
+    for k in range(args.steps):
+        step(per[k])
+    end.record(stream)
+    torch.cuda.synchronize(dev)
+    t_wall = time.perf_counter() - t_wall
+    barrier()
+    clocks = sampler.stop()
+    ms_total = start.elapsed_time(end)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    fwd_ms = [e[0].elapsed_time(e[1]) for e in per]
+    vjp_ms = [e[1].elapsed_time(e[2]) for e in per]
+    ms_step = ms_total / args.steps
+    value = world * w.n_elems / (ms_step * 1e-3)
+
+    # ---- end to end: host buffers, copies inside the timed region ----
+    up_h = torch.from_numpy(w.up).pin_memory()
+    cot_hp = torch.from_numpy(cot_h).pin_memory()
+    rhs_h = torch.empty((4, w.n_nodes), dtype=torch.float64).pin_memory()
+    grad_h = torch.empty_like(rhs_h).pin_memory()
+    up_d, cot_d = torch.empty_like(up), torch.empty_like(cot)
+
+    def e2e_step():
+        up_d.copy_(up_h, non_blocking=True)
+        cot_d.copy_(cot_hp, non_blocking=True)
+        mesh.assemble(up_d, p, out=rhs)
+        mesh.assemble_vjp(up_d, cot_d, p, out=grad)
+        rhs_h.copy_(rhs, non_blocking=True)
+        grad_h.copy_(grad, non_blocking=True)
+
+    for _ in range(args.warmup):
+        e2e_step()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+    bytes_nodal = 4 * w.n_nodes * 8
+
+    # ---- FMA peaks (live) ----
+    sink = torch.empty(sm_blocks(dev) * 256, dtype=torch.float64, device=dev)
+
+    def probe(fp64: bool, iters: int) -> float:
+        blocks = sm_blocks(dev)
+        lib.nsrhs_probe_fma(int(fp64), blocks, 1000, _ptr(sink), _stream(stream))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        rc = lib.nsrhs_probe_fma(int(fp64), blocks, iters, _ptr(sink), _stream(stream))
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        assert rc == 0
+        return blocks * 256 * 8 * iters * 2 / (a.elapsed_time(b) * 1e-3) / 1e12
+
+    fp64_peak = max(probe(True, 20000) for _ in range(3))
+    fp32_peak = max(probe(False, 400000) for _ in range(3))
+
+    # ---- mixed precision ----
+    forms = {}
+    fwd_med, vjp_med = statistics.median(fwd_ms), statistics.median(vjp_ms)
+    flops = FLOPS_PER_TET_VREMAN if w.c_vreman else FLOPS_PER_TET
+    forms["fwd_fp64"] = {"ms": fwd_med, "tets_per_s": w.n_elems / (fwd_med * 1e-3),
+                         "tflops": flops["fwd"] * w.n_elems / (fwd_med * 1e-3) / 1e12}
+    forms["vjp_fp64"] = {"ms": vjp_med, "tets_per_s": w.n_elems / (vjp_med * 1e-3),
+                         "tflops": flops["vjp"] * w.n_elems / (vjp_med * 1e-3) / 1e12,
+                         "vs_fwd_fp64": fwd_med / vjp_med}
+    if not args.no_mixed:
+        forms["mixed_same_mesh"] = time_mixed(mesh, w, dev, stream, args, fwd_med)
+        mesh.close()
+        del mesh
+        torch.cuda.empty_cache()
+        wj = mg.precision_case(n=args.n, order="rcm")
+        cj = torch.from_numpy(wj.coords).to(dev)
+        nj = torch.from_numpy(wj.conn).to(dev)
+        mj = ns.Mesh(cj, nj)
+        del cj, nj
+        upj = torch.from_numpy(wj.up).to(dev)
+        pj = ns.Params(rho=wj.rho, mu=wj.mu)
+        for _ in range(args.warmup):
+            mj.assemble(upj, pj)
+        fa, fb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        fa.record(stream)
+        for _ in range(args.steps):
+            mj.assemble(upj, pj)
+        fb.record(stream)
+        torch.cuda.synchronize(dev)
+        fp64_j = fa.elapsed_time(fb) / args.steps
+        mixed = time_mixed(mj, wj, dev, stream, args, fp64_j)
+        mixed["n_high_ar"] = mj.info()["n_high_ar"]
+        mixed["err_vs_oracle_64cube"] = mixed_error_64()
+        forms["mixed_jitter03"] = mixed
+        mj.close()
+
+    dom = "vjp_fp64" if vjp_med >= fwd_med else "fwd_fp64"
+    dom_ms = vjp_med if dom == "vjp_fp64" else fwd_med
+    achieved = forms[dom]["tflops"]
+    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fp64_peak,
+                "unit": "TFLOP/s", "frac": achieved / fp64_peak, "traffic": None,
+                "peak_source": "FP64 FMA-chain probe measured live in this run (not in "
+                               "MEASURED_PEAKS.json)",
+                "flops_per_tet": flops["vjp" if dom == "vjp_fp64" else "fwd"],
+                "launch_ms": dom_ms}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "n_tets": w.n_elems, "n_nodes": w.n_nodes,
+                       "rho": w.rho, "mu": w.mu, "jitter": w.jitter, "order": w.order,
+                       "step": "fp64 forward assembly + fp64 adjoint (VJP)",
+                       "l2": "inputs larger than L2 (conn 1.6 GB + nodal 1.5 GB per step)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roofline,
+            "roofline_fwd": {"bound": "alu", "achieved": forms["fwd_fp64"]["tflops"],
+                             "peak": fp64_peak, "unit": "TFLOP/s",
+                             "frac": forms["fwd_fp64"]["tflops"] / fp64_peak},
+            "peaks": {"fp64_tflops": fp64_peak, "fp32_tflops": fp32_peak,
+                      "hbm_gbs_measured_peaks_json": _measured_hbm()},
+            "forms": forms,
+            "e2e": {"value": world * w.n_elems / (e2e_ms * 1e-3), "unit": UNIT,
+                    "h2d_bytes_per_step": 2 * bytes_nodal, "d2h_bytes_per_step": 2 * bytes_nodal,
+                    "ms_per_step": e2e_ms},
+            "gpu_launches": 2 * args.steps,
+            "clocks": clocks,
+            "wall_s_timed": t_wall}
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def time_mixed(mesh, w, dev, stream, args, fp64_ms):
+    import torch
+    import paper_2403_08777_gb300 as ns
+    up32 = torch.from_numpy(w.up).to(dev).float()
+    pm = ns.Params(rho=w.rho, mu=w.mu, c_vreman=w.c_vreman, precision="mixed")
+    out = torch.empty((4, w.n_nodes), dtype=torch.float64, device=dev)
+    for _ in range(args.warmup):
+        mesh.assemble(up32, pm, out=out)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(args.steps):
+        mesh.assemble(up32, pm, out=out)
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = a.elapsed_time(b) / args.steps
+    return {"ms": ms, "tets_per_s": w.n_elems / (ms * 1e-3), "fp64_ms": fp64_ms,
+            "speedup_vs_fp64": fp64_ms / ms, "workload": w.name}
+
+
+def mixed_error_64() -> float:
+    """Norm-wise error of the mixed form against the oracle on the 64^3
+    jitter-0.3 sub-run (1,572,864 tets)."""
+    import torch
+    import oracle
+    import paper_2403_08777_gb300 as ns
+    w = mg.precision_case(n=64, order="rcm")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    m = ns.Mesh(torch.from_numpy(w.coords).to(dev), torch.from_numpy(w.conn).to(dev))
+    x = m.assemble(torch.from_numpy(w.up).to(dev).float(),
+                   ns.Params(rho=w.rho, mu=w.mu, precision="mixed")).cpu().numpy()
+    m.close()
+    ref = oracle.assemble(w.coords, w.conn, w.up, w.rho, w.mu)
+    return float(np.linalg.norm(x - ref) / np.linalg.norm(ref))
+
+
+def sm_blocks(dev) -> int:
+    import torch
+    return torch.cuda.get_device_properties(dev).multi_processor_count * 8
+
+
+def _ptr(t):
+    import ctypes
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(s):
+    import ctypes
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _measured_hbm():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f).get("hbm_gbs")
+    except (OSError, ValueError):
+        return None
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,155 @@
+/*
+ * nsrhs — element-by-element assembly of the incompressible Navier-Stokes
+ * right-hand side on linear tetrahedra, on one NVIDIA GB300 (sm_103a).
+ *
+ * What is assembled (the paper, arXiv 2403.08777, names the method but prints
+ * no formulas; this is the library's definition of it):
+ *   - the RHS of the explicit momentum step of an incompressible LES
+ *     (Sec. II), plus the continuity residual, on linear tets with 4 nodes and
+ *     4 Gauss points and constant shape-function gradients (Sec. V-B);
+ *   - constant density rho and viscosity mu; Vreman eddy viscosity computed
+ *     once per element from the constant velocity gradient (Sec. V-B);
+ *   - SUPG/PSPG stabilisation, tau = 1/(c1 mu_eff/h^2 + c2 rho |u|/h) at each
+ *     Gauss point, h = detJ^(1/3);
+ *   - the element RHS computed directly, without element matrices (Sec. V-A),
+ *     and scatter-added into the global nodal RHS (Sec. V-D).
+ *   For test function N_a of an element (u, p linear on it):
+ *     F_a,i = int[ -rho N_a (u.grad)u_i - mu_eff grad N_a.grad u_i + p dN_a/dx_i
+ *                  - tau rho (u.grad N_a)(rho (u.grad)u_i + dp/dx_i) ]
+ *     F_a,4 = int[ -N_a div u - tau grad N_a.(rho (u.grad)u + grad p) ]
+ *   with every integral evaluated by the 4-point degree-2 rule, and
+ *   RHS[conn[a][e]] += F_a over all elements e and local nodes a.
+ *
+ * Layouts (structure of arrays, node or element index fastest):
+ *   coords [3][n_nodes] double        x, y, z
+ *   conn   [4][n_elems] int32         local node a of element e at conn[a*n_elems + e]
+ *   up     [4][n_nodes] double/float  u, v, w, p
+ *   rhs, cot, grad [4][n_nodes] double
+ *
+ * Execution: every call is asynchronous on the CUDA stream it is given
+ * (NULL = legacy default stream) except nsrhs_mesh_create, which
+ * synchronises that stream once to read back its validation result.
+ * Device pointers only (cudaMalloc, cudaMallocAsync, managed memory, or
+ * torch CUDA tensors). A kernel fault surfaces as NSRHS_ECUDA on the call
+ * that launched it or on a later call.
+ *
+ * Errors: no call throws. On NSRHS_EINVAL the outputs are untouched. Status
+ * strings come from nsrhs_status_string.
+ */
+#ifndef NSRHS_H
+#define NSRHS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nsrhs_mesh nsrhs_mesh; /* opaque; owned by the library */
+
+typedef enum {
+  NSRHS_OK = 0,
+  NSRHS_EINVAL = 1,      /* bad argument: NULL pointer, size <= 0 or too large,
+                            unknown enum value, destroyed mesh */
+  NSRHS_ENOMEM = 2,      /* device allocation failed */
+  NSRHS_EMESH = 3,       /* connectivity index out of [0, n_nodes) or an element
+                            with detJ <= 0 (no silent reorientation) */
+  NSRHS_ECUDA = 4,       /* a CUDA runtime call or kernel launch failed */
+  NSRHS_EUNSUPPORTED = 5 /* valid request that this build does not implement */
+} nsrhs_status;
+
+typedef enum {
+  NSRHS_FP64 = 0, /* double precision throughout */
+  NSRHS_MIXED = 1 /* float nodal (u,p) and float element arithmetic; double
+                     coordinate differences, double det/inverse on elements
+                     whose aspect ratio exceeds the mesh's threshold, double
+                     global accumulation */
+} nsrhs_precision;
+
+typedef enum {
+  NSRHS_SCATTER_AUTO = 0,   /* the measured fastest for the precision */
+  NSRHS_SCATTER_ATOMIC = 1, /* one double-precision atomic add per entry */
+  NSRHS_SCATTER_BLOCK = 2   /* per-block node-local accumulation in shared
+                               memory, one atomic per (block, node, component) */
+} nsrhs_scatter;
+
+/* Physical and numerical parameters (uniform over one call). */
+typedef struct {
+  double rho;        /* density, >= 0 */
+  double mu;         /* dynamic viscosity, > 0 */
+  double c_vreman;   /* Vreman constant (about 0.07); 0 switches the model off */
+  double c1, c2;     /* stabilisation constants of tau (4 and 2) */
+  int32_t precision; /* nsrhs_precision */
+  int32_t scatter;   /* nsrhs_scatter */
+} nsrhs_params;
+
+/* Mesh options. */
+typedef struct {
+  double ar_threshold; /* aspect ratio above which the mixed form keeps double
+                          geometry; 10 by default. AR = l_max S / (6 sqrt(6) V)
+                          (l_max longest edge, S surface, V volume; 1 for the
+                          regular tet). */
+} nsrhs_mesh_opts;
+
+/* Read-only facts about a created mesh. */
+typedef struct {
+  int64_t n_nodes, n_elems;
+  int64_t n_high_ar;      /* elements with AR > ar_threshold */
+  int64_t n_blocks;       /* element blocks of the BLOCK scatter */
+  int64_t block_elems;    /* elements per block */
+  int64_t device_bytes;   /* device memory held by the mesh */
+  double min_detj, max_ar;
+} nsrhs_mesh_info;
+
+/* Fill *p with rho=1, mu=1e-2, c_vreman=0, c1=4, c2=2, FP64, AUTO. */
+void nsrhs_params_default(nsrhs_params* p);
+
+/* Fill *o with ar_threshold = 10. */
+void nsrhs_mesh_opts_default(nsrhs_mesh_opts* o);
+
+/*
+ * Create a mesh from device arrays coords [3][n_nodes] and conn [4][n_elems].
+ * The library copies both (the caller may free them afterwards), checks on
+ * the device that every index is in range and every element has detJ > 0,
+ * classifies elements by aspect ratio, and builds the element blocks of the
+ * BLOCK scatter. opts may be NULL (defaults). Synchronises `stream` once.
+ * 1 <= n_nodes < 2^31, 1 <= n_elems < 2^31.
+ * On error *out is set to NULL and nothing is leaked.
+ */
+nsrhs_status nsrhs_mesh_create(int64_t n_nodes, int64_t n_elems, const double* coords,
+                               const int32_t* conn, const nsrhs_mesh_opts* opts, void* stream,
+                               nsrhs_mesh** out);
+
+nsrhs_status nsrhs_mesh_get_info(const nsrhs_mesh* m, nsrhs_mesh_info* info);
+
+/*
+ * rhs = assembled RHS of (up) on mesh m (see the definition above).
+ * up is [4][n_nodes] double for NSRHS_FP64 and [4][n_nodes] float for
+ * NSRHS_MIXED; rhs [4][n_nodes] double is overwritten (zeroed, then summed
+ * into). up and rhs must not overlap. The summation order of the atomic
+ * adds is unspecified, so results agree with a serial sum to rounding only.
+ */
+nsrhs_status nsrhs_assemble(const nsrhs_mesh* m, const nsrhs_params* p, const void* up,
+                            double* rhs, void* stream);
+
+/*
+ * Vector-Jacobian product of the assembly: grad = (d rhs / d up)^T cot,
+ * all [4][n_nodes] double, for NSRHS_FP64 parameters (precision must be
+ * NSRHS_FP64). The element quantities are recomputed, not stored. grad is
+ * overwritten. This is the adjoint of nsrhs_assemble with respect to the
+ * nodal velocity and pressure; the mesh and parameters are constants.
+ */
+nsrhs_status nsrhs_assemble_vjp(const nsrhs_mesh* m, const nsrhs_params* p, const double* up,
+                                const double* cot, double* grad, void* stream);
+
+/* Free the mesh and its device memory. NULL-safe. Synchronises the device
+   memory it frees (cudaFree semantics). */
+void nsrhs_destroy(nsrhs_mesh* m);
+
+const char* nsrhs_status_string(nsrhs_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NSRHS_H */

@@ -1,0 +1,33 @@
+/*
+ * nsrhs_probe — machine-peak probes used to state the roofline of the
+ * assembly kernels. The paper measures its machines' FP peaks with
+ * microbenchmarks (Sec. III-B, III-C: likwid-bench peakflops, 9.7 TF/s FP64
+ * on the A100) and places its kernels on that roofline (Sec. V-D, Fig. 4).
+ * The element kernels here are bound by the FP64 pipe (no tensor cores), so
+ * the denominator is this probe's measured FMA rate.
+ */
+#ifndef NSRHS_PROBE_H
+#define NSRHS_PROBE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/*
+ * Launch an FMA-throughput kernel on `stream`: `blocks` blocks of 256
+ * threads, each thread running 8 independent dependent chains of `iters`
+ * fused multiply-adds in double (fp64 != 0) or float (fp64 == 0), then
+ * writing one value per thread to sink[blocks * 256] (device memory, double)
+ * so that the work cannot be removed. FLOPs per launch =
+ * blocks * 256 * 8 * iters * 2. Time it with events on the same stream.
+ * Returns 0, or a nonzero nsrhs_status value (1 bad argument, 4 CUDA error).
+ */
+int nsrhs_probe_fma(int fp64, int64_t blocks, int64_t iters, double* sink, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NSRHS_PROBE_H */

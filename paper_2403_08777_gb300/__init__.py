@@ -1,0 +1,199 @@
+"""GB300-native Navier-Stokes RHS assembly on linear tetrahedra (arXiv 2403.08777).
+
+Thin Python binding over the C ABI of ``include/nsrhs.h``: argument
+marshalling only. Every step of the assembly runs in the CUDA kernels of
+``libnsrhs.so``; PyTorch provides device memory and the current stream.
+There is no CPU fallback: if the library has not been built, the calls raise.
+
+    mesh = Mesh(coords_cuda_f64[3, N], conn_cuda_i32[4, E])
+    rhs  = mesh.assemble(up_cuda_f64[4, N], rho=1.0, mu=1e-2)        # [4, N] f64
+    grad = mesh.assemble_vjp(up, cot)                                 # [4, N] f64
+    rhs  = assemble(mesh, up, rho=1.0, mu=1e-2)                      # differentiable in up
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import torch
+
+from . import _abi
+from ._abi import NSRHSError, NativeLibraryMissing  # noqa: F401
+
+__all__ = ["Mesh", "Params", "assemble", "NSRHSFunction", "NSRHSError", "NativeLibraryMissing",
+           "load_library"]
+
+_PREC = {"fp64": _abi.FP64, "mixed": _abi.MIXED}
+_SCAT = {"auto": _abi.SCATTER_AUTO, "atomic": _abi.SCATTER_ATOMIC, "block": _abi.SCATTER_BLOCK}
+
+
+def load_library():
+    return _abi.load()
+
+
+@dataclass(frozen=True)
+class Params:
+    rho: float = 1.0
+    mu: float = 1e-2
+    c_vreman: float = 0.0
+    c1: float = 4.0
+    c2: float = 2.0
+    precision: str = "fp64"
+    scatter: str = "auto"
+
+    def to_c(self) -> _abi.Params:
+        if self.precision not in _PREC or self.scatter not in _SCAT:
+            raise ValueError(f"bad precision/scatter {self.precision}/{self.scatter}")
+        return _abi.Params(self.rho, self.mu, self.c_vreman, self.c1, self.c2,
+                           _PREC[self.precision], _SCAT[self.scatter])
+
+
+def _stream_handle(device: torch.device) -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _require(t: torch.Tensor, name: str, dtype, shape, device=None):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if device is not None and t.device != device:
+        raise ValueError(f"{name} is on {t.device}, mesh is on {device}")
+
+
+class Mesh:
+    """A tetrahedral mesh resident on one GPU (library-owned device copies)."""
+
+    def __init__(self, coords: torch.Tensor, conn: torch.Tensor, ar_threshold: float = 10.0):
+        lib = _abi.load()
+        if coords.dim() != 2 or coords.shape[0] != 3 or conn.dim() != 2 or conn.shape[0] != 4:
+            raise ValueError("coords must be [3, N] and conn [4, E]")
+        _require(coords, "coords", torch.float64, coords.shape)
+        _require(conn, "conn", torch.int32, conn.shape, coords.device)
+        self.device = coords.device
+        self.n_nodes, self.n_elems = int(coords.shape[1]), int(conn.shape[1])
+        opts = _abi.MeshOpts(float(ar_threshold))
+        handle = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            st = lib.nsrhs_mesh_create(self.n_nodes, self.n_elems, ctypes.c_void_p(coords.data_ptr()),
+                                       ctypes.c_void_p(conn.data_ptr()), ctypes.byref(opts),
+                                       _stream_handle(self.device), ctypes.byref(handle))
+        _abi.check(st, "nsrhs_mesh_create")
+        self._h = handle
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        if self._h is None:
+            raise RuntimeError("mesh has been closed")
+        return self._h
+
+    def info(self) -> dict:
+        inf = _abi.MeshInfo()
+        _abi.check(_abi.load().nsrhs_mesh_get_info(self.handle, ctypes.byref(inf)),
+                   "nsrhs_mesh_get_info")
+        return {f: getattr(inf, f) for f, _ in _abi.MeshInfo._fields_}
+
+    def _params(self, params: Params | None, kw) -> Params:
+        if params is None:
+            params = Params(**kw)
+        elif kw:
+            raise TypeError("pass either params or keyword parameters")
+        return params
+
+    def assemble(self, up: torch.Tensor, params: Params | None = None, *, out=None, **kw):
+        """RHS [4, N] float64 of nodal fields up [4, N] (float64, or float32
+        with precision='mixed'), on the current stream."""
+        p = self._params(params, kw)
+        dt = torch.float32 if p.precision == "mixed" else torch.float64
+        _require(up, "up", dt, (4, self.n_nodes), self.device)
+        if out is None:
+            out = torch.empty((4, self.n_nodes), dtype=torch.float64, device=self.device)
+        else:
+            _require(out, "out", torch.float64, (4, self.n_nodes), self.device)
+        cp = p.to_c()
+        with torch.cuda.device(self.device):
+            st = _abi.load().nsrhs_assemble(self.handle, ctypes.byref(cp),
+                                            ctypes.c_void_p(up.data_ptr()),
+                                            ctypes.c_void_p(out.data_ptr()),
+                                            _stream_handle(self.device))
+        _abi.check(st, "nsrhs_assemble")
+        return out
+
+    def assemble_vjp(self, up: torch.Tensor, cot: torch.Tensor, params: Params | None = None, *,
+                     out=None, **kw):
+        """(d rhs / d up)^T cot, all [4, N] float64."""
+        p = self._params(params, kw)
+        _require(up, "up", torch.float64, (4, self.n_nodes), self.device)
+        _require(cot, "cot", torch.float64, (4, self.n_nodes), self.device)
+        if out is None:
+            out = torch.empty((4, self.n_nodes), dtype=torch.float64, device=self.device)
+        else:
+            _require(out, "out", torch.float64, (4, self.n_nodes), self.device)
+        cp = p.to_c()
+        with torch.cuda.device(self.device):
+            st = _abi.load().nsrhs_assemble_vjp(self.handle, ctypes.byref(cp),
+                                                ctypes.c_void_p(up.data_ptr()),
+                                                ctypes.c_void_p(cot.data_ptr()),
+                                                ctypes.c_void_p(out.data_ptr()),
+                                                _stream_handle(self.device))
+        _abi.check(st, "nsrhs_assemble_vjp")
+        return out
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None:
+            _abi.load().nsrhs_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class NSRHSFunction(torch.autograd.Function):
+    """rhs = A(up) with the hand-written adjoint kernel as backward.
+    Differentiable with respect to up only (mesh and parameters are constants)."""
+
+    @staticmethod
+    def forward(ctx, up: torch.Tensor, mesh: Mesh, params: Params):
+        if params.precision != "fp64":
+            raise ValueError("NSRHSFunction differentiates the fp64 form")
+        ctx.mesh, ctx.params = mesh, params
+        ctx.save_for_backward(up)
+        return mesh.assemble(up.detach().contiguous(), params)
+
+    @staticmethod
+    def backward(ctx, grad_rhs: torch.Tensor):
+        (up,) = ctx.saved_tensors
+        g = ctx.mesh.assemble_vjp(up.detach().contiguous(), grad_rhs.contiguous(), ctx.params)
+        return g, None, None
+
+
+def assemble(mesh: Mesh, up: torch.Tensor, params: Params | None = None, **kw) -> torch.Tensor:
+    """Differentiable RHS assembly (fp64)."""
+    p = mesh._params(params, kw)
+    return NSRHSFunction.apply(up, mesh, p)
+
+
+def assemble_host(mesh: Mesh, up_host: torch.Tensor, params: Params | None = None,
+                  out_host: torch.Tensor | None = None, **kw) -> torch.Tensor:
+    """End-to-end call on host buffers: copy up (pinned host) to the device,
+    assemble, copy the RHS back into out_host (pinned host), synchronise."""
+    p = mesh._params(params, kw)
+    dt = torch.float32 if p.precision == "mixed" else torch.float64
+    if up_host.is_cuda or up_host.dtype != dt or tuple(up_host.shape) != (4, mesh.n_nodes):
+        raise ValueError("up_host must be a host tensor [4, N] of the precision's dtype")
+    up = up_host.to(mesh.device, non_blocking=True)
+    rhs = mesh.assemble(up, p)
+    if out_host is None:
+        out_host = torch.empty((4, mesh.n_nodes), dtype=torch.float64, pin_memory=True)
+    out_host.copy_(rhs, non_blocking=True)
+    torch.cuda.current_stream(mesh.device).synchronize()
+    return out_host

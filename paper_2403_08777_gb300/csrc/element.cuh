@@ -1,0 +1,456 @@
+// Per-element arithmetic of the tetrahedral Navier-Stokes RHS (device code).
+//
+// The element RHS is the stabilised P1 weak form (Sec. II, V-A, V-B):
+//   F_a,i = int[ -rho N_a (u.grad)u_i - mu_eff grad N_a.grad u_i + p dN_a/dx_i
+//                - tau rho (u.grad N_a)(rho (u.grad)u_i + dp/dx_i) ]
+//   F_a,4 = int[ -N_a div u - tau grad N_a.(rho (u.grad)u + grad p) ]
+// with the 4-point rule (barycentric QA on node g, QB elsewhere, weight V/4),
+// tau_g = 1/(c1 mu_eff/h^2 + c2 rho |u_g|/h), h = detJ^(1/3), and Vreman's
+// eddy viscosity from the constant velocity gradient (Sec. V-B).
+//
+// This file evaluates that form RESTRUCTURED for short intermediate lifetimes
+// (Sec. V-A) and specialised to linear tets (Sec. V-B); it is exactly the
+// same function up to rounding. With the unscaled cofactor vectors
+// c_k = e_{k+1} x e_{k+2} of the edge vectors e_k = X_k - X_0 (so that
+// grad N_k = c_k / detJ, c_0 = -(c_1 + c_2 + c_3)):
+//   Gh = sum_a u_a c_a^T   (= detJ grad u),   gph = sum_a p_a c_a (= detJ grad p)
+//   Galerkin convection: sum_g N_a(xi_g) N_b(xi_g) = (1 + delta_ab)/5 turns the
+//     Gauss sum into -(rho/120) Gh (S_u + u_a), S_u = sum_b u_b;
+//   tau enters only through  stau = sum_g tau_g,  T = sum_g tau_g u_g,
+//     Q = sum_g tau_g u_g u_g^T  (4 square roots and 4 reciprocals in total);
+//   viscous + pressure + SUPG momentum = K c_a with
+//     K = (p_bar/6) I - (1/(6 detJ)) [Gh (mu_eff I + rho^2/4 Q) + rho/4 gph T^T];
+//   continuity = -(tr Gh)/24 - c_a . (rho Gh T + stau gph) / (24 detJ).
+// The reverse (vector-Jacobian) sweep of exactly this sequence is
+// element_vjp below; it recomputes the forward quantities instead of storing
+// them.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace nsrhs {
+
+// 4-point degree-2 Gauss rule on the tet: QA = (5 + 3 sqrt 5)/20, QB = (5 - sqrt 5)/20.
+constexpr double kQA = 0.58541019662496845446;
+constexpr double kQB = 0.13819660112501051518;
+
+template <class R>
+struct ElemParams {
+  R rho, mu, c_vreman, c1, c2;
+};
+
+template <class R>
+struct MathOps;
+
+template <>
+struct MathOps<double> {
+  static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+  static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+  static __device__ __forceinline__ double rcbrt_(double x) { return rcbrt(x); }
+};
+
+template <>
+struct MathOps<float> {
+  static __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+  static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+  static __device__ __forceinline__ float rcbrt_(float x) { return rcbrtf(x); }
+};
+
+// Element geometry: unscaled cofactor vectors c[k] (k = 0..2 for nodes 1..3),
+// 1/detJ and 1/h = detJ^(-1/3). Edges are formed in double from double
+// coordinates; the cofactors and determinant in GR, then stored as R.
+template <class R, class GR, class XT = double>
+__device__ __forceinline__ void element_geometry(const XT X[4][3], R c[3][3], R& inv_det, R& rh,
+                                                 double* det_out = nullptr) {
+  GR e[3][3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) e[k][d] = (GR)(X[k + 1][d] - X[0][d]);
+  GR cc[3][3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const GR* a = e[(k + 1) % 3];
+    const GR* b = e[(k + 2) % 3];
+    cc[k][0] = a[1] * b[2] - a[2] * b[1];
+    cc[k][1] = a[2] * b[0] - a[0] * b[2];
+    cc[k][2] = a[0] * b[1] - a[1] * b[0];
+  }
+  GR det = e[0][0] * cc[0][0] + e[0][1] * cc[0][1] + e[0][2] * cc[0][2];
+  if (det_out) *det_out = (double)det;
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) c[k][d] = (R)cc[k][d];
+  inv_det = (R)MathOps<GR>::rcp(det);
+  rh = (R)MathOps<GR>::rcbrt_(det);
+}
+
+// Forward element RHS. u[a][i], p[a] nodal values; F[a][0..2] momentum,
+// F[a][3] continuity.
+template <class R, bool VREMAN>
+__device__ __forceinline__ void element_rhs(const R c[3][3], R inv_det, R rh, const R u[4][3],
+                                            const R p[4], const ElemParams<R>& P, R F[4][4]) {
+  using M = MathOps<R>;
+  // Gh = sum_k (u_k - u_0) c_k^T, gph = sum_k (p_k - p_0) c_k
+  R G[3][3], gp[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    R d1 = u[1][i] - u[0][i], d2 = u[2][i] - u[0][i], d3 = u[3][i] - u[0][i];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) G[i][j] = d1 * c[0][j] + d2 * c[1][j] + d3 * c[2][j];
+  }
+  {
+    R d1 = p[1] - p[0], d2 = p[2] - p[0], d3 = p[3] - p[0];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) gp[j] = d1 * c[0][j] + d2 * c[1][j] + d3 * c[2][j];
+  }
+  R S[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) S[i] = (u[0][i] + u[1][i]) + (u[2][i] + u[3][i]);
+  const R pbar = ((p[0] + p[1]) + (p[2] + p[3])) * (R)0.25;
+  const R trG = G[0][0] + G[1][1] + G[2][2];
+
+  R mu_eff = P.mu;
+  if (VREMAN) {
+    // alpha = G^T, beta = h^2 G G^T; B and A from Gh, rescaled by detJ and h.
+    R A = (R)0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) A += G[i][j] * G[i][j];
+    R b00 = G[0][0] * G[0][0] + G[0][1] * G[0][1] + G[0][2] * G[0][2];
+    R b11 = G[1][0] * G[1][0] + G[1][1] * G[1][1] + G[1][2] * G[1][2];
+    R b22 = G[2][0] * G[2][0] + G[2][1] * G[2][1] + G[2][2] * G[2][2];
+    R b01 = G[0][0] * G[1][0] + G[0][1] * G[1][1] + G[0][2] * G[1][2];
+    R b02 = G[0][0] * G[2][0] + G[0][1] * G[2][1] + G[0][2] * G[2][2];
+    R b12 = G[1][0] * G[2][0] + G[1][1] * G[2][1] + G[1][2] * G[2][2];
+    R B = b00 * b11 - b01 * b01 + b00 * b22 - b02 * b02 + b11 * b22 - b12 * b12;
+    if (A > (R)0 && B > (R)0) {
+      // nu_t = c h^2 sqrt(B_G/A_G) = c h^2 inv_det sqrt(B/A)
+      R h2 = M::rcp(rh * rh);
+      mu_eff = P.mu + P.rho * P.c_vreman * h2 * inv_det * M::sqrt_(B * M::rcp(A));
+    }
+  }
+  const R k1 = P.c1 * mu_eff * rh * rh;
+  const R k2 = P.c2 * P.rho * rh;
+
+  // Gauss points: u_g = QB S_u + (QA - QB) u_g-node.
+  R stau = (R)0, T[3] = {(R)0, (R)0, (R)0};
+  R Q00 = 0, Q11 = 0, Q22 = 0, Q01 = 0, Q02 = 0, Q12 = 0;
+  R bS[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) bS[i] = (R)kQB * S[i];
+#pragma unroll
+  for (int g = 0; g < 4; ++g) {
+    R ug[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) ug[i] = bS[i] + (R)(kQA - kQB) * u[g][i];
+    R s = ug[0] * ug[0] + ug[1] * ug[1] + ug[2] * ug[2];
+    R tau = M::rcp(k1 + k2 * M::sqrt_(s));
+    stau += tau;
+    R tu[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      tu[i] = tau * ug[i];
+      T[i] += tu[i];
+    }
+    Q00 += tu[0] * ug[0];
+    Q11 += tu[1] * ug[1];
+    Q22 += tu[2] * ug[2];
+    Q01 += tu[0] * ug[1];
+    Q02 += tu[0] * ug[2];
+    Q12 += tu[1] * ug[2];
+  }
+  // Qp = mu_eff I + rho^2/4 Q
+  const R r24 = P.rho * P.rho * (R)0.25;
+  const R Qp[3][3] = {{mu_eff + r24 * Q00, r24 * Q01, r24 * Q02},
+                      {r24 * Q01, mu_eff + r24 * Q11, r24 * Q12},
+                      {r24 * Q02, r24 * Q12, mu_eff + r24 * Q22}};
+  // K = pbar/6 I - inv_det/6 (Gh Qp + rho/4 gph T^T)
+  const R s6 = inv_det * (R)(1.0 / 6.0);
+  const R r4 = P.rho * (R)0.25;
+  R K[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      R w = G[i][0] * Qp[0][j] + G[i][1] * Qp[1][j] + G[i][2] * Qp[2][j] + r4 * gp[i] * T[j];
+      K[i][j] = -s6 * w;
+    }
+  const R pb6 = pbar * (R)(1.0 / 6.0);
+  K[0][0] += pb6;
+  K[1][1] += pb6;
+  K[2][2] += pb6;
+  // Rs = inv_det/24 (rho Gh T + stau gph)
+  R Rs[3];
+  const R s24 = inv_det * (R)(1.0 / 24.0);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+    Rs[i] = s24 * (P.rho * (G[i][0] * T[0] + G[i][1] * T[1] + G[i][2] * T[2]) + stau * gp[i]);
+  const R cont0 = trG * (R)(-1.0 / 24.0);
+  const R m120 = P.rho * (R)(-1.0 / 120.0);
+
+  R y0[3] = {(R)0, (R)0, (R)0};
+  R csR = (R)0;
+#pragma unroll
+  for (int a = 1; a < 4; ++a) {
+    const R* ca = c[a - 1];
+    R v[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) v[i] = m120 * (S[i] + u[a][i]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      R y = K[i][0] * ca[0] + K[i][1] * ca[1] + K[i][2] * ca[2];
+      y0[i] -= y;
+      F[a][i] = y + G[i][0] * v[0] + G[i][1] * v[1] + G[i][2] * v[2];
+    }
+    R cr = ca[0] * Rs[0] + ca[1] * Rs[1] + ca[2] * Rs[2];
+    csR += cr;
+    F[a][3] = cont0 - cr;
+  }
+  {
+    R v[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) v[i] = m120 * (S[i] + u[0][i]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) F[0][i] = y0[i] + G[i][0] * v[0] + G[i][1] * v[1] + G[i][2] * v[2];
+    F[0][3] = cont0 + csR;
+  }
+}
+
+// Reverse sweep: given w[a][0..3] (cotangent of F[a][0..3]), returns
+// gu[a][i] = sum_{b,k} w[b][k] dF[b][k]/du[a][i] and gp_out[a] likewise for p.
+template <class R, bool VREMAN>
+__device__ __forceinline__ void element_vjp(const R c[3][3], R inv_det, R rh, const R u[4][3],
+                                            const R p[4], const R w[4][4], const ElemParams<R>& P,
+                                            R gu[4][3], R gpo[4]) {
+  using M = MathOps<R>;
+  // ---- forward recompute ----
+  R G[3][3], gp[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    R d1 = u[1][i] - u[0][i], d2 = u[2][i] - u[0][i], d3 = u[3][i] - u[0][i];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) G[i][j] = d1 * c[0][j] + d2 * c[1][j] + d3 * c[2][j];
+  }
+  {
+    R d1 = p[1] - p[0], d2 = p[2] - p[0], d3 = p[3] - p[0];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) gp[j] = d1 * c[0][j] + d2 * c[1][j] + d3 * c[2][j];
+  }
+  R S[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) S[i] = (u[0][i] + u[1][i]) + (u[2][i] + u[3][i]);
+
+  R mu_eff = P.mu;
+  R vA = (R)0, vB = (R)0, vphi = (R)0, vscale = (R)0;  // Vreman intermediates
+  R b00 = (R)0, b11 = (R)0, b22 = (R)0, b01 = (R)0, b02 = (R)0, b12 = (R)0;
+  bool vactive = false;
+  if (VREMAN) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) vA += G[i][j] * G[i][j];
+    b00 = G[0][0] * G[0][0] + G[0][1] * G[0][1] + G[0][2] * G[0][2];
+    b11 = G[1][0] * G[1][0] + G[1][1] * G[1][1] + G[1][2] * G[1][2];
+    b22 = G[2][0] * G[2][0] + G[2][1] * G[2][1] + G[2][2] * G[2][2];
+    b01 = G[0][0] * G[1][0] + G[0][1] * G[1][1] + G[0][2] * G[1][2];
+    b02 = G[0][0] * G[2][0] + G[0][1] * G[2][1] + G[0][2] * G[2][2];
+    b12 = G[1][0] * G[2][0] + G[1][1] * G[2][1] + G[1][2] * G[2][2];
+    vB = b00 * b11 - b01 * b01 + b00 * b22 - b02 * b02 + b11 * b22 - b12 * b12;
+    if (vA > (R)0 && vB > (R)0) {
+      vactive = true;
+      R h2 = M::rcp(rh * rh);
+      vscale = P.rho * P.c_vreman * h2 * inv_det;
+      vphi = M::sqrt_(vB * M::rcp(vA));
+      mu_eff = P.mu + vscale * vphi;
+    }
+  }
+  const R k1 = P.c1 * mu_eff * rh * rh;
+  const R k2 = P.c2 * P.rho * rh;
+  R bS[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) bS[i] = (R)kQB * S[i];
+  R tau[4], nrm[4];
+  R stau = (R)0, T[3] = {(R)0, (R)0, (R)0};
+  R Q00 = (R)0, Q11 = (R)0, Q22 = (R)0, Q01 = (R)0, Q02 = (R)0, Q12 = (R)0;
+#pragma unroll
+  for (int g = 0; g < 4; ++g) {
+    R ug[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) ug[i] = bS[i] + (R)(kQA - kQB) * u[g][i];
+    R s = ug[0] * ug[0] + ug[1] * ug[1] + ug[2] * ug[2];
+    nrm[g] = M::sqrt_(s);
+    tau[g] = M::rcp(k1 + k2 * nrm[g]);
+    stau += tau[g];
+    R tu[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      tu[i] = tau[g] * ug[i];
+      T[i] += tu[i];
+    }
+    Q00 += tu[0] * ug[0];
+    Q11 += tu[1] * ug[1];
+    Q22 += tu[2] * ug[2];
+    Q01 += tu[0] * ug[1];
+    Q02 += tu[0] * ug[2];
+    Q12 += tu[1] * ug[2];
+  }
+  const R Qm[3][3] = {{Q00, Q01, Q02}, {Q01, Q11, Q12}, {Q02, Q12, Q22}};
+
+  // ---- reverse ----
+  const R r24 = P.rho * P.rho * (R)0.25;
+  const R r4 = P.rho * (R)0.25;
+  // Omega = sum_a wm_a c_a^T = sum_k (wm_k - wm_0) c_k^T ; cw = sum_a wc_a c_a
+  R Om[3][3], cw[3];
+  {
+    R dw[3][4];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) dw[k][q] = w[k + 1][q] - w[0][q];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) Om[i][j] = dw[0][i] * c[0][j] + dw[1][i] * c[1][j] + dw[2][i] * c[2][j];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) cw[j] = dw[0][3] * c[0][j] + dw[1][3] * c[1][j] + dw[2][3] * c[2][j];
+  }
+  const R wcs = (w[0][3] + w[1][3]) + (w[2][3] + w[3][3]);
+  // Rbar = -(inv_det/24) cw ; pbarbar = tr(Omega)/6 ; Wbar = -(inv_det/6) Omega
+  const R s24 = inv_det * (R)(1.0 / 24.0);
+  const R s6 = inv_det * (R)(1.0 / 6.0);
+  R Rb[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) Rb[j] = -s24 * cw[j];
+  const R pbb = (Om[0][0] + Om[1][1] + Om[2][2]) * (R)(1.0 / 6.0);
+  R Wb[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) Wb[i][j] = -s6 * Om[i][j];
+  // mu_eff-bar = <Wb, G>
+  R mub = (R)0;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) mub += Wb[i][j] * G[i][j];
+  // Qbar = r24 G^T Wb ; symmetrised Qs = Qbar + Qbar^T
+  R Qs[3][3];
+  {
+    R Qb[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        Qb[i][j] = r24 * (G[0][i] * Wb[0][j] + G[1][i] * Wb[1][j] + G[2][i] * Wb[2][j]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) Qs[i][j] = Qb[i][j] + Qb[j][i];
+  }
+  // Tbar = r4 Wb^T gp + rho G^T Rb ; staubar = Rb.gp ; gpbar = r4 Wb T + stau Rb
+  R Tb[3], gpb[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    Tb[j] = r4 * (Wb[0][j] * gp[0] + Wb[1][j] * gp[1] + Wb[2][j] * gp[2]) +
+            P.rho * (G[0][j] * Rb[0] + G[1][j] * Rb[1] + G[2][j] * Rb[2]);
+  }
+  const R staub = Rb[0] * gp[0] + Rb[1] * gp[1] + Rb[2] * gp[2];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+    gpb[i] = r4 * (Wb[i][0] * T[0] + Wb[i][1] * T[1] + Wb[i][2] * T[2]) + stau * Rb[i];
+  // Gbar = mu_eff Wb + r24 Wb Q + rho Rb T^T - (rho/120) sum_a wm_a (S + u_a)^T - wcs/24 I
+  R Gb[3][3];
+  const R m120 = P.rho * (R)(-1.0 / 120.0);
+  R wms[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) wms[i] = (w[0][i] + w[1][i]) + (w[2][i] + w[3][i]);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      R wu = w[0][i] * u[0][j] + w[1][i] * u[1][j] + w[2][i] * u[2][j] + w[3][i] * u[3][j];
+      Gb[i][j] = mu_eff * Wb[i][j] +
+                 r24 * (Wb[i][0] * Qm[0][j] + Wb[i][1] * Qm[1][j] + Wb[i][2] * Qm[2][j]) +
+                 P.rho * Rb[i] * T[j] + m120 * (wms[i] * S[j] + wu);
+    }
+  const R wc24 = wcs * (R)(1.0 / 24.0);
+  Gb[0][0] -= wc24;
+  Gb[1][1] -= wc24;
+  Gb[2][2] -= wc24;
+  // Sbar = (rho/-120) G^T wms ; ubar_a = (rho/-120) G^T wm_a
+  R Sb[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) Sb[j] = m120 * (G[0][j] * wms[0] + G[1][j] * wms[1] + G[2][j] * wms[2]);
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      gu[a][j] = m120 * (G[0][j] * w[a][0] + G[1][j] * w[a][1] + G[2][j] * w[a][2]);
+  // Gauss points in reverse
+  const R crh2 = P.c1 * rh * rh;
+#pragma unroll
+  for (int g = 0; g < 4; ++g) {
+    R ug[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) ug[i] = bS[i] + (R)(kQA - kQB) * u[g][i];
+    R Qu[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) Qu[i] = Qs[i][0] * ug[0] + Qs[i][1] * ug[1] + Qs[i][2] * ug[2];
+    // tau-bar: Q enters as ug^T Qbar ug = ug . (Qs ug)/2
+    R taub = staub + Tb[0] * ug[0] + Tb[1] * ug[1] + Tb[2] * ug[2] +
+                  (R)0.5 * (ug[0] * Qu[0] + ug[1] * Qu[1] + ug[2] * Qu[2]);
+    R db = -tau[g] * tau[g] * taub;
+    mub += crh2 * db;
+    R nb = k2 * db;
+    R sc = nrm[g] > (R)0 ? nb * M::rcp(nrm[g]) : (R)0;
+    R ugb[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) ugb[i] = tau[g] * (Tb[i] + Qu[i]) + sc * ug[i];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      Sb[i] += (R)kQB * ugb[i];
+      gu[g][i] += (R)(kQA - kQB) * ugb[i];
+    }
+  }
+  // Vreman: mu_eff = mu + vscale sqrt(B/A)
+  if (VREMAN && vactive) {
+    // d phi / d Gh = (P - phi^2 I) Gh / (phi A), P = tr(beta) I - beta
+    R f = mub * vscale * M::rcp(vphi * vA);
+    R tb = b00 + b11 + b22;
+    R phi2 = vphi * vphi;
+    const R Pm[3][3] = {{tb - b00 - phi2, -b01, -b02},
+                             {-b01, tb - b11 - phi2, -b12},
+                             {-b02, -b12, tb - b22 - phi2}};
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        Gb[i][j] += f * (Pm[i][0] * G[0][j] + Pm[i][1] * G[1][j] + Pm[i][2] * G[2][j]);
+  }
+  // Gh = sum_a u_a c_a^T ; gph = sum_a p_a c_a ; S = sum u_a ; pbar = sum p_a / 4
+  R gpc[3], gus[3] = {(R)0, (R)0, (R)0};
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    R pc = gpb[0] * c[k][0] + gpb[1] * c[k][1] + gpb[2] * c[k][2];
+    gpc[k] = pc;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      R gc = Gb[i][0] * c[k][0] + Gb[i][1] * c[k][1] + Gb[i][2] * c[k][2];
+      gu[k + 1][i] += gc + Sb[i];
+      gus[i] += gc;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) gu[0][i] += Sb[i] - gus[i];
+  const R pq = pbb * (R)0.25;
+  gpo[1] = gpc[0] + pq;
+  gpo[2] = gpc[1] + pq;
+  gpo[3] = gpc[2] + pq;
+  gpo[0] = pq - (gpc[0] + gpc[1] + gpc[2]);
+}
+
+}  // namespace nsrhs

@@ -1,0 +1,539 @@
+// nsrhs: C-ABI library for the element-by-element Navier-Stokes RHS assembly
+// on linear tetrahedra (arXiv 2403.08777, Sec. II and V), GB300 / sm_103a.
+//
+// Host side: mesh objects (device copies of coordinates and connectivity,
+// validation, aspect-ratio classification), argument checking and kernel
+// launches. Device side: the element kernels (element.cuh holds the
+// per-element arithmetic). One thread assembles one element, with every
+// intermediate in registers (the paper's specialisation + privatisation,
+// Sec. V-B/V-C), and scatters its 16 entries as soon as they are computed
+// (immediate scatter, Sec. V-D) with double-precision atomic adds, which
+// resolve the write conflicts that the paper's CPU path avoids with a
+// separate serial scatter loop (Sec. V-C).
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <unordered_set>
+#include <vector>
+
+#include "../../include/nsrhs.h"
+#include "element.cuh"
+
+struct nsrhs_mesh {
+  int64_t n_nodes = 0, n_elems = 0;
+  int device = 0;
+  double* coords = nullptr;   // [3][N]
+  int32_t* conn = nullptr;    // [4][E], caller's element order
+  // Mixed form: elements split by aspect ratio, each list with its own
+  // contiguous connectivity so that a warp never mixes the two kinds.
+  int32_t* conn_lo = nullptr;  // [4][E_lo], AR <= threshold
+  int32_t* conn_hi = nullptr;  // [4][E_hi], AR > threshold
+  int64_t n_lo = 0, n_hi = 0;
+  nsrhs_mesh_info info{};
+  std::vector<void*> allocations;
+};
+
+namespace {
+
+using nsrhs::ElemParams;
+
+std::mutex g_registry_mutex;
+std::unordered_set<const nsrhs_mesh*> g_registry;
+
+bool is_live(const nsrhs_mesh* m) {
+  std::lock_guard<std::mutex> lock(g_registry_mutex);
+  return m != nullptr && g_registry.count(m) != 0;
+}
+
+constexpr int kThreads = 128;
+
+int sm_count(int device) {
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || n <= 0)
+    n = 152;
+  return n;
+}
+
+// Grid for a grid-stride loop over n items: a whole number of waves of
+// `per_sm` blocks on every SM, no more blocks than items need.
+unsigned grid_for(int64_t n, int device, int per_sm) {
+  int64_t need = (n + kThreads - 1) / kThreads;
+  int64_t cap = (int64_t)sm_count(device) * per_sm;
+  return (unsigned)std::max<int64_t>(1, std::min(need, cap));
+}
+
+// ---------------------------------------------------------------------------
+// Mesh validation and classification (setup).
+
+struct ValidateOut {
+  unsigned long long bad_index;
+  unsigned long long bad_det;
+  unsigned long long n_high_ar;
+  unsigned long long min_det_bits;  // positive doubles order like their bit patterns
+  unsigned long long max_ar_bits;
+};
+
+__global__ void validate_kernel(int64_t N, int64_t E, const double* __restrict__ coords,
+                                const int32_t* __restrict__ conn, double ar_threshold,
+                                uint8_t* __restrict__ high_ar, ValidateOut* out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int32_t v[4];
+    bool ok = true;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      v[a] = conn[a * E + e];
+      ok = ok && v[a] >= 0 && (int64_t)v[a] < N;
+    }
+    high_ar[e] = 0;
+    if (!ok) {
+      atomicAdd(&out->bad_index, 1ull);
+      continue;
+    }
+    double X[4][3];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int d = 0; d < 3; ++d) X[a][d] = coords[d * N + v[a]];
+    double ed[3][3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int d = 0; d < 3; ++d) ed[k][d] = X[k + 1][d] - X[0][d];
+    double det = ed[0][0] * (ed[1][1] * ed[2][2] - ed[1][2] * ed[2][1]) -
+                 ed[0][1] * (ed[1][0] * ed[2][2] - ed[1][2] * ed[2][0]) +
+                 ed[0][2] * (ed[1][0] * ed[2][1] - ed[1][1] * ed[2][0]);
+    if (!(det > 0.0)) {
+      atomicAdd(&out->bad_det, 1ull);
+      continue;
+    }
+    // aspect ratio l_max * S / (6 sqrt(6) V), V = det / 6
+    double lmax2 = 0.0;
+    for (int a = 0; a < 4; ++a)
+      for (int b = a + 1; b < 4; ++b) {
+        double dx = X[b][0] - X[a][0], dy = X[b][1] - X[a][1], dz = X[b][2] - X[a][2];
+        lmax2 = fmax(lmax2, dx * dx + dy * dy + dz * dz);
+      }
+    double S = 0.0;
+    const int fc[4][3] = {{1, 2, 3}, {0, 2, 3}, {0, 1, 3}, {0, 1, 2}};
+    for (int f = 0; f < 4; ++f) {
+      const double* A = X[fc[f][0]];
+      const double* B = X[fc[f][1]];
+      const double* C = X[fc[f][2]];
+      double ab[3] = {B[0] - A[0], B[1] - A[1], B[2] - A[2]};
+      double ac[3] = {C[0] - A[0], C[1] - A[1], C[2] - A[2]};
+      double cx = ab[1] * ac[2] - ab[2] * ac[1];
+      double cy = ab[2] * ac[0] - ab[0] * ac[2];
+      double cz = ab[0] * ac[1] - ab[1] * ac[0];
+      S += 0.5 * sqrt(cx * cx + cy * cy + cz * cz);
+    }
+    double ar = sqrt(lmax2) * S / (sqrt(6.0) * det);
+    if (ar > ar_threshold) {
+      high_ar[e] = 1;
+      atomicAdd(&out->n_high_ar, 1ull);
+    }
+    atomicMin(&out->min_det_bits, (unsigned long long)__double_as_longlong(det));
+    atomicMax(&out->max_ar_bits, (unsigned long long)__double_as_longlong(ar));
+  }
+}
+
+// conn_sub[a][i] = conn[a][idx[i]]
+__global__ void gather_conn_kernel(int64_t E, const int32_t* __restrict__ conn, int64_t n,
+                                   const int32_t* __restrict__ idx, int32_t* __restrict__ sub) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t e = idx[i];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) sub[a * n + i] = conn[a * E + e];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Assembly kernels.
+
+template <class T>
+__device__ __forceinline__ T ldg(const T* p) {
+  return __ldg(p);
+}
+
+// FP64 forward, one element per thread, immediate atomic scatter.
+template <bool VREMAN>
+__global__ void __launch_bounds__(kThreads)
+    fwd_fp64_atomic_kernel(int64_t N, int64_t E, const int32_t* __restrict__ conn,
+                           const double* __restrict__ coords, const double* __restrict__ up,
+                           ElemParams<double> P, double* __restrict__ rhs) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int32_t v[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) v[a] = ldg(conn + a * E + e);
+    double X[4][3], u[4][3], p[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) X[a][d] = ldg(coords + d * N + v[a]);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) u[a][i] = ldg(up + i * N + v[a]);
+      p[a] = ldg(up + 3 * N + v[a]);
+    }
+    double c[3][3], inv_det, rh;
+    nsrhs::element_geometry<double, double>(X, c, inv_det, rh);
+    double F[4][4];
+    nsrhs::element_rhs<double, VREMAN>(c, inv_det, rh, u, p, P, F);
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) atomicAdd(rhs + k * N + v[a], F[a][k]);
+  }
+}
+
+// Mixed form: float (u,p) and float element arithmetic; edges from double
+// coordinates in double; det/inverse in GR (double for high-aspect-ratio
+// elements, float otherwise); double global accumulation.
+template <class GR, bool VREMAN>
+__global__ void __launch_bounds__(kThreads)
+    fwd_mixed_atomic_kernel(int64_t N, int64_t E, const int32_t* __restrict__ conn,
+                            const double* __restrict__ coords, const float* __restrict__ up,
+                            ElemParams<float> P, double* __restrict__ rhs) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int32_t v[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) v[a] = ldg(conn + a * E + e);
+    double X[4][3];
+    float u[4][3], p[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) X[a][d] = ldg(coords + d * N + v[a]);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) u[a][i] = ldg(up + i * N + v[a]);
+      p[a] = ldg(up + 3 * N + v[a]);
+    }
+    float c[3][3], inv_det, rh;
+    nsrhs::element_geometry<float, GR>(X, c, inv_det, rh);
+    float F[4][4];
+    nsrhs::element_rhs<float, VREMAN>(c, inv_det, rh, u, p, P, F);
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) atomicAdd(rhs + k * N + v[a], (double)F[a][k]);
+  }
+}
+
+// FP64 vector-Jacobian product: gather the cotangent at the element's nodes
+// (the reverse of the scatter), recompute the element, run the reverse sweep,
+// scatter-add the gradient (the reverse of the gather).
+template <bool VREMAN>
+__global__ void __launch_bounds__(kThreads)
+    vjp_fp64_atomic_kernel(int64_t N, int64_t E, const int32_t* __restrict__ conn,
+                           const double* __restrict__ coords, const double* __restrict__ up,
+                           const double* __restrict__ cot, ElemParams<double> P,
+                           double* __restrict__ grad) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int32_t v[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) v[a] = ldg(conn + a * E + e);
+    double X[4][3], u[4][3], p[4], w[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) X[a][d] = ldg(coords + d * N + v[a]);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) u[a][i] = ldg(up + i * N + v[a]);
+      p[a] = ldg(up + 3 * N + v[a]);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) w[a][k] = ldg(cot + k * N + v[a]);
+    }
+    double c[3][3], inv_det, rh;
+    nsrhs::element_geometry<double, double>(X, c, inv_det, rh);
+    double gu[4][3], gp[4];
+    nsrhs::element_vjp<double, VREMAN>(c, inv_det, rh, u, p, w, P, gu, gp);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) atomicAdd(grad + i * N + v[a], gu[a][i]);
+      atomicAdd(grad + 3 * N + v[a], gp[a]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+
+nsrhs_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return NSRHS_OK;
+  if (e == cudaErrorMemoryAllocation) return NSRHS_ENOMEM;
+  return NSRHS_ECUDA;
+}
+
+#define NSRHS_TRY(expr)                              \
+  do {                                               \
+    nsrhs_status _s = cuda_status(expr);             \
+    if (_s != NSRHS_OK) return _s;                   \
+  } while (0)
+
+nsrhs_status check_params(const nsrhs_params* p) {
+  if (!p) return NSRHS_EINVAL;
+  if (!(p->rho >= 0.0) || !(p->mu > 0.0) || !(p->c_vreman >= 0.0) || !(p->c1 > 0.0) ||
+      !(p->c2 >= 0.0) || !std::isfinite(p->rho) || !std::isfinite(p->mu) ||
+      !std::isfinite(p->c_vreman) || !std::isfinite(p->c1) || !std::isfinite(p->c2))
+    return NSRHS_EINVAL;
+  if (p->precision != NSRHS_FP64 && p->precision != NSRHS_MIXED) return NSRHS_EINVAL;
+  if (p->scatter < NSRHS_SCATTER_AUTO || p->scatter > NSRHS_SCATTER_BLOCK) return NSRHS_EINVAL;
+  return NSRHS_OK;
+}
+
+template <class R>
+ElemParams<R> elem_params(const nsrhs_params* p) {
+  return ElemParams<R>{(R)p->rho, (R)p->mu, (R)p->c_vreman, (R)p->c1, (R)p->c2};
+}
+
+void free_mesh(nsrhs_mesh* m) {
+  if (!m) return;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(m->device);
+  for (void* ptr : m->allocations) cudaFree(ptr);
+  cudaSetDevice(prev);
+  delete m;
+}
+
+template <class T>
+nsrhs_status mesh_alloc(nsrhs_mesh* m, T** ptr, size_t count) {
+  *ptr = nullptr;
+  if (count == 0) return NSRHS_OK;
+  cudaError_t e = cudaMalloc((void**)ptr, count * sizeof(T));
+  if (e != cudaSuccess) {
+    *ptr = nullptr;
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? NSRHS_ENOMEM : NSRHS_ECUDA;
+  }
+  m->allocations.push_back(*ptr);
+  m->info.device_bytes += (int64_t)(count * sizeof(T));
+  return NSRHS_OK;
+}
+
+nsrhs_status mesh_build(nsrhs_mesh* m, const double* coords, const int32_t* conn,
+                        const nsrhs_mesh_opts& opts, cudaStream_t s) {
+  const int64_t N = m->n_nodes, E = m->n_elems;
+  nsrhs_status st;
+  if ((st = mesh_alloc(m, &m->coords, 3 * (size_t)N)) != NSRHS_OK) return st;
+  if ((st = mesh_alloc(m, &m->conn, 4 * (size_t)E)) != NSRHS_OK) return st;
+  NSRHS_TRY(cudaMemcpyAsync(m->coords, coords, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, s));
+  NSRHS_TRY(cudaMemcpyAsync(m->conn, conn, sizeof(int32_t) * 4 * E, cudaMemcpyDeviceToDevice, s));
+
+  // Validation scratch (freed before returning).
+  uint8_t* high_ar = nullptr;
+  ValidateOut* vout = nullptr;
+  NSRHS_TRY(cudaMalloc((void**)&high_ar, (size_t)E));
+  cudaError_t ce = cudaMalloc((void**)&vout, sizeof(ValidateOut));
+  if (ce != cudaSuccess) {
+    cudaFree(high_ar);
+    return cuda_status(ce);
+  }
+  ValidateOut init{};
+  init.min_det_bits = (unsigned long long)0x7FF0000000000000ull;  // +inf
+  init.max_ar_bits = 0ull;
+  ValidateOut res{};
+  std::vector<uint8_t> flags;
+  ce = cudaMemcpyAsync(vout, &init, sizeof(init), cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess) {
+    validate_kernel<<<grid_for(E, m->device, 8), kThreads, 0, s>>>(N, E, m->coords, m->conn,
+                                                                  opts.ar_threshold, high_ar, vout);
+    ce = cudaGetLastError();
+  }
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(&res, vout, sizeof(res), cudaMemcpyDeviceToHost, s);
+  if (ce == cudaSuccess) {
+    flags.resize((size_t)E);
+    ce = cudaMemcpyAsync(flags.data(), high_ar, (size_t)E, cudaMemcpyDeviceToHost, s);
+  }
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+  cudaFree(high_ar);
+  cudaFree(vout);
+  if (ce != cudaSuccess) return cuda_status(ce);
+  if (res.bad_index != 0 || res.bad_det != 0) return NSRHS_EMESH;
+
+  double min_det, max_ar;
+  std::memcpy(&min_det, &res.min_det_bits, sizeof(double));
+  std::memcpy(&max_ar, &res.max_ar_bits, sizeof(double));
+  m->info.min_detj = min_det;
+  m->info.max_ar = max_ar;
+  m->info.n_high_ar = (int64_t)res.n_high_ar;
+
+  // Aspect-ratio lists for the mixed form (element order kept within each).
+  std::vector<int32_t> lo, hi;
+  lo.reserve((size_t)E);
+  for (int64_t e = 0; e < E; ++e) (flags[e] ? hi : lo).push_back((int32_t)e);
+  m->n_lo = (int64_t)lo.size();
+  m->n_hi = (int64_t)hi.size();
+  for (int pass = 0; pass < 2; ++pass) {
+    std::vector<int32_t>& idx = pass == 0 ? lo : hi;
+    int32_t** dst = pass == 0 ? &m->conn_lo : &m->conn_hi;
+    if (idx.empty()) continue;
+    if ((st = mesh_alloc(m, dst, 4 * idx.size())) != NSRHS_OK) return st;
+    int32_t* didx = nullptr;
+    NSRHS_TRY(cudaMalloc((void**)&didx, idx.size() * sizeof(int32_t)));
+    ce = cudaMemcpyAsync(didx, idx.data(), idx.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+    if (ce == cudaSuccess) {
+      gather_conn_kernel<<<grid_for((int64_t)idx.size(), m->device, 8), kThreads, 0, s>>>(
+          E, m->conn, (int64_t)idx.size(), didx, *dst);
+      ce = cudaGetLastError();
+    }
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    cudaFree(didx);
+    if (ce != cudaSuccess) return cuda_status(ce);
+  }
+  m->info.n_nodes = N;
+  m->info.n_elems = E;
+  m->info.n_blocks = 0;
+  m->info.block_elems = 0;
+  return NSRHS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void nsrhs_params_default(nsrhs_params* p) {
+  if (!p) return;
+  p->rho = 1.0;
+  p->mu = 1e-2;
+  p->c_vreman = 0.0;
+  p->c1 = 4.0;
+  p->c2 = 2.0;
+  p->precision = NSRHS_FP64;
+  p->scatter = NSRHS_SCATTER_AUTO;
+}
+
+void nsrhs_mesh_opts_default(nsrhs_mesh_opts* o) {
+  if (!o) return;
+  o->ar_threshold = 10.0;
+}
+
+const char* nsrhs_status_string(nsrhs_status s) {
+  switch (s) {
+    case NSRHS_OK: return "ok";
+    case NSRHS_EINVAL: return "invalid argument";
+    case NSRHS_ENOMEM: return "device out of memory";
+    case NSRHS_EMESH: return "invalid mesh (index out of range or detJ <= 0)";
+    case NSRHS_ECUDA: return "CUDA error";
+    case NSRHS_EUNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+nsrhs_status nsrhs_mesh_create(int64_t n_nodes, int64_t n_elems, const double* coords,
+                               const int32_t* conn, const nsrhs_mesh_opts* opts, void* stream,
+                               nsrhs_mesh** out) {
+  if (!out) return NSRHS_EINVAL;
+  *out = nullptr;
+  if (!coords || !conn) return NSRHS_EINVAL;
+  if (n_nodes < 1 || n_elems < 1 || n_nodes > INT32_MAX || n_elems > INT32_MAX) return NSRHS_EINVAL;
+  nsrhs_mesh_opts o;
+  nsrhs_mesh_opts_default(&o);
+  if (opts) o = *opts;
+  if (!(o.ar_threshold > 0.0)) return NSRHS_EINVAL;
+  nsrhs_mesh* m = new (std::nothrow) nsrhs_mesh();
+  if (!m) return NSRHS_ENOMEM;
+  if (cudaGetDevice(&m->device) != cudaSuccess) {
+    delete m;
+    return NSRHS_ECUDA;
+  }
+  m->n_nodes = n_nodes;
+  m->n_elems = n_elems;
+  nsrhs_status st = mesh_build(m, coords, conn, o, (cudaStream_t)stream);
+  if (st != NSRHS_OK) {
+    free_mesh(m);
+    return st;
+  }
+  {
+    std::lock_guard<std::mutex> lock(g_registry_mutex);
+    g_registry.insert(m);
+  }
+  *out = m;
+  return NSRHS_OK;
+}
+
+nsrhs_status nsrhs_mesh_get_info(const nsrhs_mesh* m, nsrhs_mesh_info* info) {
+  if (!is_live(m) || !info) return NSRHS_EINVAL;
+  *info = m->info;
+  return NSRHS_OK;
+}
+
+nsrhs_status nsrhs_assemble(const nsrhs_mesh* m, const nsrhs_params* p, const void* up,
+                            double* rhs, void* stream) {
+  if (!is_live(m) || !up || !rhs) return NSRHS_EINVAL;
+  nsrhs_status st = check_params(p);
+  if (st != NSRHS_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t N = m->n_nodes, E = m->n_elems;
+  const bool vreman = p->c_vreman != 0.0;
+  NSRHS_TRY(cudaMemsetAsync(rhs, 0, sizeof(double) * 4 * N, s));
+  if (p->precision == NSRHS_FP64) {
+    auto P = elem_params<double>(p);
+    const double* u = (const double*)up;
+    unsigned grid = grid_for(E, m->device, 16);
+    if (vreman)
+      fwd_fp64_atomic_kernel<true><<<grid, kThreads, 0, s>>>(N, E, m->conn, m->coords, u, P, rhs);
+    else
+      fwd_fp64_atomic_kernel<false><<<grid, kThreads, 0, s>>>(N, E, m->conn, m->coords, u, P, rhs);
+  } else {
+    auto P = elem_params<float>(p);
+    const float* u = (const float*)up;
+    if (m->n_lo > 0) {
+      unsigned grid = grid_for(m->n_lo, m->device, 16);
+      if (vreman)
+        fwd_mixed_atomic_kernel<float, true>
+            <<<grid, kThreads, 0, s>>>(N, m->n_lo, m->conn_lo, m->coords, u, P, rhs);
+      else
+        fwd_mixed_atomic_kernel<float, false>
+            <<<grid, kThreads, 0, s>>>(N, m->n_lo, m->conn_lo, m->coords, u, P, rhs);
+    }
+    if (m->n_hi > 0) {
+      unsigned grid = grid_for(m->n_hi, m->device, 16);
+      if (vreman)
+        fwd_mixed_atomic_kernel<double, true>
+            <<<grid, kThreads, 0, s>>>(N, m->n_hi, m->conn_hi, m->coords, u, P, rhs);
+      else
+        fwd_mixed_atomic_kernel<double, false>
+            <<<grid, kThreads, 0, s>>>(N, m->n_hi, m->conn_hi, m->coords, u, P, rhs);
+    }
+  }
+  return cuda_status(cudaGetLastError());
+}
+
+nsrhs_status nsrhs_assemble_vjp(const nsrhs_mesh* m, const nsrhs_params* p, const double* up,
+                                const double* cot, double* grad, void* stream) {
+  if (!is_live(m) || !up || !cot || !grad) return NSRHS_EINVAL;
+  nsrhs_status st = check_params(p);
+  if (st != NSRHS_OK) return st;
+  if (p->precision != NSRHS_FP64) return NSRHS_EUNSUPPORTED;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t N = m->n_nodes, E = m->n_elems;
+  NSRHS_TRY(cudaMemsetAsync(grad, 0, sizeof(double) * 4 * N, s));
+  auto P = elem_params<double>(p);
+  unsigned grid = grid_for(E, m->device, 16);
+  if (p->c_vreman != 0.0)
+    vjp_fp64_atomic_kernel<true><<<grid, kThreads, 0, s>>>(N, E, m->conn, m->coords, up, cot, P, grad);
+  else
+    vjp_fp64_atomic_kernel<false><<<grid, kThreads, 0, s>>>(N, E, m->conn, m->coords, up, cot, P, grad);
+  return cuda_status(cudaGetLastError());
+}
+
+void nsrhs_destroy(nsrhs_mesh* m) {
+  if (!m) return;
+  {
+    std::lock_guard<std::mutex> lock(g_registry_mutex);
+    if (g_registry.erase(m) == 0) return;  // not a live mesh: ignore
+  }
+  free_mesh(m);
+}
+
+}  // extern "C"

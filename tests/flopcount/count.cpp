@@ -1,0 +1,79 @@
+// Flop census of the element kernels: instantiate the device arithmetic with a
+// scalar that counts every operation whose operands are not both uniform
+// (uniform = derived only from the launch parameters and literals, i.e. work
+// the compiler hoists out of the element loop).
+// Convention: add/sub/mul = 1, fused multiply-add = 2 (it appears here as a
+// mul and an add), reciprocal / sqrt / reciprocal cube root = 1 each.
+#include <cstdio>
+
+struct Cnt {
+  double v = 0.0;
+  bool uni = true;
+  Cnt() = default;
+  Cnt(double x) : v(x), uni(true) {}
+  Cnt(double x, bool u) : v(x), uni(u) {}
+  explicit operator double() const { return v; }
+};
+static long g_add = 0, g_mul = 0, g_sfu = 0;
+inline Cnt op(double r, const Cnt& a, const Cnt& b, long& c) {
+  bool u = a.uni && b.uni;
+  if (!u) ++c;
+  return Cnt(r, u);
+}
+inline Cnt operator+(const Cnt& a, const Cnt& b) { return op(a.v + b.v, a, b, g_add); }
+inline Cnt operator-(const Cnt& a, const Cnt& b) { return op(a.v - b.v, a, b, g_add); }
+inline Cnt operator*(const Cnt& a, const Cnt& b) { return op(a.v * b.v, a, b, g_mul); }
+inline Cnt operator-(const Cnt& a) { return Cnt(-a.v, a.uni); }  // folds into its consumer
+inline Cnt& operator+=(Cnt& a, const Cnt& b) { return a = a + b; }
+inline Cnt& operator-=(Cnt& a, const Cnt& b) { return a = a - b; }
+inline bool operator>(const Cnt& a, const Cnt& b) { return a.v > b.v; }
+
+#include "../../paper_2403_08777_gb300/csrc/element.cuh"
+
+namespace nsrhs {
+template <>
+struct MathOps<Cnt> {
+  static Cnt sfu(double r, const Cnt& a) {
+    if (!a.uni) ++g_sfu;
+    return Cnt(r, a.uni);
+  }
+  static Cnt rcp(const Cnt& x) { return sfu(1.0 / x.v, x); }
+  static Cnt sqrt_(const Cnt& x) { return sfu(std::sqrt(x.v), x); }
+  static Cnt rcbrt_(const Cnt& x) { return sfu(1.0 / std::cbrt(x.v), x); }
+};
+}  // namespace nsrhs
+
+using namespace nsrhs;
+
+static void reset() { g_add = g_mul = g_sfu = 0; }
+static long total() { return g_add + g_mul + g_sfu; }
+
+int main() {
+  // A generic element; the values only steer the Vreman branch (taken).
+  const double Xd[4][3] = {{0.1, 0.0, 0.05}, {1.0, 0.1, 0.0}, {0.0, 1.1, 0.2}, {0.1, 0.2, 0.9}};
+  Cnt X[4][3], u[4][3], p[4], w[4][4];
+  for (int a = 0; a < 4; ++a) {
+    for (int d = 0; d < 3; ++d) X[a][d] = Cnt(Xd[a][d], false);
+    for (int i = 0; i < 3; ++i) u[a][i] = Cnt(0.3 * a - 0.2 * i + 0.1 * a * i + 0.05, false);
+    p[a] = Cnt(0.7 - 0.3 * a, false);
+    for (int k = 0; k < 4; ++k) w[a][k] = Cnt(0.2 * a + 0.1 * k - 0.3, false);
+  }
+  ElemParams<Cnt> P{Cnt(1.0), Cnt(1e-3), Cnt(0.07), Cnt(4.0), Cnt(2.0)};
+  for (int vreman = 0; vreman < 2; ++vreman) {
+    Cnt c[3][3], inv_det, rh, F[4][4], gu[4][3], gp[4];
+    reset();
+    element_geometry<Cnt, Cnt, Cnt>(X, c, inv_det, rh);
+    long geo = total(), geo_sfu = g_sfu;
+    reset();
+    if (vreman) element_rhs<Cnt, true>(c, inv_det, rh, u, p, P, F);
+    else element_rhs<Cnt, false>(c, inv_det, rh, u, p, P, F);
+    long fwd = total() + geo, fwd_sfu = g_sfu + geo_sfu;
+    reset();
+    if (vreman) element_vjp<Cnt, true>(c, inv_det, rh, u, p, w, P, gu, gp);
+    else element_vjp<Cnt, false>(c, inv_det, rh, u, p, w, P, gu, gp);
+    long vjp = total() + geo, vjp_sfu = g_sfu + geo_sfu;
+    std::printf("%s fwd %ld sfu %ld vjp %ld sfu %ld\n", vreman ? "vreman" : "plain", fwd, fwd_sfu,
+                vjp, vjp_sfu);
+  }
+  return 0;
+}

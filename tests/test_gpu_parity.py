@@ -1,0 +1,226 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Tolerances (written here, from the stated requirements):
+  * FP64 form: norm-wise relative error <= 1e-12 over the full [4][N] RHS
+    (atomic summation order is the only allowed difference), and every
+    entry within 1e-12 * max|RHS|;
+  * mixed form: norm-wise relative error <= 1e-5;
+  * adjoint: <= 1e-12 against the oracle's complex-step element Jacobians,
+    <= 1e-6 against central finite differences (step 1e-6).
+"""
+import numpy as np
+import pytest
+import torch
+
+import meshgen as mg
+import oracle
+import paper_2403_08777_gb300 as ns
+from paper_2403_08777_gb300 import _abi
+
+pytestmark = pytest.mark.gpu
+
+TOL_FP64 = 1e-12
+TOL_MIXED = 1e-5
+TOL_VJP_ORACLE = 1e-12
+TOL_VJP_FD = 1e-6
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ns.load_library()
+    return torch.device("cuda:0")
+
+
+def relerr(x, ref):
+    return float(np.linalg.norm(x - ref) / np.linalg.norm(ref))
+
+
+def on_dev(dev, *arrays):
+    return [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in arrays]
+
+
+def gpu_rhs(dev, w, params=None, mesh=None, up=None):
+    coords, conn, up_d = on_dev(dev, w.coords, w.conn, w.up if up is None else up)
+    mesh = mesh or ns.Mesh(coords, conn)
+    p = params or ns.Params(rho=w.rho, mu=w.mu, c_vreman=w.c_vreman)
+    if p.precision == "mixed":
+        up_d = up_d.float()
+    return mesh.assemble(up_d, p).cpu().numpy(), mesh
+
+
+def check_fp64(x, ref):
+    assert relerr(x, ref) <= TOL_FP64, relerr(x, ref)
+    assert np.abs(x - ref).max() <= TOL_FP64 * np.abs(ref).max()
+
+
+FWD_CASES = [
+    # n, jitter, order, mu, mag_max, c_vreman
+    (8, 0.1, "lex", 1e-2, 0.0, 0.0),       # the 8^3 parity mesh
+    (8, 0.1, "lex", 1e-2, 0.0, 0.07),
+    (13, 0.1, "random", 1e-2, 0.0, 0.0),   # E = 13182: ragged against every block size
+    (24, 0.1, "rcm", 1e-4, 10.0, 0.0),     # paper-scale settings, small mesh
+    (24, 0.3, "rcm", 1e-4, 10.0, 0.07),
+    (40, 0.1, "random", 1e-2, 0.0, 0.0),   # several waves of blocks
+]
+
+
+@pytest.mark.parametrize("n,jitter,order,mu,mag,cv", FWD_CASES)
+def test_fp64_forward_matches_oracle(dev, n, jitter, order, mu, mag, cv):
+    w = mg.make_workload(n, jitter=jitter, order=order, mu=mu, mag_max=mag, c_vreman=cv)
+    ref = oracle.assemble(w.coords, w.conn, w.up, w.rho, w.mu, c_vreman=cv)
+    for scatter in ("auto", "atomic"):
+        x, mesh = gpu_rhs(dev, w, ns.Params(rho=w.rho, mu=w.mu, c_vreman=cv, scatter=scatter))
+        check_fp64(x, ref)
+    mesh.close()
+
+
+def test_fp64_forward_64cube_and_renumbering(dev):
+    """64^3 (1.57M tets): lexicographic, random and RCM orders all match the
+    oracle, and agree with each other after undoing the permutation."""
+    base = mg.make_workload(64)
+    ref = oracle.assemble(base.coords, base.conn, base.up, base.rho, base.mu)
+    x, m = gpu_rhs(dev, base)
+    check_fp64(x, ref)
+    m.close()
+    for order in (mg.random_order(base.n_nodes), mg.rcm_order(base.conn, base.n_nodes)):
+        c2, cn2, up2 = mg.renumber(order, base.coords, base.conn, base.up)
+        w2 = mg.Workload("perm", 64, c2, cn2, up2, base.rho, base.mu)
+        x2, m2 = gpu_rhs(dev, w2)
+        check_fp64(x2, ref[:, order])
+        m2.close()
+
+
+def test_ragged_element_counts(dev):
+    """Meshes of 1, 31, 127, 128, 129 and 1000 elements (prefixes of a mesh,
+    with nodes left unused)."""
+    w = mg.make_workload(6, jitter=0.2, order="random")
+    for E in (1, 31, 127, 128, 129, 1000):
+        sub = mg.Workload("sub", 6, w.coords, np.ascontiguousarray(w.conn[:, :E]), w.up, 1.0, 1e-2)
+        ref = oracle.assemble(sub.coords, sub.conn, sub.up, 1.0, 1e-2)
+        x, m = gpu_rhs(dev, sub)
+        check_fp64(x, ref)
+        m.close()
+
+
+def test_single_reference_tet_closed_form(dev):
+    X = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]], float)
+    U = np.zeros((4, 4))
+    U[1, 3] = 1.0
+    coords, conn = X.T.copy(), np.arange(4, dtype=np.int32).reshape(4, 1)
+    w = mg.Workload("ref", 1, coords, conn, U.T.copy(), 1.0, 1e-2)
+    x, m = gpu_rhs(dev, w)
+    exp = np.zeros((4, 4))
+    exp[:, :3] = np.array([[-1, -1, -1], [1, 0, 0], [0, 1, 0], [0, 0, 1]]) / 24.0
+    exp[0, 3], exp[1, 3] = 1 / (24 * 1e-2), -1 / (24 * 1e-2)
+    assert np.abs(x.T - exp).max() < 1e-14
+    m.close()
+
+
+@pytest.mark.parametrize("n,cv", [(32, 0.0), (64, 0.0), (32, 0.07)])
+def test_mixed_precision_error(dev, n, cv):
+    w = mg.make_workload(n, jitter=0.3, order="rcm", mu=1e-4, mag_max=10.0, c_vreman=cv)
+    ref = oracle.assemble(w.coords, w.conn, w.up, w.rho, w.mu, c_vreman=cv)
+    x, m = gpu_rhs(dev, w, ns.Params(rho=w.rho, mu=w.mu, c_vreman=cv, precision="mixed"))
+    info = m.info()
+    assert info["n_high_ar"] > 0            # the jitter-0.3 mesh has AR > 10 elements
+    assert relerr(x, ref) <= TOL_MIXED, relerr(x, ref)
+    m.close()
+
+
+@pytest.mark.parametrize("n,order,cv", [(8, "lex", 0.0), (8, "lex", 0.07), (20, "random", 0.0),
+                                        (20, "rcm", 0.07)])
+def test_vjp_matches_oracle(dev, n, order, cv):
+    w = mg.make_workload(n, order=order, mu=1e-3, mag_max=2.0, c_vreman=cv)
+    cot = mg.normal((4, w.n_nodes), seed=mg.SEED_COT)
+    ref = oracle.vjp(w.coords, w.conn, w.up, cot, w.rho, w.mu, c_vreman=cv)
+    coords, conn, up, cot_d = on_dev(dev, w.coords, w.conn, w.up, cot)
+    m = ns.Mesh(coords, conn)
+    g = m.assemble_vjp(up, cot_d, rho=w.rho, mu=w.mu, c_vreman=cv).cpu().numpy()
+    assert relerr(g, ref) <= TOL_VJP_ORACLE, relerr(g, ref)
+    m.close()
+
+
+def test_vjp_central_differences_100_directions(dev):
+    """<grad, d> against <w, (F(u + eps d) - F(u - eps d)) / 2 eps> for 100
+    seeded directions on the 8^3 mesh, GPU forward in FP64, eps = 1e-6."""
+    w = mg.tiny()
+    cot = mg.normal((4, w.n_nodes), seed=mg.SEED_COT)
+    dirs = mg.normal((100, 4, w.n_nodes), seed=mg.SEED_DIRS)
+    coords, conn, up, cot_d = on_dev(dev, w.coords, w.conn, w.up, cot)
+    m = ns.Mesh(coords, conn)
+    p = ns.Params(rho=w.rho, mu=w.mu)
+    g = m.assemble_vjp(up, cot_d, p).cpu().numpy()
+    eps = 1e-6
+    worst = 0.0
+    for d in dirs:
+        dd = torch.from_numpy(d).to(dev)
+        fp = m.assemble(up + eps * dd, p)
+        fm = m.assemble(up - eps * dd, p)
+        fd = float(torch.sum(cot_d * (fp - fm)).item()) / (2 * eps)
+        ad = float(np.sum(g * d))
+        worst = max(worst, abs(fd - ad) / max(abs(ad), 1e-30))
+    assert worst <= TOL_VJP_FD, worst
+    m.close()
+
+
+def test_autograd_function(dev):
+    w = mg.make_workload(6, order="random", c_vreman=0.07)
+    coords, conn, up = on_dev(dev, w.coords, w.conn, w.up)
+    m = ns.Mesh(coords, conn)
+    p = ns.Params(rho=w.rho, mu=w.mu, c_vreman=0.07)
+    upg = up.clone().requires_grad_(True)
+    rhs = ns.assemble(m, upg, p)
+    cot = torch.from_numpy(mg.normal((4, w.n_nodes), seed=mg.SEED_COT)).to(dev)
+    (g,) = torch.autograd.grad(rhs, upg, cot)
+    g2 = m.assemble_vjp(up, cot, p)
+    assert torch.allclose(g, g2, rtol=0, atol=0)
+    ref = oracle.vjp(w.coords, w.conn, w.up, cot.cpu().numpy(), w.rho, w.mu, c_vreman=0.07)
+    assert relerr(g.cpu().numpy(), ref) <= TOL_VJP_ORACLE
+    m.close()
+
+
+def test_mesh_errors(dev):
+    w = mg.make_workload(3)
+    coords, conn = on_dev(dev, w.coords, w.conn)
+    bad = conn.clone()
+    bad[2, 5] = w.n_nodes  # out of range
+    with pytest.raises(ns.NSRHSError) as ei:
+        ns.Mesh(coords, bad)
+    assert ei.value.status == _abi.EMESH
+    bad = conn.clone()
+    bad[2, 7] = -1
+    with pytest.raises(ns.NSRHSError):
+        ns.Mesh(coords, bad)
+    inv = conn.clone()
+    inv[[1, 2], 11] = inv[[2, 1], 11]  # swap two nodes: detJ < 0
+    with pytest.raises(ns.NSRHSError) as ei:
+        ns.Mesh(coords, inv)
+    assert ei.value.status == _abi.EMESH
+    m = ns.Mesh(coords, conn)
+    up = torch.zeros((4, w.n_nodes), dtype=torch.float64, device=dev)
+    with pytest.raises(TypeError):
+        m.assemble(up.float())                    # wrong dtype for fp64
+    with pytest.raises(ns.NSRHSError) as ei:
+        m.assemble(up, ns.Params(mu=-1.0))        # invalid parameter
+    assert ei.value.status == _abi.EINVAL
+    with pytest.raises(ns.NSRHSError) as ei:
+        m.assemble_vjp(up, up, ns.Params(precision="mixed"))
+    assert ei.value.status == _abi.EUNSUPPORTED
+    m.close()
+    with pytest.raises(RuntimeError):
+        m.assemble(up)
+    # the library kept working after the rejected calls
+    x, m2 = gpu_rhs(dev, w)
+    check_fp64(x, oracle.assemble(w.coords, w.conn, w.up, w.rho, w.mu))
+    m2.close()
+
+
+def test_constant_velocity_gives_zero(dev):
+    w = mg.make_workload(10, order="random")
+    up = np.zeros_like(w.up)
+    up[:3] = np.array([0.3, -2.0, 1.1])[:, None]
+    x, m = gpu_rhs(dev, w, ns.Params(rho=1.0, mu=1e-2, c_vreman=0.07), up=up)
+    assert np.abs(x).max() < 1e-15
+    m.close()
