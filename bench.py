@@ -44,6 +44,12 @@ UNIT = "tets/s"
 FLOPS_PER_TET = {"fwd": 571, "vjp": 1170}
 FLOPS_PER_TET_VREMAN = {"fwd": 640, "vjp": 1315}
 
+# DRAM bytes per tet (dram__bytes_read.sum + dram__bytes_write.sum) from one
+# ncu capture of each kernel on the 128^3-hex RCM mesh, scaled to a launch by
+# the element count (traffic grows in proportion). None once a kernel has
+# changed since its counters were taken.
+DRAM_BYTES_PER_TET = {"fwd_fp64": 199.4, "vjp_fp64": 277.3}
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -335,10 +341,10 @@ def run_ours(args):
         b.record(stream)
         torch.cuda.synchronize(dev)
         assert rc == 0
-        return blocks * 256 * 8 * iters * 2 / (a.elapsed_time(b) * 1e-3) / 1e12
+        return blocks * 256 * 16 * iters * 2 / (a.elapsed_time(b) * 1e-3) / 1e12
 
-    fp64_peak = max(probe(True, 20000) for _ in range(3))
-    fp32_peak = max(probe(False, 400000) for _ in range(3))
+    fp64_peak = max(probe(True, 12000) for _ in range(3))
+    fp32_peak = max(probe(False, 200000) for _ in range(3))
 
     # ---- mixed precision ----
     forms = {}
@@ -380,7 +386,9 @@ def run_ours(args):
     dom_ms = vjp_med if dom == "vjp_fp64" else fwd_med
     achieved = forms[dom]["tflops"]
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fp64_peak,
-                "unit": "TFLOP/s", "frac": achieved / fp64_peak, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / fp64_peak,
+                "traffic": (DRAM_BYTES_PER_TET[dom] * w.n_elems
+                            if DRAM_BYTES_PER_TET.get(dom) is not None else None),
                 "peak_source": "FP64 FMA-chain probe measured live in this run (not in "
                                "MEASURED_PEAKS.json)",
                 "flops_per_tet": flops["vjp" if dom == "vjp_fp64" else "fwd"],

@@ -17,11 +17,11 @@ extern "C" {
 
 /*
  * Launch an FMA-throughput kernel on `stream`: `blocks` blocks of 256
- * threads, each thread running 8 independent dependent chains of `iters`
+ * threads, each thread running 16 independent dependent chains of `iters`
  * fused multiply-adds in double (fp64 != 0) or float (fp64 == 0), then
  * writing one value per thread to sink[blocks * 256] (device memory, double)
  * so that the work cannot be removed. FLOPs per launch =
- * blocks * 256 * 8 * iters * 2. Time it with events on the same stream.
+ * blocks * 256 * 16 * iters * 2. Time it with events on the same stream.
  * Returns 0, or a nonzero nsrhs_status value (1 bad argument, 4 CUDA error).
  */
 int nsrhs_probe_fma(int fp64, int64_t blocks, int64_t iters, double* sink, void* stream);

@@ -146,5 +146,7 @@ def submesh_for_nodes(conn, nodes):
     over this sub-mesh equals its RHS over the full mesh (sampled parity at
     sizes where the full oracle would be slow). Returns conn_sub [4][E_sub]."""
     conn = np.asarray(conn)
-    mask = np.isin(conn, np.asarray(nodes)).any(axis=0)
+    mark = np.zeros(int(conn.max()) + 1, bool)
+    mark[np.asarray(nodes)] = True
+    mask = mark[conn].any(axis=0)
     return np.ascontiguousarray(conn[:, mask])

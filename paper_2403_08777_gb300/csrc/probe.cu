@@ -10,21 +10,20 @@ namespace {
 
 template <class T>
 __global__ void __launch_bounds__(256) fma_chain_kernel(int64_t iters, T a, T b, double* sink) {
-  // 8 independent chains per thread hide the pipe latency.
-  T x0 = (T)threadIdx.x * (T)1e-3, x1 = x0 + (T)1, x2 = x0 + (T)2, x3 = x0 + (T)3;
-  T x4 = x0 + (T)4, x5 = x0 + (T)5, x6 = x0 + (T)6, x7 = x0 + (T)7;
+  // 16 independent dependent chains per thread, loop unrolled, so that the
+  // FMA pipe (not latency or loop overhead) limits the rate.
+  T x[16];
+#pragma unroll
+  for (int c = 0; c < 16; ++c) x[c] = (T)threadIdx.x * (T)1e-3 + (T)c;
+#pragma unroll 4
   for (int64_t i = 0; i < iters; ++i) {
-    x0 = fma(x0, a, b);
-    x1 = fma(x1, a, b);
-    x2 = fma(x2, a, b);
-    x3 = fma(x3, a, b);
-    x4 = fma(x4, a, b);
-    x5 = fma(x5, a, b);
-    x6 = fma(x6, a, b);
-    x7 = fma(x7, a, b);
+#pragma unroll
+    for (int c = 0; c < 16; ++c) x[c] = fma(x[c], a, b);
   }
-  sink[blockIdx.x * (int64_t)blockDim.x + threadIdx.x] =
-      (double)(((x0 + x1) + (x2 + x3)) + ((x4 + x5) + (x6 + x7)));
+  T acc = (T)0;
+#pragma unroll
+  for (int c = 0; c < 16; ++c) acc += x[c];
+  sink[blockIdx.x * (int64_t)blockDim.x + threadIdx.x] = (double)acc;
 }
 
 }  // namespace

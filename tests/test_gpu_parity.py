@@ -175,7 +175,8 @@ def test_autograd_function(dev):
     cot = torch.from_numpy(mg.normal((4, w.n_nodes), seed=mg.SEED_COT)).to(dev)
     (g,) = torch.autograd.grad(rhs, upg, cot)
     g2 = m.assemble_vjp(up, cot, p)
-    assert torch.allclose(g, g2, rtol=0, atol=0)
+    # same kernel; only the order of the atomic adds may differ between runs
+    assert relerr(g.cpu().numpy(), g2.cpu().numpy()) <= 1e-14
     ref = oracle.vjp(w.coords, w.conn, w.up, cot.cpu().numpy(), w.rho, w.mu, c_vreman=0.07)
     assert relerr(g.cpu().numpy(), ref) <= TOL_VJP_ORACLE
     m.close()
