@@ -148,6 +148,51 @@ void nsrhs_destroy(nsrhs_mesh* m);
 
 const char* nsrhs_status_string(nsrhs_status s);
 
+/*
+ * ---- Mesh check that allocates nothing ----
+ * The paper has no counterpart to this call; it exists for callers that
+ * cannot allocate device memory: code that owns all GPU memory through its
+ * own fixed arena, or runs where a cudaMalloc (which may synchronise the
+ * device, fail late, or be forbidden by the host framework) is not allowed.
+ * nsrhs_mesh_create copies the mesh and allocates scratch for its checks;
+ * this call performs the same checks on the caller's arrays in place and
+ * writes only to the caller's result.
+ *
+ * Checks every element of coords [3][n_nodes] / conn [4][n_elems] (device
+ * arrays) exactly as nsrhs_mesh_create does and writes one
+ * nsrhs_mesh_check_result into *result_dev (caller-owned DEVICE memory):
+ * the number of elements with an index out of [0, n_nodes), the number with
+ * detJ <= 0, the number with aspect ratio > ar_threshold, and the minimum
+ * detJ / maximum aspect ratio over the valid elements (+inf / 0 if none).
+ * Asynchronous on `stream`; read the result after synchronising it.
+ *
+ * Scratch: a file-scope device array of NSRHS_CHECK_SCRATCH_BLOCKS partial
+ * results (64 bytes each, 64 KiB in all) that every GPU which loads the
+ * library holds until the process exits. Every call writes the partials it
+ * uses before reading them, so no state carries over from the last call; but
+ * all calls share that one array, so calls whose kernels overlap on the GPU
+ * (different streams, or different host threads, without ordering between
+ * them) race and may return wrong results. Serialise them.
+ *
+ * The first call on each device looks up the array's device address (with
+ * that device current) and remembers it; make that first call before any
+ * stream capture. 1 <= n_nodes, n_elems < 2^31 and ar_threshold > 0, else
+ * NSRHS_EINVAL. No cudaMalloc, cudaFree or other allocating call is made.
+ */
+#define NSRHS_CHECK_SCRATCH_BLOCKS 1024
+
+typedef struct {
+  int64_t bad_index; /* elements with a node index outside [0, n_nodes) */
+  int64_t bad_det;   /* elements with detJ <= 0 */
+  int64_t n_high_ar; /* valid elements with aspect ratio > ar_threshold */
+  double min_detj;   /* over valid elements */
+  double max_ar;     /* over valid elements */
+} nsrhs_mesh_check_result;
+
+nsrhs_status nsrhs_mesh_check_noalloc(int64_t n_nodes, int64_t n_elems, const double* coords,
+                                      const int32_t* conn, double ar_threshold, void* stream,
+                                      nsrhs_mesh_check_result* result_dev);
+
 #ifdef __cplusplus
 }
 #endif

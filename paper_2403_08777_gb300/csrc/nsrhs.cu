@@ -143,6 +143,163 @@ __global__ void validate_kernel(int64_t N, int64_t E, const double* __restrict__
   }
 }
 
+// ---------------------------------------------------------------------------
+// Mesh check without allocation (nsrhs_mesh_check_noalloc). The same
+// per-element checks as validate_kernel; partial results per block go to a
+// static device array instead of cudaMalloc'd memory, and a one-block kernel
+// reduces them into the caller's result.
+
+struct CheckPartial {
+  unsigned long long bad_index, bad_det, n_high_ar;
+  double min_det, max_ar;
+  double pad[3];  // 64 bytes
+};
+static_assert(sizeof(CheckPartial) == 64, "CheckPartial layout");
+
+// One slot per block of check_partials_kernel (64 KiB). Host code must not
+// pass this symbol to a kernel: it uses the address from cudaGetSymbolAddress.
+static __device__ __align__(256) CheckPartial g_check_scratch[NSRHS_CHECK_SCRATCH_BLOCKS];
+
+constexpr int kCheckThreads = 256;
+
+__global__ void __launch_bounds__(kCheckThreads)
+    check_partials_kernel(int64_t N, int64_t E, const double* __restrict__ coords,
+                          const int32_t* __restrict__ conn, double ar_threshold,
+                          CheckPartial* __restrict__ partials) {
+  unsigned long long bad_index = 0, bad_det = 0, n_high = 0;
+  double min_det = __longlong_as_double(0x7FF0000000000000ll), max_ar = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int32_t v[4];
+    bool ok = true;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      v[a] = conn[a * E + e];
+      ok = ok && v[a] >= 0 && (int64_t)v[a] < N;
+    }
+    if (!ok) {
+      ++bad_index;
+      continue;
+    }
+    double X[4][3];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int d = 0; d < 3; ++d) X[a][d] = coords[d * N + v[a]];
+    double ed[3][3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int d = 0; d < 3; ++d) ed[k][d] = X[k + 1][d] - X[0][d];
+    double det = ed[0][0] * (ed[1][1] * ed[2][2] - ed[1][2] * ed[2][1]) -
+                 ed[0][1] * (ed[1][0] * ed[2][2] - ed[1][2] * ed[2][0]) +
+                 ed[0][2] * (ed[1][0] * ed[2][1] - ed[1][1] * ed[2][0]);
+    if (!(det > 0.0)) {
+      ++bad_det;
+      continue;
+    }
+    double lmax2 = 0.0;
+    for (int a = 0; a < 4; ++a)
+      for (int b = a + 1; b < 4; ++b) {
+        double dx = X[b][0] - X[a][0], dy = X[b][1] - X[a][1], dz = X[b][2] - X[a][2];
+        lmax2 = fmax(lmax2, dx * dx + dy * dy + dz * dz);
+      }
+    double S = 0.0;
+    const int fc[4][3] = {{1, 2, 3}, {0, 2, 3}, {0, 1, 3}, {0, 1, 2}};
+    for (int f = 0; f < 4; ++f) {
+      const double* A = X[fc[f][0]];
+      const double* B = X[fc[f][1]];
+      const double* C = X[fc[f][2]];
+      double ab[3] = {B[0] - A[0], B[1] - A[1], B[2] - A[2]};
+      double ac[3] = {C[0] - A[0], C[1] - A[1], C[2] - A[2]};
+      double cx = ab[1] * ac[2] - ab[2] * ac[1];
+      double cy = ab[2] * ac[0] - ab[0] * ac[2];
+      double cz = ab[0] * ac[1] - ab[1] * ac[0];
+      S += 0.5 * sqrt(cx * cx + cy * cy + cz * cz);
+    }
+    double ar = sqrt(lmax2) * S / (sqrt(6.0) * det);
+    if (ar > ar_threshold) ++n_high;
+    min_det = fmin(min_det, det);
+    max_ar = fmax(max_ar, ar);
+  }
+  __shared__ CheckPartial red[kCheckThreads];
+  red[threadIdx.x] = CheckPartial{bad_index, bad_det, n_high, min_det, max_ar, {0.0, 0.0, 0.0}};
+  __syncthreads();
+  for (int stride = kCheckThreads / 2; stride > 0; stride >>= 1) {
+    if ((int)threadIdx.x < stride) {
+      CheckPartial& a = red[threadIdx.x];
+      const CheckPartial& b = red[threadIdx.x + stride];
+      a.bad_index += b.bad_index;
+      a.bad_det += b.bad_det;
+      a.n_high_ar += b.n_high_ar;
+      a.min_det = fmin(a.min_det, b.min_det);
+      a.max_ar = fmax(a.max_ar, b.max_ar);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partials[blockIdx.x] = red[0];
+}
+
+__global__ void __launch_bounds__(kCheckThreads)
+    check_reduce_kernel(int n_partials, const CheckPartial* __restrict__ partials,
+                        nsrhs_mesh_check_result* __restrict__ result) {
+  CheckPartial acc{0ull, 0ull, 0ull, __longlong_as_double(0x7FF0000000000000ll), 0.0,
+                   {0.0, 0.0, 0.0}};
+  for (int i = threadIdx.x; i < n_partials; i += blockDim.x) {
+    const CheckPartial& b = partials[i];
+    acc.bad_index += b.bad_index;
+    acc.bad_det += b.bad_det;
+    acc.n_high_ar += b.n_high_ar;
+    acc.min_det = fmin(acc.min_det, b.min_det);
+    acc.max_ar = fmax(acc.max_ar, b.max_ar);
+  }
+  __shared__ CheckPartial red[kCheckThreads];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int stride = kCheckThreads / 2; stride > 0; stride >>= 1) {
+    if ((int)threadIdx.x < stride) {
+      CheckPartial& a = red[threadIdx.x];
+      const CheckPartial& b = red[threadIdx.x + stride];
+      a.bad_index += b.bad_index;
+      a.bad_det += b.bad_det;
+      a.n_high_ar += b.n_high_ar;
+      a.min_det = fmin(a.min_det, b.min_det);
+      a.max_ar = fmax(a.max_ar, b.max_ar);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    result->bad_index = (int64_t)red[0].bad_index;
+    result->bad_det = (int64_t)red[0].bad_det;
+    result->n_high_ar = (int64_t)red[0].n_high_ar;
+    result->min_detj = red[0].min_det;
+    result->max_ar = red[0].max_ar;
+  }
+}
+
+constexpr int kMaxDevices = 64;
+std::mutex g_check_mutex;
+CheckPartial* g_check_addr[kMaxDevices] = {};
+
+// Device address of g_check_scratch on the current device (looked up once per
+// device with that device current).
+nsrhs_status check_scratch_address(CheckPartial** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return NSRHS_ECUDA;
+  std::lock_guard<std::mutex> lock(g_check_mutex);
+  if (g_check_addr[dev] == nullptr) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_check_scratch);
+    if (e != cudaSuccess || p == nullptr) {
+      cudaGetLastError();
+      return NSRHS_ECUDA;
+    }
+    g_check_addr[dev] = (CheckPartial*)p;
+  }
+  *out = g_check_addr[dev];
+  return NSRHS_OK;
+}
+
 // conn_sub[a][i] = conn[a][idx[i]]
 __global__ void gather_conn_kernel(int64_t E, const int32_t* __restrict__ conn, int64_t n,
                                    const int32_t* __restrict__ idx, int32_t* __restrict__ sub) {
@@ -524,6 +681,28 @@ nsrhs_status nsrhs_assemble_vjp(const nsrhs_mesh* m, const nsrhs_params* p, cons
     vjp_fp64_atomic_kernel<true><<<grid, kThreads, 0, s>>>(N, E, m->conn, m->coords, up, cot, P, grad);
   else
     vjp_fp64_atomic_kernel<false><<<grid, kThreads, 0, s>>>(N, E, m->conn, m->coords, up, cot, P, grad);
+  return cuda_status(cudaGetLastError());
+}
+
+nsrhs_status nsrhs_mesh_check_noalloc(int64_t n_nodes, int64_t n_elems, const double* coords,
+                                      const int32_t* conn, double ar_threshold, void* stream,
+                                      nsrhs_mesh_check_result* result_dev) {
+  if (!coords || !conn || !result_dev) return NSRHS_EINVAL;
+  if (n_nodes < 1 || n_elems < 1 || n_nodes > INT32_MAX || n_elems > INT32_MAX) return NSRHS_EINVAL;
+  if (!(ar_threshold > 0.0)) return NSRHS_EINVAL;
+  CheckPartial* scratch = nullptr;
+  nsrhs_status st = check_scratch_address(&scratch);
+  if (st != NSRHS_OK) return st;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int64_t need = (n_elems + kCheckThreads - 1) / kCheckThreads;
+  int64_t cap = std::min<int64_t>((int64_t)sm_count(dev) * 4, NSRHS_CHECK_SCRATCH_BLOCKS);
+  int grid = (int)std::max<int64_t>(1, std::min(need, cap));
+  cudaStream_t s = (cudaStream_t)stream;
+  check_partials_kernel<<<grid, kCheckThreads, 0, s>>>(n_nodes, n_elems, coords, conn,
+                                                       ar_threshold, scratch);
+  NSRHS_TRY(cudaGetLastError());
+  check_reduce_kernel<<<1, kCheckThreads, 0, s>>>(grid, scratch, result_dev);
   return cuda_status(cudaGetLastError());
 }
 
