@@ -26,6 +26,17 @@ extern "C" {
  */
 int nsrhs_probe_fma(int fp64, int64_t blocks, int64_t iters, double* sink, void* stream);
 
+/*
+ * Evaluate this library's double-precision special functions beside CUDA's
+ * on n device values x: which = 0 reciprocal (x > 0), 1 square root
+ * (x >= 0), 2 reciprocal cube root (x > 0), 3 float -> double widening of
+ * float(x). ours[i] / ref[i] (device arrays of n doubles) receive the
+ * library's and CUDA's results. Used by the tests to bound the error of the
+ * kernels' special functions. Returns 0, 1 (bad argument) or 4 (CUDA error).
+ */
+int nsrhs_probe_special(int which, int64_t n, const double* x, double* ours, double* ref,
+                        void* stream);
+
 #ifdef __cplusplus
 }
 #endif

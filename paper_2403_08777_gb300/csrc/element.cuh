@@ -29,6 +29,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "fastmath.cuh"
+
 namespace nsrhs {
 
 // 4-point degree-2 Gauss rule on the tet: QA = (5 + 3 sqrt 5)/20, QB = (5 - sqrt 5)/20.
@@ -43,11 +45,13 @@ struct ElemParams {
 template <class R>
 struct MathOps;
 
+// Double precision: seed + one cubic correction (fastmath.cuh). Arguments
+// are positive (reciprocals, cube roots) or non-negative (square roots).
 template <>
 struct MathOps<double> {
-  static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
-  static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
-  static __device__ __forceinline__ double rcbrt_(double x) { return rcbrt(x); }
+  static __device__ __forceinline__ double rcp(double x) { return rcp_pos(x); }
+  static __device__ __forceinline__ double sqrt_(double x) { return sqrt_nonneg(x); }
+  static __device__ __forceinline__ double rcbrt_(double x) { return rcbrt_pos(x); }
 };
 
 template <>
@@ -57,17 +61,13 @@ struct MathOps<float> {
   static __device__ __forceinline__ float rcbrt_(float x) { return rcbrtf(x); }
 };
 
-// Element geometry: unscaled cofactor vectors c[k] (k = 0..2 for nodes 1..3),
-// 1/detJ and 1/h = detJ^(-1/3). Edges are formed in double from double
-// coordinates; the cofactors and determinant in GR, then stored as R.
-template <class R, class GR, class XT = double>
-__device__ __forceinline__ void element_geometry(const XT X[4][3], R c[3][3], R& inv_det, R& rh,
-                                                 double* det_out = nullptr) {
-  GR e[3][3];
-#pragma unroll
-  for (int k = 0; k < 3; ++k)
-#pragma unroll
-    for (int d = 0; d < 3; ++d) e[k][d] = (GR)(X[k + 1][d] - X[0][d]);
+// Element geometry from the edge vectors e[k] = X_{k+1} - X_0: unscaled
+// cofactor vectors c[k] (k = 0..2 for nodes 1..3), 1/detJ and
+// 1/h = detJ^(-1/3); cofactors and determinant in GR, stored as R.
+template <class R, class GR>
+__device__ __forceinline__ void element_geometry_from_edges(const GR e[3][3], R c[3][3],
+                                                            R& inv_det, R& rh,
+                                                            double* det_out = nullptr) {
   GR cc[3][3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
@@ -85,6 +85,18 @@ __device__ __forceinline__ void element_geometry(const XT X[4][3], R c[3][3], R&
     for (int d = 0; d < 3; ++d) c[k][d] = (R)cc[k][d];
   inv_det = (R)MathOps<GR>::rcp(det);
   rh = (R)MathOps<GR>::rcbrt_(det);
+}
+
+// Element geometry from node coordinates X (edges formed in XT, then GR).
+template <class R, class GR, class XT = double>
+__device__ __forceinline__ void element_geometry(const XT X[4][3], R c[3][3], R& inv_det, R& rh,
+                                                 double* det_out = nullptr) {
+  GR e[3][3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) e[k][d] = (GR)(X[k + 1][d] - X[0][d]);
+  element_geometry_from_edges<R, GR>(e, c, inv_det, rh, det_out);
 }
 
 // Forward element RHS. u[a][i], p[a] nodal values; F[a][0..2] momentum,
@@ -109,7 +121,7 @@ __device__ __forceinline__ void element_rhs(const R c[3][3], R inv_det, R rh, co
   R S[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) S[i] = (u[0][i] + u[1][i]) + (u[2][i] + u[3][i]);
-  const R pbar = ((p[0] + p[1]) + (p[2] + p[3])) * (R)0.25;
+  const R psum = (p[0] + p[1]) + (p[2] + p[3]);
   const R trG = G[0][0] + G[1][1] + G[2][2];
 
   R mu_eff = P.mu;
@@ -163,60 +175,82 @@ __device__ __forceinline__ void element_rhs(const R c[3][3], R inv_det, R rh, co
     Q02 += tu[0] * ug[2];
     Q12 += tu[1] * ug[2];
   }
-  // Qp = mu_eff I + rho^2/4 Q
-  const R r24 = P.rho * P.rho * (R)0.25;
-  const R Qp[3][3] = {{mu_eff + r24 * Q00, r24 * Q01, r24 * Q02},
-                      {r24 * Q01, mu_eff + r24 * Q11, r24 * Q12},
-                      {r24 * Q02, r24 * Q12, mu_eff + r24 * Q22}};
-  // K = pbar/6 I - inv_det/6 (Gh Qp + rho/4 gph T^T)
+  // K = pbar/6 I - inv_det/6 [Gh (mu_eff I + rho^2/4 Q) + rho/4 gph T^T], with the
+  // scalar factors folded into Qp and gq before the 3x3 product so that each
+  // entry is one chain of fused multiply-adds.
   const R s6 = inv_det * (R)(1.0 / 6.0);
-  const R r4 = P.rho * (R)0.25;
+  const R a2 = -s6 * (P.rho * P.rho * (R)0.25);
+  const R a1 = -s6 * mu_eff;
+  const R b4 = -s6 * (P.rho * (R)0.25);
+  const R Qp[3][3] = {{a2 * Q00 + a1, a2 * Q01, a2 * Q02},
+                      {a2 * Q01, a2 * Q11 + a1, a2 * Q12},
+                      {a2 * Q02, a2 * Q12, a2 * Q22 + a1}};
+  const R pb6 = psum * (R)(1.0 / 24.0);
   R K[3][3];
 #pragma unroll
-  for (int i = 0; i < 3; ++i)
+  for (int i = 0; i < 3; ++i) {
+    const R gq = b4 * gp[i];
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-      R w = G[i][0] * Qp[0][j] + G[i][1] * Qp[1][j] + G[i][2] * Qp[2][j] + r4 * gp[i] * T[j];
-      K[i][j] = -s6 * w;
+      R acc = (i == j) ? gq * T[j] + pb6 : gq * T[j];
+      acc = G[i][0] * Qp[0][j] + acc;
+      acc = G[i][1] * Qp[1][j] + acc;
+      K[i][j] = G[i][2] * Qp[2][j] + acc;
     }
-  const R pb6 = pbar * (R)(1.0 / 6.0);
-  K[0][0] += pb6;
-  K[1][1] += pb6;
-  K[2][2] += pb6;
+  }
   // Rs = inv_det/24 (rho Gh T + stau gph)
-  R Rs[3];
   const R s24 = inv_det * (R)(1.0 / 24.0);
+  const R sT = s24 * P.rho;
+  const R sg = s24 * stau;
+  R Rs[3];
 #pragma unroll
-  for (int i = 0; i < 3; ++i)
-    Rs[i] = s24 * (P.rho * (G[i][0] * T[0] + G[i][1] * T[1] + G[i][2] * T[2]) + stau * gp[i]);
+  for (int i = 0; i < 3; ++i) {
+    R acc = sg * gp[i];
+    acc = (sT * T[0]) * G[i][0] + acc;
+    acc = (sT * T[1]) * G[i][1] + acc;
+    Rs[i] = (sT * T[2]) * G[i][2] + acc;
+  }
   const R cont0 = trG * (R)(-1.0 / 24.0);
+  // Galerkin convection -(rho/120) Gh (S_u + u_a) = Gh v_a, v_a = m120 u_a + m120 S_u
   const R m120 = P.rho * (R)(-1.0 / 120.0);
-
-  R y0[3] = {(R)0, (R)0, (R)0};
-  R csR = (R)0;
+  R mS[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) mS[i] = m120 * S[i];
+  R ysum[3] = {(R)0, (R)0, (R)0};
+  R csum = (R)0;
 #pragma unroll
   for (int a = 1; a < 4; ++a) {
     const R* ca = c[a - 1];
     R v[3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) v[i] = m120 * (S[i] + u[a][i]);
+    for (int i = 0; i < 3; ++i) v[i] = m120 * u[a][i] + mS[i];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      R y = K[i][0] * ca[0] + K[i][1] * ca[1] + K[i][2] * ca[2];
-      y0[i] -= y;
-      F[a][i] = y + G[i][0] * v[0] + G[i][1] * v[1] + G[i][2] * v[2];
+      R y = K[i][0] * ca[0];
+      y = K[i][1] * ca[1] + y;
+      y = K[i][2] * ca[2] + y;
+      ysum[i] += y;
+      R f = G[i][0] * v[0] + y;
+      f = G[i][1] * v[1] + f;
+      F[a][i] = G[i][2] * v[2] + f;
     }
-    R cr = ca[0] * Rs[0] + ca[1] * Rs[1] + ca[2] * Rs[2];
-    csR += cr;
-    F[a][3] = cont0 - cr;
+    R f3 = cont0 - ca[0] * Rs[0];
+    f3 = f3 - ca[1] * Rs[1];
+    F[a][3] = f3 - ca[2] * Rs[2];
+    csum += F[a][3];
   }
   {
     R v[3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) v[i] = m120 * (S[i] + u[0][i]);
+    for (int i = 0; i < 3; ++i) v[i] = m120 * u[0][i] + mS[i];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) F[0][i] = y0[i] + G[i][0] * v[0] + G[i][1] * v[1] + G[i][2] * v[2];
-    F[0][3] = cont0 + csR;
+    for (int i = 0; i < 3; ++i) {
+      R f = G[i][0] * v[0] - ysum[i];
+      f = G[i][1] * v[1] + f;
+      F[0][i] = G[i][2] * v[2] + f;
+    }
+    // sum_a c_a = 0: the continuity entries sum to 4 cont0
+    F[0][3] = (R)4 * cont0 - csum;
   }
 }
 

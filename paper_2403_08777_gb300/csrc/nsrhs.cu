@@ -29,6 +29,7 @@ struct nsrhs_mesh {
   int64_t n_nodes = 0, n_elems = 0;
   int device = 0;
   double* coords = nullptr;   // [3][N]
+  float2* coords_hl = nullptr;  // [3][N] (hi, lo) float pairs: hi + lo = coords to ~2^-48
   int32_t* conn = nullptr;    // [4][E], caller's element order
   // Mixed form: elements split by aspect ratio, each list with its own
   // contiguous connectivity so that a warp never mixes the two kinds.
@@ -300,6 +301,17 @@ nsrhs_status check_scratch_address(CheckPartial** out) {
   return NSRHS_OK;
 }
 
+// hl[i] = (hi, lo) with hi = float(x[i]), lo = float(x[i] - hi)
+__global__ void split_coords_kernel(int64_t n, const double* __restrict__ x,
+                                    float2* __restrict__ hl) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = x[i];
+    const float hi = __double2float_rn(v);
+    hl[i] = make_float2(hi, __double2float_rn(v - (double)hi));
+  }
+}
+
 // conn_sub[a][i] = conn[a][idx[i]]
 __global__ void gather_conn_kernel(int64_t E, const int32_t* __restrict__ conn, int64_t n,
                                    const int32_t* __restrict__ idx, int32_t* __restrict__ sub) {
@@ -350,37 +362,58 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
-// Mixed form: float (u,p) and float element arithmetic; edges from double
-// coordinates in double; det/inverse in GR (double for high-aspect-ratio
-// elements, float otherwise); double global accumulation.
-template <class GR, bool VREMAN>
+// Mixed form: float (u,p) and float element arithmetic, double global
+// accumulation. Edges: for elements with aspect ratio <= threshold from the
+// (hi, lo) float pairs of the coordinates, (hi_k - hi_0) + (lo_k - lo_0), with
+// float cofactors/determinant; for the others (HIGH_AR) from the double
+// coordinates, with double cofactors/determinant/inverse. Float results are
+// widened to double with integer operations (no FP64 conversions).
+template <bool HIGH_AR, bool VREMAN>
 __global__ void __launch_bounds__(kThreads)
     fwd_mixed_atomic_kernel(int64_t N, int64_t E, const int32_t* __restrict__ conn,
-                            const double* __restrict__ coords, const float* __restrict__ up,
+                            const double* __restrict__ coords,
+                            const float2* __restrict__ coords_hl, const float* __restrict__ up,
                             ElemParams<float> P, double* __restrict__ rhs) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E;
        e += (int64_t)gridDim.x * blockDim.x) {
     int32_t v[4];
 #pragma unroll
     for (int a = 0; a < 4; ++a) v[a] = ldg(conn + a * E + e);
-    double X[4][3];
     float u[4][3], p[4];
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
-#pragma unroll
-      for (int d = 0; d < 3; ++d) X[a][d] = ldg(coords + d * N + v[a]);
 #pragma unroll
       for (int i = 0; i < 3; ++i) u[a][i] = ldg(up + i * N + v[a]);
       p[a] = ldg(up + 3 * N + v[a]);
     }
     float c[3][3], inv_det, rh;
-    nsrhs::element_geometry<float, GR>(X, c, inv_det, rh);
+    if (HIGH_AR) {
+      double X[4][3];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) X[a][d] = ldg(coords + d * N + v[a]);
+      nsrhs::element_geometry<float, double>(X, c, inv_det, rh);
+    } else {
+      float2 X[4][3];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) X[a][d] = ldg(coords_hl + d * N + v[a]);
+      float ed[3][3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+          ed[k][d] = (X[k + 1][d].x - X[0][d].x) + (X[k + 1][d].y - X[0][d].y);
+      nsrhs::element_geometry_from_edges<float, float>(ed, c, inv_det, rh);
+    }
     float F[4][4];
     nsrhs::element_rhs<float, VREMAN>(c, inv_det, rh, u, p, P, F);
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int k = 0; k < 4; ++k) atomicAdd(rhs + k * N + v[a], (double)F[a][k]);
+      for (int k = 0; k < 4; ++k) atomicAdd(rhs + k * N + v[a], nsrhs::widen_f32(F[a][k]));
   }
 }
 
@@ -485,6 +518,10 @@ nsrhs_status mesh_build(nsrhs_mesh* m, const double* coords, const int32_t* conn
   if ((st = mesh_alloc(m, &m->conn, 4 * (size_t)E)) != NSRHS_OK) return st;
   NSRHS_TRY(cudaMemcpyAsync(m->coords, coords, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, s));
   NSRHS_TRY(cudaMemcpyAsync(m->conn, conn, sizeof(int32_t) * 4 * E, cudaMemcpyDeviceToDevice, s));
+  if ((st = mesh_alloc(m, &m->coords_hl, 3 * (size_t)N)) != NSRHS_OK) return st;
+  split_coords_kernel<<<grid_for(3 * N, m->device, 8), kThreads, 0, s>>>(3 * N, m->coords,
+                                                                         m->coords_hl);
+  NSRHS_TRY(cudaGetLastError());
 
   // Validation scratch (freed before returning).
   uint8_t* high_ar = nullptr;
@@ -647,20 +684,20 @@ nsrhs_status nsrhs_assemble(const nsrhs_mesh* m, const nsrhs_params* p, const vo
     if (m->n_lo > 0) {
       unsigned grid = grid_for(m->n_lo, m->device, 16);
       if (vreman)
-        fwd_mixed_atomic_kernel<float, true>
-            <<<grid, kThreads, 0, s>>>(N, m->n_lo, m->conn_lo, m->coords, u, P, rhs);
+        fwd_mixed_atomic_kernel<false, true><<<grid, kThreads, 0, s>>>(
+            N, m->n_lo, m->conn_lo, m->coords, m->coords_hl, u, P, rhs);
       else
-        fwd_mixed_atomic_kernel<float, false>
-            <<<grid, kThreads, 0, s>>>(N, m->n_lo, m->conn_lo, m->coords, u, P, rhs);
+        fwd_mixed_atomic_kernel<false, false><<<grid, kThreads, 0, s>>>(
+            N, m->n_lo, m->conn_lo, m->coords, m->coords_hl, u, P, rhs);
     }
     if (m->n_hi > 0) {
       unsigned grid = grid_for(m->n_hi, m->device, 16);
       if (vreman)
-        fwd_mixed_atomic_kernel<double, true>
-            <<<grid, kThreads, 0, s>>>(N, m->n_hi, m->conn_hi, m->coords, u, P, rhs);
+        fwd_mixed_atomic_kernel<true, true><<<grid, kThreads, 0, s>>>(
+            N, m->n_hi, m->conn_hi, m->coords, m->coords_hl, u, P, rhs);
       else
-        fwd_mixed_atomic_kernel<double, false>
-            <<<grid, kThreads, 0, s>>>(N, m->n_hi, m->conn_hi, m->coords, u, P, rhs);
+        fwd_mixed_atomic_kernel<true, false><<<grid, kThreads, 0, s>>>(
+            N, m->n_hi, m->conn_hi, m->coords, m->coords_hl, u, P, rhs);
     }
   }
   return cuda_status(cudaGetLastError());
