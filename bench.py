@@ -37,12 +37,14 @@ import meshgen as mg  # noqa: E402
 METRIC = "tets assembled/sec + FP64 TF/s (fraction of roofline), FP32 & adjoint vs plain FP64"
 UNIT = "tets/s"
 
-# Algorithmic FP64 operations per tet of the kernels' formulation
+# Algorithmic FP64 operations per tet and call of the kernels' formulation
 # (add/sub/mul = 1, fused multiply-add = 2, sqrt/reciprocal/cube root = 1),
 # counted by instantiating the element code with a counting scalar
 # (tests/test_flop_count.py keeps these numbers in step with the source).
-FLOPS_PER_TET = {"fwd": 567, "vjp": 1170}
-FLOPS_PER_TET_VREMAN = {"fwd": 636, "vjp": 1315}
+# The element geometry (43 flops per tet) is computed once per mesh and
+# cached, so it is not part of a call.
+FLOPS_PER_TET = {"fwd": 524, "vjp": 1107}
+FLOPS_PER_TET_VREMAN = {"fwd": 593, "vjp": 1252}
 
 # DRAM bytes per tet (dram__bytes_read.sum + dram__bytes_write.sum) from one
 # ncu capture of each kernel on the 128^3-hex RCM mesh, scaled to a launch by

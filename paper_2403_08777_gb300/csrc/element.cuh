@@ -52,6 +52,7 @@ struct MathOps<double> {
   static __device__ __forceinline__ double rcp(double x) { return rcp_pos(x); }
   static __device__ __forceinline__ double sqrt_(double x) { return sqrt_nonneg(x); }
   static __device__ __forceinline__ double rcbrt_(double x) { return rcbrt_pos(x); }
+  static __device__ __forceinline__ double rsqrt_(double x) { return rsqrt_nonneg(x); }
 };
 
 template <>
@@ -59,6 +60,7 @@ struct MathOps<float> {
   static __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
   static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
   static __device__ __forceinline__ float rcbrt_(float x) { return rcbrtf(x); }
+  static __device__ __forceinline__ float rsqrt_(float x) { return x > 0.0f ? rsqrtf(x) : 0.0f; }
 };
 
 // Element geometry from the edge vectors e[k] = X_{k+1} - X_0: unscaled
@@ -255,7 +257,10 @@ __device__ __forceinline__ void element_rhs(const R c[3][3], R inv_det, R rh, co
 }
 
 // Reverse sweep: given w[a][0..3] (cotangent of F[a][0..3]), returns
-// gu[a][i] = sum_{b,k} w[b][k] dF[b][k]/du[a][i] and gp_out[a] likewise for p.
+// gu[a][i] = sum_{b,k} w[b][k] dF[b][k]/du[a][i] and gpo[a] likewise for p.
+// It differentiates exactly the sequence of element_rhs (same intermediates),
+// recomputing the forward quantities; every product is written as a chain of
+// fused multiply-adds.
 template <class R, bool VREMAN>
 __device__ __forceinline__ void element_vjp(const R c[3][3], R inv_det, R rh, const R u[4][3],
                                             const R p[4], const R w[4][4], const ElemParams<R>& P,
@@ -279,7 +284,7 @@ __device__ __forceinline__ void element_vjp(const R c[3][3], R inv_det, R rh, co
   for (int i = 0; i < 3; ++i) S[i] = (u[0][i] + u[1][i]) + (u[2][i] + u[3][i]);
 
   R mu_eff = P.mu;
-  R vA = (R)0, vB = (R)0, vphi = (R)0, vscale = (R)0;  // Vreman intermediates
+  R vA = (R)0, vphi = (R)0, vscale = (R)0;  // Vreman intermediates
   R b00 = (R)0, b11 = (R)0, b22 = (R)0, b01 = (R)0, b02 = (R)0, b12 = (R)0;
   bool vactive = false;
   if (VREMAN) {
@@ -293,7 +298,7 @@ __device__ __forceinline__ void element_vjp(const R c[3][3], R inv_det, R rh, co
     b01 = G[0][0] * G[1][0] + G[0][1] * G[1][1] + G[0][2] * G[1][2];
     b02 = G[0][0] * G[2][0] + G[0][1] * G[2][1] + G[0][2] * G[2][2];
     b12 = G[1][0] * G[2][0] + G[1][1] * G[2][1] + G[1][2] * G[2][2];
-    vB = b00 * b11 - b01 * b01 + b00 * b22 - b02 * b02 + b11 * b22 - b12 * b12;
+    R vB = b00 * b11 - b01 * b01 + b00 * b22 - b02 * b02 + b11 * b22 - b12 * b12;
     if (vA > (R)0 && vB > (R)0) {
       vactive = true;
       R h2 = M::rcp(rh * rh);
@@ -302,12 +307,13 @@ __device__ __forceinline__ void element_vjp(const R c[3][3], R inv_det, R rh, co
       mu_eff = P.mu + vscale * vphi;
     }
   }
-  const R k1 = P.c1 * mu_eff * rh * rh;
-  const R k2 = P.c2 * P.rho * rh;
+  const R rh2 = rh * rh;
+  const R k1 = (P.c1 * mu_eff) * rh2;
+  const R k2 = (P.c2 * P.rho) * rh;
   R bS[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) bS[i] = (R)kQB * S[i];
-  R tau[4], nrm[4];
+  R tau[4], yr[4];  // tau_g and 1/|u_g| (0 where u_g = 0)
   R stau = (R)0, T[3] = {(R)0, (R)0, (R)0};
   R Q00 = (R)0, Q11 = (R)0, Q22 = (R)0, Q01 = (R)0, Q02 = (R)0, Q12 = (R)0;
 #pragma unroll
@@ -316,8 +322,8 @@ __device__ __forceinline__ void element_vjp(const R c[3][3], R inv_det, R rh, co
 #pragma unroll
     for (int i = 0; i < 3; ++i) ug[i] = bS[i] + (R)(kQA - kQB) * u[g][i];
     R s = ug[0] * ug[0] + ug[1] * ug[1] + ug[2] * ug[2];
-    nrm[g] = M::sqrt_(s);
-    tau[g] = M::rcp(k1 + k2 * nrm[g]);
+    yr[g] = M::rsqrt_(s);
+    tau[g] = M::rcp(k2 * (s * yr[g]) + k1);
     stau += tau[g];
     R tu[3];
 #pragma unroll
@@ -332,12 +338,9 @@ __device__ __forceinline__ void element_vjp(const R c[3][3], R inv_det, R rh, co
     Q02 += tu[0] * ug[2];
     Q12 += tu[1] * ug[2];
   }
-  const R Qm[3][3] = {{Q00, Q01, Q02}, {Q01, Q11, Q12}, {Q02, Q12, Q22}};
 
   // ---- reverse ----
-  const R r24 = P.rho * P.rho * (R)0.25;
-  const R r4 = P.rho * (R)0.25;
-  // Omega = sum_a wm_a c_a^T = sum_k (wm_k - wm_0) c_k^T ; cw = sum_a wc_a c_a
+  // Omega = sum_a wm_a c_a^T and cw = sum_a wc_a c_a, with c_0 = -(c_1 + c_2 + c_3)
   R Om[3][3], cw[3];
   {
     R dw[3][4];
@@ -348,84 +351,111 @@ __device__ __forceinline__ void element_vjp(const R c[3][3], R inv_det, R rh, co
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-      for (int j = 0; j < 3; ++j) Om[i][j] = dw[0][i] * c[0][j] + dw[1][i] * c[1][j] + dw[2][i] * c[2][j];
+      for (int j = 0; j < 3; ++j)
+        Om[i][j] = dw[0][i] * c[0][j] + dw[1][i] * c[1][j] + dw[2][i] * c[2][j];
 #pragma unroll
     for (int j = 0; j < 3; ++j) cw[j] = dw[0][3] * c[0][j] + dw[1][3] * c[1][j] + dw[2][3] * c[2][j];
   }
   const R wcs = (w[0][3] + w[1][3]) + (w[2][3] + w[3][3]);
-  // Rbar = -(inv_det/24) cw ; pbarbar = tr(Omega)/6 ; Wbar = -(inv_det/6) Omega
-  const R s24 = inv_det * (R)(1.0 / 24.0);
   const R s6 = inv_det * (R)(1.0 / 6.0);
-  R Rb[3];
+  const R s24 = inv_det * (R)(1.0 / 24.0);
+  const R a1 = -s6 * mu_eff;
+  const R a2 = -s6 * (P.rho * P.rho * (R)0.25);
+  const R b4 = -s6 * (P.rho * (R)0.25);
+  // Rbar = -(inv_det/24) cw, Rq = rho Rbar
+  R Rb[3], Rq[3];
 #pragma unroll
-  for (int j = 0; j < 3; ++j) Rb[j] = -s24 * cw[j];
-  const R pbb = (Om[0][0] + Om[1][1] + Om[2][2]) * (R)(1.0 / 6.0);
-  R Wb[3][3];
+  for (int j = 0; j < 3; ++j) {
+    Rb[j] = -s24 * cw[j];
+    Rq[j] = P.rho * Rb[j];
+  }
+  // pressure mean: pbar-bar / 4 = tr(Omega)/24
+  const R pq = (Om[0][0] + Om[1][1] + Om[2][2]) * (R)(1.0 / 24.0);
+  // mu_eff-bar = <Wbar, G> with Wbar = -(inv_det/6) Omega
+  R mub;
+  {
+    R acc = Om[0][0] * G[0][0];
 #pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) Wb[i][j] = -s6 * Om[i][j];
-  // mu_eff-bar = <Wb, G>
-  R mub = (R)0;
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) mub += Wb[i][j] * G[i][j];
-  // Qbar = r24 G^T Wb ; symmetrised Qs = Qbar + Qbar^T
+    for (int q = 1; q < 9; ++q) acc = Om[q / 3][q % 3] * G[q / 3][q % 3] + acc;
+    mub = -s6 * acc;
+  }
+  // Qbar = a2 G^T Omega; symmetrised Qs = Qbar + Qbar^T
   R Qs[3][3];
   {
-    R Qb[3][3];
+    R Mt[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int j = 0; j < 3; ++j)
-        Qb[i][j] = r24 * (G[0][i] * Wb[0][j] + G[1][i] * Wb[1][j] + G[2][i] * Wb[2][j]);
+        Mt[i][j] = G[0][i] * Om[0][j] + G[1][i] * Om[1][j] + G[2][i] * Om[2][j];
+    const R a22 = a2 + a2;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) Qs[i][i] = a22 * Mt[i][i];
+    Qs[0][1] = Qs[1][0] = a2 * (Mt[0][1] + Mt[1][0]);
+    Qs[0][2] = Qs[2][0] = a2 * (Mt[0][2] + Mt[2][0]);
+    Qs[1][2] = Qs[2][1] = a2 * (Mt[1][2] + Mt[2][1]);
+  }
+  // Tbar = b4 Omega^T gph + G^T Rq ; staubar = Rbar . gph ; gpbar = b4 Omega T + stau Rbar
+  R Tb[3], gpb[3];
+  {
+    R gq[3], bT[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      gq[i] = b4 * gp[i];
+      bT[i] = b4 * T[i];
+    }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      R acc = Om[0][j] * gq[0];
+      acc = Om[1][j] * gq[1] + acc;
+      acc = Om[2][j] * gq[2] + acc;
+      acc = G[0][j] * Rq[0] + acc;
+      acc = G[1][j] * Rq[1] + acc;
+      Tb[j] = G[2][j] * Rq[2] + acc;
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      R acc = stau * Rb[i];
+      acc = Om[i][0] * bT[0] + acc;
+      acc = Om[i][1] * bT[1] + acc;
+      gpb[i] = Om[i][2] * bT[2] + acc;
+    }
+  }
+  const R staub = Rb[0] * gp[0] + Rb[1] * gp[1] + Rb[2] * gp[2];
+  // Gbar = Omega Qp' + Rq T^T + sum_a wm_a v_a^T - (sum_a wc_a)/24 I,
+  // Qp' = a2 Q + a1 I, v_a = -(rho/120)(u_a + S_u)
+  R Gb[3][3];
+  {
+    const R Qp[3][3] = {{a2 * Q00 + a1, a2 * Q01, a2 * Q02},
+                        {a2 * Q01, a2 * Q11 + a1, a2 * Q12},
+                        {a2 * Q02, a2 * Q12, a2 * Q22 + a1}};
+    const R m120 = P.rho * (R)(-1.0 / 120.0);
+    R v[4][3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const R mS = m120 * S[j];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) v[a][j] = m120 * u[a][j] + mS;
+    }
+    const R wc24 = wcs * (R)(1.0 / 24.0);
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-      for (int j = 0; j < 3; ++j) Qs[i][j] = Qb[i][j] + Qb[j][i];
+      for (int j = 0; j < 3; ++j) {
+        R acc = (i == j) ? Rq[i] * T[j] - wc24 : Rq[i] * T[j];
+        acc = Om[i][0] * Qp[0][j] + acc;
+        acc = Om[i][1] * Qp[1][j] + acc;
+        acc = Om[i][2] * Qp[2][j] + acc;
+        acc = w[0][i] * v[0][j] + acc;
+        acc = w[1][i] * v[1][j] + acc;
+        acc = w[2][i] * v[2][j] + acc;
+        Gb[i][j] = w[3][i] * v[3][j] + acc;
+      }
   }
-  // Tbar = r4 Wb^T gp + rho G^T Rb ; staubar = Rb.gp ; gpbar = r4 Wb T + stau Rb
-  R Tb[3], gpb[3];
-#pragma unroll
-  for (int j = 0; j < 3; ++j) {
-    Tb[j] = r4 * (Wb[0][j] * gp[0] + Wb[1][j] * gp[1] + Wb[2][j] * gp[2]) +
-            P.rho * (G[0][j] * Rb[0] + G[1][j] * Rb[1] + G[2][j] * Rb[2]);
-  }
-  const R staub = Rb[0] * gp[0] + Rb[1] * gp[1] + Rb[2] * gp[2];
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-    gpb[i] = r4 * (Wb[i][0] * T[0] + Wb[i][1] * T[1] + Wb[i][2] * T[2]) + stau * Rb[i];
-  // Gbar = mu_eff Wb + r24 Wb Q + rho Rb T^T - (rho/120) sum_a wm_a (S + u_a)^T - wcs/24 I
-  R Gb[3][3];
-  const R m120 = P.rho * (R)(-1.0 / 120.0);
-  R wms[3];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) wms[i] = (w[0][i] + w[1][i]) + (w[2][i] + w[3][i]);
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      R wu = w[0][i] * u[0][j] + w[1][i] * u[1][j] + w[2][i] * u[2][j] + w[3][i] * u[3][j];
-      Gb[i][j] = mu_eff * Wb[i][j] +
-                 r24 * (Wb[i][0] * Qm[0][j] + Wb[i][1] * Qm[1][j] + Wb[i][2] * Qm[2][j]) +
-                 P.rho * Rb[i] * T[j] + m120 * (wms[i] * S[j] + wu);
-    }
-  const R wc24 = wcs * (R)(1.0 / 24.0);
-  Gb[0][0] -= wc24;
-  Gb[1][1] -= wc24;
-  Gb[2][2] -= wc24;
-  // Sbar = (rho/-120) G^T wms ; ubar_a = (rho/-120) G^T wm_a
-  R Sb[3];
-#pragma unroll
-  for (int j = 0; j < 3; ++j) Sb[j] = m120 * (G[0][j] * wms[0] + G[1][j] * wms[1] + G[2][j] * wms[2]);
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int j = 0; j < 3; ++j)
-      gu[a][j] = m120 * (G[0][j] * w[a][0] + G[1][j] * w[a][1] + G[2][j] * w[a][2]);
-  // Gauss points in reverse
-  const R crh2 = P.c1 * rh * rh;
+  // Gauss points in reverse: ugb_g = dL/du_g
+  R ugb[4][3];
+  R Usum[3] = {(R)0, (R)0, (R)0};
+  const R crh2 = P.c1 * rh2;
 #pragma unroll
   for (int g = 0; g < 4; ++g) {
     R ug[3];
@@ -434,57 +464,86 @@ __device__ __forceinline__ void element_vjp(const R c[3][3], R inv_det, R rh, co
     R Qu[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) Qu[i] = Qs[i][0] * ug[0] + Qs[i][1] * ug[1] + Qs[i][2] * ug[2];
-    // tau-bar: Q enters as ug^T Qbar ug = ug . (Qs ug)/2
-    R taub = staub + Tb[0] * ug[0] + Tb[1] * ug[1] + Tb[2] * ug[2] +
-                  (R)0.5 * (ug[0] * Qu[0] + ug[1] * Qu[1] + ug[2] * Qu[2]);
-    R db = -tau[g] * tau[g] * taub;
-    mub += crh2 * db;
-    R nb = k2 * db;
-    R sc = nrm[g] > (R)0 ? nb * M::rcp(nrm[g]) : (R)0;
-    R ugb[3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) ugb[i] = tau[g] * (Tb[i] + Qu[i]) + sc * ug[i];
+    // tau-bar: Q enters as ug^T Qbar ug = ug . (Qs ug) / 2
+    R taub = Tb[0] * ug[0] + staub;
+    taub = Tb[1] * ug[1] + taub;
+    taub = Tb[2] * ug[2] + taub;
+    taub = (R)0.5 * (ug[0] * Qu[0] + ug[1] * Qu[1] + ug[2] * Qu[2]) + taub;
+    const R db = -(tau[g] * tau[g]) * taub;  // d(1/d)
+    mub = crh2 * db + mub;
+    const R sc = (k2 * yr[g]) * db;           // d|u_g| / du_g = u_g / |u_g|
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      Sb[i] += (R)kQB * ugb[i];
-      gu[g][i] += (R)(kQA - kQB) * ugb[i];
+      R acc = sc * ug[i];
+      acc = tau[g] * Tb[i] + acc;
+      ugb[g][i] = tau[g] * Qu[i] + acc;
+      Usum[i] += ugb[g][i];
     }
   }
-  // Vreman: mu_eff = mu + vscale sqrt(B/A)
+  // Vreman: mu_eff = mu + vscale sqrt(B/A):
+  // d phi / d Gh = (P - phi^2 I) Gh / (phi A), P = tr(beta) I - beta
   if (VREMAN && vactive) {
-    // d phi / d Gh = (P - phi^2 I) Gh / (phi A), P = tr(beta) I - beta
     R f = mub * vscale * M::rcp(vphi * vA);
     R tb = b00 + b11 + b22;
     R phi2 = vphi * vphi;
     const R Pm[3][3] = {{tb - b00 - phi2, -b01, -b02},
-                             {-b01, tb - b11 - phi2, -b12},
-                             {-b02, -b12, tb - b22 - phi2}};
+                        {-b01, tb - b11 - phi2, -b12},
+                        {-b02, -b12, tb - b22 - phi2}};
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int j = 0; j < 3; ++j)
         Gb[i][j] += f * (Pm[i][0] * G[0][j] + Pm[i][1] * G[1][j] + Pm[i][2] * G[2][j]);
   }
-  // Gh = sum_a u_a c_a^T ; gph = sum_a p_a c_a ; S = sum u_a ; pbar = sum p_a / 4
-  R gpc[3], gus[3] = {(R)0, (R)0, (R)0};
+  // Gh = sum_a u_a c_a^T, S = sum_a u_a, u_g = QB S + (QA - QB) u_g, and the
+  // convection's -(rho/120) Gh (S + u_a): gu_a = Gb c_a + Sbar + Hm^T wm_a + (QA-QB) ugb_a
+  // with Hm = -(rho/120) Gh and Sbar = Hm^T sum_a wm_a + QB sum_g ugb_g.
+  {
+    const R m120 = P.rho * (R)(-1.0 / 120.0);
+    R Hm[3][3];
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    R pc = gpb[0] * c[k][0] + gpb[1] * c[k][1] + gpb[2] * c[k][2];
-    gpc[k] = pc;
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) Hm[i][j] = m120 * G[i][j];
+    R Sb[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      R acc = (R)kQB * Usum[j];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) acc = Hm[i][j] * ((w[0][i] + w[1][i]) + (w[2][i] + w[3][i])) + acc;
+      Sb[j] = acc;
+    }
+    R zsum[3] = {(R)0, (R)0, (R)0};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        R z = Gb[i][0] * c[k][0] + Gb[i][1] * c[k][1] + Gb[i][2] * c[k][2];
+        zsum[i] += z;
+        R acc = (R)(kQA - kQB) * ugb[k + 1][i] + (z + Sb[i]);
+        acc = Hm[0][i] * w[k + 1][0] + acc;
+        acc = Hm[1][i] * w[k + 1][1] + acc;
+        gu[k + 1][i] = Hm[2][i] * w[k + 1][2] + acc;
+      }
+    }
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      R gc = Gb[i][0] * c[k][0] + Gb[i][1] * c[k][1] + Gb[i][2] * c[k][2];
-      gu[k + 1][i] += gc + Sb[i];
-      gus[i] += gc;
+      R acc = (R)(kQA - kQB) * ugb[0][i] + (Sb[i] - zsum[i]);
+      acc = Hm[0][i] * w[0][0] + acc;
+      acc = Hm[1][i] * w[0][1] + acc;
+      gu[0][i] = Hm[2][i] * w[0][2] + acc;
     }
   }
+  // gph = sum_a p_a c_a, p_bar = sum_a p_a / 4
+  R gsum = (R)0;
 #pragma unroll
-  for (int i = 0; i < 3; ++i) gu[0][i] += Sb[i] - gus[i];
-  const R pq = pbb * (R)0.25;
-  gpo[1] = gpc[0] + pq;
-  gpo[2] = gpc[1] + pq;
-  gpo[3] = gpc[2] + pq;
-  gpo[0] = pq - (gpc[0] + gpc[1] + gpc[2]);
+  for (int k = 0; k < 3; ++k) {
+    R acc = gpb[0] * c[k][0] + pq;
+    acc = gpb[1] * c[k][1] + acc;
+    gpo[k + 1] = gpb[2] * c[k][2] + acc;
+    gsum += gpo[k + 1];
+  }
+  gpo[0] = (R)4 * pq - gsum;
 }
 
 }  // namespace nsrhs

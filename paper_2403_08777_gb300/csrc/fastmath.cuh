@@ -13,7 +13,7 @@
 // With seeds good to about 2^-20 the corrected results are within a few
 // units in the last place of the correctly rounded values (tests compare them
 // with CUDA's own division, sqrt and rcbrt). Each costs 3, 5 and 6 FP64
-// instructions.
+// instructions (the inverse square root, 5).
 //
 // Domains: rcp_pos and rcbrt_pos take finite x > 0 (the callers guarantee
 // it); sqrt_nonneg takes s >= 0 and returns 0 for zero and subnormal s.
@@ -64,6 +64,19 @@ __device__ __forceinline__ double sqrt_nonneg(double s) {
   return tiny ? 0.0 : r;
 }
 
+// 1/sqrt(s): seed y, e = 1 - s y^2, y' = y (1 + e/2 + 3 e^2/8); 0 for zero and
+// subnormal s (so that s * rsqrt_nonneg(s) = 0 there).
+__device__ __forceinline__ double rsqrt_nonneg(double s) {
+  const bool tiny = __double2hiint(s) < 0x00100000;
+  const double ss = tiny ? 1.0 : s;
+  double y;
+  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(ss));
+  const double e = fma(-ss, y * y, 1.0);
+  const double p = fma(0.375, e, 0.5);
+  const double r = fma(y * e, p, y);
+  return tiny ? 0.0 : r;
+}
+
 __device__ __forceinline__ double rcbrt_pos(double x) {
   const int hi = __double2hiint(x);
   const int ex = (hi >> 20) & 0x7ff;
@@ -84,6 +97,7 @@ inline double widen_f32(float f) { return (double)f; }
 inline double rcp_pos(double x) { return 1.0 / x; }
 inline double sqrt_nonneg(double s) { return s > 0.0 ? sqrt(s) : 0.0; }
 inline double rcbrt_pos(double x) { return 1.0 / cbrt(x); }
+inline double rsqrt_nonneg(double s) { return s > 0.0 ? 1.0 / sqrt(s) : 0.0; }
 
 #endif
 

@@ -29,13 +29,13 @@ struct nsrhs_mesh {
   int64_t n_nodes = 0, n_elems = 0;
   int device = 0;
   double* coords = nullptr;   // [3][N]
-  float2* coords_hl = nullptr;  // [3][N] (hi, lo) float pairs: hi + lo = coords to ~2^-48
   int32_t* conn = nullptr;    // [4][E], caller's element order
-  // Mixed form: elements split by aspect ratio, each list with its own
-  // contiguous connectivity so that a warp never mixes the two kinds.
-  int32_t* conn_lo = nullptr;  // [4][E_lo], AR <= threshold
-  int32_t* conn_hi = nullptr;  // [4][E_hi], AR > threshold
-  int64_t n_lo = 0, n_hi = 0;
+  // Element geometry computed once in double precision (cofactor vectors
+  // c[k][d] at rows 3k+d, then 1/detJ, then detJ^(-1/3)), [kGeomRows][E]:
+  // it depends on the mesh only, and one streamed 88-byte record costs far
+  // less on GB300 than the ~40 FP64 instructions that recompute it.
+  double* geom = nullptr;
+  float* geom_f = nullptr;    // the same rounded to float, for the mixed form
   nsrhs_mesh_info info{};
   std::vector<void*> allocations;
 };
@@ -53,6 +53,7 @@ bool is_live(const nsrhs_mesh* m) {
 }
 
 constexpr int kThreads = 128;
+constexpr int kGeomRows = 11;
 
 int sm_count(int device) {
   int n = 0;
@@ -301,25 +302,34 @@ nsrhs_status check_scratch_address(CheckPartial** out) {
   return NSRHS_OK;
 }
 
-// hl[i] = (hi, lo) with hi = float(x[i]), lo = float(x[i] - hi)
-__global__ void split_coords_kernel(int64_t n, const double* __restrict__ x,
-                                    float2* __restrict__ hl) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const double v = x[i];
-    const float hi = __double2float_rn(v);
-    hl[i] = make_float2(hi, __double2float_rn(v - (double)hi));
-  }
-}
-
-// conn_sub[a][i] = conn[a][idx[i]]
-__global__ void gather_conn_kernel(int64_t E, const int32_t* __restrict__ conn, int64_t n,
-                                   const int32_t* __restrict__ idx, int32_t* __restrict__ sub) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    int64_t e = idx[i];
+// Cached element geometry (setup): double cofactors, 1/detJ and detJ^(-1/3)
+// of every element, and their float roundings.
+__global__ void geometry_kernel(int64_t N, int64_t E, const double* __restrict__ coords,
+                                const int32_t* __restrict__ conn, double* __restrict__ geom,
+                                float* __restrict__ geom_f) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double X[4][3];
 #pragma unroll
-    for (int a = 0; a < 4; ++a) sub[a * n + i] = conn[a * E + e];
+    for (int a = 0; a < 4; ++a) {
+      const int64_t v = conn[a * E + e];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) X[a][d] = coords[d * N + v];
+    }
+    double c[3][3], inv_det, rh;
+    nsrhs::element_geometry<double, double>(X, c, inv_det, rh);
+    double g[kGeomRows];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int d = 0; d < 3; ++d) g[3 * k + d] = c[k][d];
+    g[9] = inv_det;
+    g[10] = rh;
+#pragma unroll
+    for (int q = 0; q < kGeomRows; ++q) {
+      geom[q * E + e] = g[q];
+      geom_f[q * E + e] = __double2float_rn(g[q]);
+    }
   }
 }
 
@@ -331,28 +341,39 @@ __device__ __forceinline__ T ldg(const T* p) {
   return __ldg(p);
 }
 
-// FP64 forward, one element per thread, immediate atomic scatter.
+template <class R>
+__device__ __forceinline__ void load_geometry(const R* __restrict__ geom, int64_t E, int64_t e,
+                                              R c[3][3], R& inv_det, R& rh) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) c[k][d] = ldg(geom + (3 * k + d) * E + e);
+  inv_det = ldg(geom + 9 * E + e);
+  rh = ldg(geom + 10 * E + e);
+}
+
+// FP64 forward, one element per thread: streamed connectivity and cached
+// geometry, gathered nodal (u, p), register-resident element arithmetic,
+// immediate atomic scatter of the 16 entries.
 template <bool VREMAN>
 __global__ void __launch_bounds__(kThreads)
     fwd_fp64_atomic_kernel(int64_t N, int64_t E, const int32_t* __restrict__ conn,
-                           const double* __restrict__ coords, const double* __restrict__ up,
+                           const double* __restrict__ geom, const double* __restrict__ up,
                            ElemParams<double> P, double* __restrict__ rhs) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E;
        e += (int64_t)gridDim.x * blockDim.x) {
     int32_t v[4];
 #pragma unroll
     for (int a = 0; a < 4; ++a) v[a] = ldg(conn + a * E + e);
-    double X[4][3], u[4][3], p[4];
+    double u[4][3], p[4];
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
-#pragma unroll
-      for (int d = 0; d < 3; ++d) X[a][d] = ldg(coords + d * N + v[a]);
 #pragma unroll
       for (int i = 0; i < 3; ++i) u[a][i] = ldg(up + i * N + v[a]);
       p[a] = ldg(up + 3 * N + v[a]);
     }
     double c[3][3], inv_det, rh;
-    nsrhs::element_geometry<double, double>(X, c, inv_det, rh);
+    load_geometry(geom, E, e, c, inv_det, rh);
     double F[4][4];
     nsrhs::element_rhs<double, VREMAN>(c, inv_det, rh, u, p, P, F);
 #pragma unroll
@@ -362,17 +383,14 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
-// Mixed form: float (u,p) and float element arithmetic, double global
-// accumulation. Edges: for elements with aspect ratio <= threshold from the
-// (hi, lo) float pairs of the coordinates, (hi_k - hi_0) + (lo_k - lo_0), with
-// float cofactors/determinant; for the others (HIGH_AR) from the double
-// coordinates, with double cofactors/determinant/inverse. Float results are
-// widened to double with integer operations (no FP64 conversions).
-template <bool HIGH_AR, bool VREMAN>
+// Mixed form: float (u, p) and float element arithmetic on the cached
+// geometry (computed in double for every element, so the determinant and
+// inverse of high-aspect-ratio elements are double-accurate), double global
+// accumulation; float results are widened to double with integer operations.
+template <bool VREMAN>
 __global__ void __launch_bounds__(kThreads)
     fwd_mixed_atomic_kernel(int64_t N, int64_t E, const int32_t* __restrict__ conn,
-                            const double* __restrict__ coords,
-                            const float2* __restrict__ coords_hl, const float* __restrict__ up,
+                            const float* __restrict__ geom_f, const float* __restrict__ up,
                             ElemParams<float> P, double* __restrict__ rhs) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E;
        e += (int64_t)gridDim.x * blockDim.x) {
@@ -387,27 +405,7 @@ __global__ void __launch_bounds__(kThreads)
       p[a] = ldg(up + 3 * N + v[a]);
     }
     float c[3][3], inv_det, rh;
-    if (HIGH_AR) {
-      double X[4][3];
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int d = 0; d < 3; ++d) X[a][d] = ldg(coords + d * N + v[a]);
-      nsrhs::element_geometry<float, double>(X, c, inv_det, rh);
-    } else {
-      float2 X[4][3];
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int d = 0; d < 3; ++d) X[a][d] = ldg(coords_hl + d * N + v[a]);
-      float ed[3][3];
-#pragma unroll
-      for (int k = 0; k < 3; ++k)
-#pragma unroll
-        for (int d = 0; d < 3; ++d)
-          ed[k][d] = (X[k + 1][d].x - X[0][d].x) + (X[k + 1][d].y - X[0][d].y);
-      nsrhs::element_geometry_from_edges<float, float>(ed, c, inv_det, rh);
-    }
+    load_geometry(geom_f, E, e, c, inv_det, rh);
     float F[4][4];
     nsrhs::element_rhs<float, VREMAN>(c, inv_det, rh, u, p, P, F);
 #pragma unroll
@@ -423,7 +421,7 @@ __global__ void __launch_bounds__(kThreads)
 template <bool VREMAN>
 __global__ void __launch_bounds__(kThreads)
     vjp_fp64_atomic_kernel(int64_t N, int64_t E, const int32_t* __restrict__ conn,
-                           const double* __restrict__ coords, const double* __restrict__ up,
+                           const double* __restrict__ geom, const double* __restrict__ up,
                            const double* __restrict__ cot, ElemParams<double> P,
                            double* __restrict__ grad) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E;
@@ -431,11 +429,9 @@ __global__ void __launch_bounds__(kThreads)
     int32_t v[4];
 #pragma unroll
     for (int a = 0; a < 4; ++a) v[a] = ldg(conn + a * E + e);
-    double X[4][3], u[4][3], p[4], w[4][4];
+    double u[4][3], p[4], w[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
-#pragma unroll
-      for (int d = 0; d < 3; ++d) X[a][d] = ldg(coords + d * N + v[a]);
 #pragma unroll
       for (int i = 0; i < 3; ++i) u[a][i] = ldg(up + i * N + v[a]);
       p[a] = ldg(up + 3 * N + v[a]);
@@ -443,7 +439,7 @@ __global__ void __launch_bounds__(kThreads)
       for (int k = 0; k < 4; ++k) w[a][k] = ldg(cot + k * N + v[a]);
     }
     double c[3][3], inv_det, rh;
-    nsrhs::element_geometry<double, double>(X, c, inv_det, rh);
+    load_geometry(geom, E, e, c, inv_det, rh);
     double gu[4][3], gp[4];
     nsrhs::element_vjp<double, VREMAN>(c, inv_det, rh, u, p, w, P, gu, gp);
 #pragma unroll
@@ -518,10 +514,6 @@ nsrhs_status mesh_build(nsrhs_mesh* m, const double* coords, const int32_t* conn
   if ((st = mesh_alloc(m, &m->conn, 4 * (size_t)E)) != NSRHS_OK) return st;
   NSRHS_TRY(cudaMemcpyAsync(m->coords, coords, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, s));
   NSRHS_TRY(cudaMemcpyAsync(m->conn, conn, sizeof(int32_t) * 4 * E, cudaMemcpyDeviceToDevice, s));
-  if ((st = mesh_alloc(m, &m->coords_hl, 3 * (size_t)N)) != NSRHS_OK) return st;
-  split_coords_kernel<<<grid_for(3 * N, m->device, 8), kThreads, 0, s>>>(3 * N, m->coords,
-                                                                         m->coords_hl);
-  NSRHS_TRY(cudaGetLastError());
 
   // Validation scratch (freed before returning).
   uint8_t* high_ar = nullptr;
@@ -536,7 +528,6 @@ nsrhs_status mesh_build(nsrhs_mesh* m, const double* coords, const int32_t* conn
   init.min_det_bits = (unsigned long long)0x7FF0000000000000ull;  // +inf
   init.max_ar_bits = 0ull;
   ValidateOut res{};
-  std::vector<uint8_t> flags;
   ce = cudaMemcpyAsync(vout, &init, sizeof(init), cudaMemcpyHostToDevice, s);
   if (ce == cudaSuccess) {
     validate_kernel<<<grid_for(E, m->device, 8), kThreads, 0, s>>>(N, E, m->coords, m->conn,
@@ -544,10 +535,6 @@ nsrhs_status mesh_build(nsrhs_mesh* m, const double* coords, const int32_t* conn
     ce = cudaGetLastError();
   }
   if (ce == cudaSuccess) ce = cudaMemcpyAsync(&res, vout, sizeof(res), cudaMemcpyDeviceToHost, s);
-  if (ce == cudaSuccess) {
-    flags.resize((size_t)E);
-    ce = cudaMemcpyAsync(flags.data(), high_ar, (size_t)E, cudaMemcpyDeviceToHost, s);
-  }
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
   cudaFree(high_ar);
   cudaFree(vout);
@@ -561,29 +548,13 @@ nsrhs_status mesh_build(nsrhs_mesh* m, const double* coords, const int32_t* conn
   m->info.max_ar = max_ar;
   m->info.n_high_ar = (int64_t)res.n_high_ar;
 
-  // Aspect-ratio lists for the mixed form (element order kept within each).
-  std::vector<int32_t> lo, hi;
-  lo.reserve((size_t)E);
-  for (int64_t e = 0; e < E; ++e) (flags[e] ? hi : lo).push_back((int32_t)e);
-  m->n_lo = (int64_t)lo.size();
-  m->n_hi = (int64_t)hi.size();
-  for (int pass = 0; pass < 2; ++pass) {
-    std::vector<int32_t>& idx = pass == 0 ? lo : hi;
-    int32_t** dst = pass == 0 ? &m->conn_lo : &m->conn_hi;
-    if (idx.empty()) continue;
-    if ((st = mesh_alloc(m, dst, 4 * idx.size())) != NSRHS_OK) return st;
-    int32_t* didx = nullptr;
-    NSRHS_TRY(cudaMalloc((void**)&didx, idx.size() * sizeof(int32_t)));
-    ce = cudaMemcpyAsync(didx, idx.data(), idx.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s);
-    if (ce == cudaSuccess) {
-      gather_conn_kernel<<<grid_for((int64_t)idx.size(), m->device, 8), kThreads, 0, s>>>(
-          E, m->conn, (int64_t)idx.size(), didx, *dst);
-      ce = cudaGetLastError();
-    }
-    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
-    cudaFree(didx);
-    if (ce != cudaSuccess) return cuda_status(ce);
-  }
+  // Cached geometry (double and float) of every element.
+  if ((st = mesh_alloc(m, &m->geom, kGeomRows * (size_t)E)) != NSRHS_OK) return st;
+  if ((st = mesh_alloc(m, &m->geom_f, kGeomRows * (size_t)E)) != NSRHS_OK) return st;
+  geometry_kernel<<<grid_for(E, m->device, 8), kThreads, 0, s>>>(N, E, m->coords, m->conn,
+                                                                 m->geom, m->geom_f);
+  NSRHS_TRY(cudaGetLastError());
+  NSRHS_TRY(cudaStreamSynchronize(s));
   m->info.n_nodes = N;
   m->info.n_elems = E;
   m->info.n_blocks = 0;
@@ -670,35 +641,21 @@ nsrhs_status nsrhs_assemble(const nsrhs_mesh* m, const nsrhs_params* p, const vo
   const int64_t N = m->n_nodes, E = m->n_elems;
   const bool vreman = p->c_vreman != 0.0;
   NSRHS_TRY(cudaMemsetAsync(rhs, 0, sizeof(double) * 4 * N, s));
+  unsigned grid = grid_for(E, m->device, 16);
   if (p->precision == NSRHS_FP64) {
     auto P = elem_params<double>(p);
     const double* u = (const double*)up;
-    unsigned grid = grid_for(E, m->device, 16);
     if (vreman)
-      fwd_fp64_atomic_kernel<true><<<grid, kThreads, 0, s>>>(N, E, m->conn, m->coords, u, P, rhs);
+      fwd_fp64_atomic_kernel<true><<<grid, kThreads, 0, s>>>(N, E, m->conn, m->geom, u, P, rhs);
     else
-      fwd_fp64_atomic_kernel<false><<<grid, kThreads, 0, s>>>(N, E, m->conn, m->coords, u, P, rhs);
+      fwd_fp64_atomic_kernel<false><<<grid, kThreads, 0, s>>>(N, E, m->conn, m->geom, u, P, rhs);
   } else {
     auto P = elem_params<float>(p);
     const float* u = (const float*)up;
-    if (m->n_lo > 0) {
-      unsigned grid = grid_for(m->n_lo, m->device, 16);
-      if (vreman)
-        fwd_mixed_atomic_kernel<false, true><<<grid, kThreads, 0, s>>>(
-            N, m->n_lo, m->conn_lo, m->coords, m->coords_hl, u, P, rhs);
-      else
-        fwd_mixed_atomic_kernel<false, false><<<grid, kThreads, 0, s>>>(
-            N, m->n_lo, m->conn_lo, m->coords, m->coords_hl, u, P, rhs);
-    }
-    if (m->n_hi > 0) {
-      unsigned grid = grid_for(m->n_hi, m->device, 16);
-      if (vreman)
-        fwd_mixed_atomic_kernel<true, true><<<grid, kThreads, 0, s>>>(
-            N, m->n_hi, m->conn_hi, m->coords, m->coords_hl, u, P, rhs);
-      else
-        fwd_mixed_atomic_kernel<true, false><<<grid, kThreads, 0, s>>>(
-            N, m->n_hi, m->conn_hi, m->coords, m->coords_hl, u, P, rhs);
-    }
+    if (vreman)
+      fwd_mixed_atomic_kernel<true><<<grid, kThreads, 0, s>>>(N, E, m->conn, m->geom_f, u, P, rhs);
+    else
+      fwd_mixed_atomic_kernel<false><<<grid, kThreads, 0, s>>>(N, E, m->conn, m->geom_f, u, P, rhs);
   }
   return cuda_status(cudaGetLastError());
 }
@@ -715,9 +672,9 @@ nsrhs_status nsrhs_assemble_vjp(const nsrhs_mesh* m, const nsrhs_params* p, cons
   auto P = elem_params<double>(p);
   unsigned grid = grid_for(E, m->device, 16);
   if (p->c_vreman != 0.0)
-    vjp_fp64_atomic_kernel<true><<<grid, kThreads, 0, s>>>(N, E, m->conn, m->coords, up, cot, P, grad);
+    vjp_fp64_atomic_kernel<true><<<grid, kThreads, 0, s>>>(N, E, m->conn, m->geom, up, cot, P, grad);
   else
-    vjp_fp64_atomic_kernel<false><<<grid, kThreads, 0, s>>>(N, E, m->conn, m->coords, up, cot, P, grad);
+    vjp_fp64_atomic_kernel<false><<<grid, kThreads, 0, s>>>(N, E, m->conn, m->geom, up, cot, P, grad);
   return cuda_status(cudaGetLastError());
 }
 

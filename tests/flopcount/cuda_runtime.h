@@ -7,4 +7,5 @@
 inline double rcbrt(double x) { return 1.0 / std::cbrt(x); }
 inline float rcbrtf(float x) { return 1.0f / std::cbrt(x); }
 inline float __frcp_rn(float x) { return 1.0f / x; }
+inline float rsqrtf(float x) { return 1.0f / std::sqrt(x); }
 using std::sqrt;

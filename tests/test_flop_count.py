@@ -30,7 +30,8 @@ def test_flop_census_matches_bench(tmp_path):
     got = {}
     for line in out.splitlines():
         m = re.match(r"(\w+) fwd (\d+) sfu \d+ vjp (\d+) sfu \d+", line)
-        got[m.group(1)] = (int(m.group(2)), int(m.group(3)))
+        if m:
+            got[m.group(1)] = (int(m.group(2)), int(m.group(3)))
     plain, vrem = bench_constants()
     assert got["plain"] == plain
     assert got["vreman"] == vrem
