@@ -1,0 +1,294 @@
+// Element blocks for shared-memory staged gathers and scatters.
+//
+// Setup (once per mesh): elements are put in Morton order of their centroids,
+// so that consecutive elements are close in space, and cut into blocks of
+// kBlockElems elements. For every block the sorted list of the distinct nodes
+// it touches, its local connectivity (an index into that list per element
+// and local node) and, per distinct node, the run of contribution slots
+// (slot = 4 * element-in-block + local node) that land on it are stored.
+//
+// Assembly (per call): one CTA per block loads the nodal values of its
+// distinct nodes once into shared memory, each thread computes one element
+// from shared memory, writes its 16 entries to shared memory, and each
+// distinct node's entries are summed in double precision in a fixed order
+// (its run) and added to the global RHS with one atomic per component. The
+// global atomics drop from 16 per element to 4 per (block, distinct node), and
+// the sums inside a block do not depend on scheduling.
+#pragma once
+
+#include <cstdint>
+#include <cstring>
+#include <cuda_runtime.h>
+
+#include "element.cuh"
+
+namespace nsrhs {
+
+constexpr int kBlockElems = 256;
+constexpr int kBlockSlots = 4 * kBlockElems;  // at most this many distinct nodes
+
+// ---- setup ----
+
+// Order-preserving map of doubles to unsigned 64-bit integers.
+__device__ __forceinline__ unsigned long long ordered_bits(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  return (b & 0x8000000000000000ull) ? ~b : (b | 0x8000000000000000ull);
+}
+__host__ __device__ __forceinline__ double from_ordered_bits(unsigned long long o) {
+  const unsigned long long b = (o & 0x8000000000000000ull) ? (o & 0x7fffffffffffffffull) : ~o;
+  double d;
+  memcpy(&d, &b, sizeof(d));
+  return d;
+}
+
+// box[0..2] = ordered min of x,y,z; box[3..5] = ordered max. Initialise box to
+// (~0, ~0, ~0, 0, 0, 0).
+__global__ void bbox_kernel(int64_t N, const double* __restrict__ coords,
+                            unsigned long long* __restrict__ box) {
+  unsigned long long lo[3] = {~0ull, ~0ull, ~0ull}, hi[3] = {0ull, 0ull, 0ull};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const unsigned long long o = ordered_bits(coords[d * N + i]);
+      lo[d] = o < lo[d] ? o : lo[d];
+      hi[d] = o > hi[d] ? o : hi[d];
+    }
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    atomicMin(box + d, lo[d]);
+    atomicMax(box + 3 + d, hi[d]);
+  }
+}
+
+__device__ __forceinline__ unsigned long long spread3(unsigned long long v) {
+  // 21 bits -> every third bit of 63
+  v &= 0x1fffffull;
+  v = (v | (v << 32)) & 0x1f00000000ffffull;
+  v = (v | (v << 16)) & 0x1f0000ff0000ffull;
+  v = (v | (v << 8)) & 0x100f00f00f00f00full;
+  v = (v | (v << 4)) & 0x10c30c30c30c30c3ull;
+  v = (v | (v << 2)) & 0x1249249249249249ull;
+  return v;
+}
+
+// key[e] = Morton code of the element centroid in the bounding box, id[e] = e.
+__global__ void morton_kernel(int64_t N, int64_t E, const double* __restrict__ coords,
+                              const int32_t* __restrict__ conn, double x0, double y0, double z0,
+                              double sx, double sy, double sz,
+                              unsigned long long* __restrict__ key, int32_t* __restrict__ id) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double cx = 0.0, cy = 0.0, cz = 0.0;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const int64_t v = conn[a * E + e];
+      cx += coords[v];
+      cy += coords[N + v];
+      cz += coords[2 * N + v];
+    }
+    const double q = 2097151.0;  // 2^21 - 1
+    const unsigned long long ix = (unsigned long long)fmin(fmax((0.25 * cx - x0) * sx, 0.0), q);
+    const unsigned long long iy = (unsigned long long)fmin(fmax((0.25 * cy - y0) * sy, 0.0), q);
+    const unsigned long long iz = (unsigned long long)fmin(fmax((0.25 * cz - z0) * sz, 0.0), q);
+    key[e] = spread3(ix) | (spread3(iy) << 1) | (spread3(iz) << 2);
+    id[e] = (int32_t)e;
+  }
+}
+
+// out[a][i] = in[a][perm[i]]
+__global__ void permute_conn_kernel(int64_t E, const int32_t* __restrict__ in,
+                                    const int32_t* __restrict__ perm, int32_t* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < E;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = perm[i];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) out[a * E + i] = in[a * E + e];
+  }
+}
+
+// Per block: sort its (node << 16 | slot) keys, find the distinct nodes.
+// pass 0 writes counts[b] = number of distinct nodes;
+// pass 1 (node_off = exclusive sum of counts) writes
+//   nodes[node_off[b] + j]        j-th distinct node (ascending)
+//   runs[node_off[b] + b + j]     first sorted position of node j (runs[.. + n] = #valid)
+//   slots[b * kBlockSlots + i]    slot of sorted position i
+//   lconn[a * E + e]              distinct-node index of (element e, local node a)
+__global__ void __launch_bounds__(kBlockElems)
+    block_plan_kernel(int pass, int64_t E, const int32_t* __restrict__ conn,
+                      int64_t* __restrict__ counts, const int64_t* __restrict__ node_off,
+                      int32_t* __restrict__ nodes, uint16_t* __restrict__ runs,
+                      uint16_t* __restrict__ slots, uint16_t* __restrict__ lconn) {
+  __shared__ unsigned long long key[kBlockSlots];
+  __shared__ int part[kBlockElems];
+  const int tid = threadIdx.x;
+  const int64_t b = blockIdx.x;
+  const int64_t e0 = b * kBlockElems;
+  for (int i = tid; i < kBlockSlots; i += kBlockElems) {
+    const int64_t e = e0 + (i >> 2);
+    key[i] = e < E ? (((unsigned long long)(uint32_t)conn[(int64_t)(i & 3) * E + e] << 16) |
+                      (unsigned long long)i)
+                   : ~0ull;
+  }
+  __syncthreads();
+  // bitonic sort, ascending
+  for (int k = 2; k <= kBlockSlots; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = tid; i < kBlockSlots; i += kBlockElems) {
+        const int ixj = i ^ j;
+        if (ixj > i) {
+          const unsigned long long a = key[i], c = key[ixj];
+          const bool up = (i & k) == 0;
+          if ((a > c) == up) {
+            key[i] = c;
+            key[ixj] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  // distinct-node flags: thread tid owns sorted positions 4 tid .. 4 tid + 3
+  int flag[4], local = 0;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int i = 4 * tid + r;
+    const unsigned long long kk = key[i];
+    const bool valid = kk != ~0ull;
+    flag[r] = valid && (i == 0 || (key[i - 1] >> 16) != (kk >> 16));
+    local += flag[r];
+  }
+  part[tid] = local;
+  __syncthreads();
+  // inclusive scan of part[] (Hillis-Steele)
+  for (int off = 1; off < kBlockElems; off <<= 1) {
+    const int v = tid >= off ? part[tid - off] : 0;
+    __syncthreads();
+    part[tid] += v;
+    __syncthreads();
+  }
+  const int n_distinct = part[kBlockElems - 1];
+  if (pass == 0) {
+    if (tid == 0) counts[b] = n_distinct;
+    return;
+  }
+  const int64_t off = node_off[b];
+  int u = part[tid] - local - 1;  // distinct index before this thread's first position
+  int n_valid_here = 0;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int i = 4 * tid + r;
+    const unsigned long long kk = key[i];
+    if (kk == ~0ull) continue;
+    ++n_valid_here;
+    u += flag[r];
+    const int slot = (int)(kk & 0xffffull);
+    slots[b * kBlockSlots + i] = (uint16_t)slot;
+    if (flag[r]) {
+      nodes[off + u] = (int32_t)(kk >> 16);
+      runs[off + b + u] = (uint16_t)i;
+    }
+    lconn[(int64_t)(slot & 3) * E + e0 + (slot >> 2)] = (uint16_t)u;
+  }
+  // number of valid positions = elements in the block * 4
+  if (tid == 0) {
+    const int64_t ne = (E - e0) < kBlockElems ? (E - e0) : kBlockElems;
+    runs[off + b + n_distinct] = (uint16_t)(4 * ne);
+  }
+  (void)n_valid_here;
+}
+
+// ---- assembly ----
+
+// Sum of a node's contributions. double: plain double sum. float: compensated
+// float sum (Knuth's TwoSum keeps the rounding error of every addition), which
+// carries about 48 bits, widened and added in double at the end; this keeps
+// the mixed form's accumulation double-accurate without FP64 instructions per
+// contribution.
+template <class R>
+struct NodeSum;
+template <>
+struct NodeSum<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double x) { s += x; }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct NodeSum<float> {
+  float s = 0.0f, c = 0.0f;
+  __device__ __forceinline__ void add(float x) {
+    const float t = s + x;
+    const float bp = t - s;
+    c += (s - (t - bp)) + (x - bp);
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return widen_f32(s) + widen_f32(c); }
+};
+
+// Forward assembly with block-staged gathers and scatters; R is the element
+// arithmetic type (float: mixed form, double: FP64 form). Dynamic shared
+// memory: 8 * kBlockSlots * sizeof(R) bytes.
+template <class R, bool VREMAN>
+__global__ void __launch_bounds__(kBlockElems)
+    fwd_block_kernel(int64_t N, int64_t E, int64_t n_blocks, const int64_t* __restrict__ node_off,
+                     const int32_t* __restrict__ nodes, const uint16_t* __restrict__ runs,
+                     const uint16_t* __restrict__ slots, const uint16_t* __restrict__ lconn,
+                     const R* __restrict__ geom, const R* __restrict__ up, ElemParams<R> P,
+                     double* __restrict__ rhs) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R* su = reinterpret_cast<R*>(smem_raw);  // [4][kBlockSlots] nodal u, v, w, p
+  R* sF = su + 4 * kBlockSlots;             // [4][kBlockSlots] element entries by slot
+  const int tid = threadIdx.x;
+  for (int64_t b = blockIdx.x; b < n_blocks; b += gridDim.x) {
+    const int64_t off = node_off[b];
+    const int nb = (int)(node_off[b + 1] - off);
+    for (int j = tid; j < nb; j += kBlockElems) {
+      const int64_t v = __ldg(nodes + off + j);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) su[k * kBlockSlots + j] = __ldg(up + k * N + v);
+    }
+    __syncthreads();
+    const int64_t e = b * kBlockElems + tid;
+    if (e < E) {
+      int lc[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) lc[a] = __ldg(lconn + a * E + e);
+      R u[4][3], p[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) u[a][i] = su[i * kBlockSlots + lc[a]];
+        p[a] = su[3 * kBlockSlots + lc[a]];
+      }
+      R c[3][3], inv_det, rh;
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) c[k][d] = __ldg(geom + (3 * k + d) * E + e);
+      inv_det = __ldg(geom + 9 * E + e);
+      rh = __ldg(geom + 10 * E + e);
+      R F[4][4];
+      element_rhs<R, VREMAN>(c, inv_det, rh, u, p, P, F);
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) sF[k * kBlockSlots + 4 * tid + a] = F[a][k];
+    }
+    __syncthreads();
+    const uint16_t* bslots = slots + b * kBlockSlots;
+    for (int j = tid; j < nb; j += kBlockElems) {
+      const int r0 = __ldg(runs + off + b + j), r1 = __ldg(runs + off + b + j + 1);
+      const int64_t v = __ldg(nodes + off + j);
+      NodeSum<R> acc[4];
+      for (int q = r0; q < r1; ++q) {
+        const int sl = __ldg(bslots + q);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc[k].add(sF[k * kBlockSlots + sl]);
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) atomicAdd(rhs + k * N + v, acc[k].value());
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace nsrhs

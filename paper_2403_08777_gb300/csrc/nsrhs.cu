@@ -22,7 +22,10 @@
 #include <unordered_set>
 #include <vector>
 
+#include <cub/cub.cuh>
+
 #include "../../include/nsrhs.h"
+#include "blocks.cuh"
 #include "element.cuh"
 
 struct nsrhs_mesh {
@@ -36,6 +39,15 @@ struct nsrhs_mesh {
   // less on GB300 than the ~40 FP64 instructions that recompute it.
   double* geom = nullptr;
   float* geom_f = nullptr;    // the same rounded to float, for the mixed form
+  // Element blocks (blocks.cuh): elements are stored in Morton order of
+  // their centroids; per block of kBlockElems elements its distinct nodes,
+  // their contribution runs and the local connectivity.
+  int64_t n_blocks = 0;
+  int64_t* blk_node_off = nullptr;  // [n_blocks + 1]
+  int32_t* blk_nodes = nullptr;     // [blk_node_off[n_blocks]]
+  uint16_t* blk_runs = nullptr;     // [blk_node_off[n_blocks] + n_blocks]
+  uint16_t* blk_slots = nullptr;    // [n_blocks * kBlockSlots]
+  uint16_t* blk_lconn = nullptr;    // [4][E]
   nsrhs_mesh_info info{};
   std::vector<void*> allocations;
 };
@@ -506,6 +518,99 @@ nsrhs_status mesh_alloc(nsrhs_mesh* m, T** ptr, size_t count) {
   return NSRHS_OK;
 }
 
+// Scoped device buffer for setup temporaries.
+struct DevBuf {
+  void* p = nullptr;
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+  cudaError_t alloc(size_t bytes) { return cudaMalloc(&p, bytes ? bytes : 1); }
+  template <class T>
+  T* as() const {
+    return static_cast<T*>(p);
+  }
+};
+
+nsrhs_status morton_reorder(nsrhs_mesh* m, cudaStream_t s) {
+  const int64_t N = m->n_nodes, E = m->n_elems;
+  DevBuf box, keys, keys2, ids, ids2, tmp, conn2;
+  NSRHS_TRY(box.alloc(6 * sizeof(unsigned long long)));
+  const unsigned long long init[6] = {~0ull, ~0ull, ~0ull, 0ull, 0ull, 0ull};
+  NSRHS_TRY(cudaMemcpyAsync(box.p, init, sizeof(init), cudaMemcpyHostToDevice, s));
+  nsrhs::bbox_kernel<<<grid_for(N, m->device, 4), kThreads, 0, s>>>(N, m->coords,
+                                                                    box.as<unsigned long long>());
+  NSRHS_TRY(cudaGetLastError());
+  unsigned long long hb[6];
+  NSRHS_TRY(cudaMemcpyAsync(hb, box.p, sizeof(hb), cudaMemcpyDeviceToHost, s));
+  NSRHS_TRY(cudaStreamSynchronize(s));
+  double lo[3], sc[3];
+  for (int d = 0; d < 3; ++d) {
+    lo[d] = nsrhs::from_ordered_bits(hb[d]);
+    const double ext = nsrhs::from_ordered_bits(hb[3 + d]) - lo[d];
+    sc[d] = ext > 0.0 ? 2097151.0 / ext : 0.0;
+  }
+  NSRHS_TRY(keys.alloc(E * sizeof(unsigned long long)));
+  NSRHS_TRY(keys2.alloc(E * sizeof(unsigned long long)));
+  NSRHS_TRY(ids.alloc(E * sizeof(int32_t)));
+  NSRHS_TRY(ids2.alloc(E * sizeof(int32_t)));
+  nsrhs::morton_kernel<<<grid_for(E, m->device, 8), kThreads, 0, s>>>(
+      N, E, m->coords, m->conn, lo[0], lo[1], lo[2], sc[0], sc[1], sc[2],
+      keys.as<unsigned long long>(), ids.as<int32_t>());
+  NSRHS_TRY(cudaGetLastError());
+  size_t tmp_bytes = 0;
+  NSRHS_TRY(cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, keys.as<unsigned long long>(),
+                                            keys2.as<unsigned long long>(), ids.as<int32_t>(),
+                                            ids2.as<int32_t>(), (int)E, 0, 63, s));
+  NSRHS_TRY(tmp.alloc(tmp_bytes));
+  NSRHS_TRY(cub::DeviceRadixSort::SortPairs(tmp.p, tmp_bytes, keys.as<unsigned long long>(),
+                                            keys2.as<unsigned long long>(), ids.as<int32_t>(),
+                                            ids2.as<int32_t>(), (int)E, 0, 63, s));
+  NSRHS_TRY(conn2.alloc(4 * E * sizeof(int32_t)));
+  nsrhs::permute_conn_kernel<<<grid_for(E, m->device, 8), kThreads, 0, s>>>(
+      E, m->conn, ids2.as<int32_t>(), conn2.as<int32_t>());
+  NSRHS_TRY(cudaGetLastError());
+  NSRHS_TRY(cudaMemcpyAsync(m->conn, conn2.p, 4 * E * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+  NSRHS_TRY(cudaStreamSynchronize(s));
+  return NSRHS_OK;
+}
+
+nsrhs_status build_blocks(nsrhs_mesh* m, cudaStream_t s) {
+  const int64_t E = m->n_elems;
+  const int64_t nb = (E + nsrhs::kBlockElems - 1) / nsrhs::kBlockElems;
+  if (nb > INT32_MAX) return NSRHS_EINVAL;
+  m->n_blocks = nb;
+  nsrhs_status st;
+  DevBuf counts, tmp;
+  NSRHS_TRY(counts.alloc((nb + 1) * sizeof(int64_t)));
+  if ((st = mesh_alloc(m, &m->blk_node_off, (size_t)nb + 1)) != NSRHS_OK) return st;
+  if ((st = mesh_alloc(m, &m->blk_lconn, 4 * (size_t)E)) != NSRHS_OK) return st;
+  if ((st = mesh_alloc(m, &m->blk_slots, (size_t)nb * nsrhs::kBlockSlots)) != NSRHS_OK) return st;
+  // pass 0: distinct nodes per block
+  nsrhs::block_plan_kernel<<<(unsigned)nb, nsrhs::kBlockElems, 0, s>>>(
+      0, E, m->conn, counts.as<int64_t>(), nullptr, nullptr, nullptr, nullptr, nullptr);
+  NSRHS_TRY(cudaGetLastError());
+  // node_off = exclusive prefix sum of the counts (counts[nb] = 0)
+  {
+    NSRHS_TRY(cudaMemsetAsync(counts.as<int64_t>() + nb, 0, sizeof(int64_t), s));
+    size_t tmp_bytes = 0;
+    NSRHS_TRY(cub::DeviceScan::ExclusiveSum(nullptr, tmp_bytes, counts.as<int64_t>(),
+                                            m->blk_node_off, (int)nb + 1, s));
+    NSRHS_TRY(tmp.alloc(tmp_bytes));
+    NSRHS_TRY(cub::DeviceScan::ExclusiveSum(tmp.p, tmp_bytes, counts.as<int64_t>(),
+                                            m->blk_node_off, (int)nb + 1, s));
+  }
+  int64_t total = 0;
+  NSRHS_TRY(cudaMemcpyAsync(&total, m->blk_node_off + nb, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  NSRHS_TRY(cudaStreamSynchronize(s));
+  if ((st = mesh_alloc(m, &m->blk_nodes, (size_t)total)) != NSRHS_OK) return st;
+  if ((st = mesh_alloc(m, &m->blk_runs, (size_t)(total + nb))) != NSRHS_OK) return st;
+  nsrhs::block_plan_kernel<<<(unsigned)nb, nsrhs::kBlockElems, 0, s>>>(
+      1, E, m->conn, nullptr, m->blk_node_off, m->blk_nodes, m->blk_runs, m->blk_slots,
+      m->blk_lconn);
+  NSRHS_TRY(cudaGetLastError());
+  return NSRHS_OK;
+}
+
 nsrhs_status mesh_build(nsrhs_mesh* m, const double* coords, const int32_t* conn,
                         const nsrhs_mesh_opts& opts, cudaStream_t s) {
   const int64_t N = m->n_nodes, E = m->n_elems;
@@ -548,17 +653,21 @@ nsrhs_status mesh_build(nsrhs_mesh* m, const double* coords, const int32_t* conn
   m->info.max_ar = max_ar;
   m->info.n_high_ar = (int64_t)res.n_high_ar;
 
+  // Morton order of the element centroids (the RHS does not depend on the
+  // element order, up to rounding).
+  if ((st = morton_reorder(m, s)) != NSRHS_OK) return st;
   // Cached geometry (double and float) of every element.
   if ((st = mesh_alloc(m, &m->geom, kGeomRows * (size_t)E)) != NSRHS_OK) return st;
   if ((st = mesh_alloc(m, &m->geom_f, kGeomRows * (size_t)E)) != NSRHS_OK) return st;
   geometry_kernel<<<grid_for(E, m->device, 8), kThreads, 0, s>>>(N, E, m->coords, m->conn,
                                                                  m->geom, m->geom_f);
   NSRHS_TRY(cudaGetLastError());
+  if ((st = build_blocks(m, s)) != NSRHS_OK) return st;
   NSRHS_TRY(cudaStreamSynchronize(s));
   m->info.n_nodes = N;
   m->info.n_elems = E;
-  m->info.n_blocks = 0;
-  m->info.block_elems = 0;
+  m->info.n_blocks = m->n_blocks;
+  m->info.block_elems = nsrhs::kBlockElems;
   return NSRHS_OK;
 }
 
@@ -641,6 +750,33 @@ nsrhs_status nsrhs_assemble(const nsrhs_mesh* m, const nsrhs_params* p, const vo
   const int64_t N = m->n_nodes, E = m->n_elems;
   const bool vreman = p->c_vreman != 0.0;
   NSRHS_TRY(cudaMemsetAsync(rhs, 0, sizeof(double) * 4 * N, s));
+  // AUTO: atomics for the FP64 form (its FP64 pipe, not the scatter, is the
+  // limit, and the block sums would add FP64 work); blocks for the mixed form
+  // (bound by L2 atomics and gathers).
+  const bool block = p->scatter == NSRHS_SCATTER_BLOCK ||
+                     (p->scatter == NSRHS_SCATTER_AUTO && p->precision == NSRHS_MIXED);
+  if (block) {
+    const int64_t nb = m->n_blocks;
+    const unsigned grid = (unsigned)std::max<int64_t>(
+        1, std::min<int64_t>(nb, (int64_t)sm_count(m->device) * 4));
+    if (p->precision == NSRHS_FP64) {
+      auto P = elem_params<double>(p);
+      const size_t smem = 8 * nsrhs::kBlockSlots * sizeof(double);
+      auto kern = vreman ? nsrhs::fwd_block_kernel<double, true> : nsrhs::fwd_block_kernel<double, false>;
+      NSRHS_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      kern<<<grid, nsrhs::kBlockElems, smem, s>>>(N, E, nb, m->blk_node_off, m->blk_nodes,
+                                                  m->blk_runs, m->blk_slots, m->blk_lconn, m->geom,
+                                                  (const double*)up, P, rhs);
+    } else {
+      auto P = elem_params<float>(p);
+      const size_t smem = 8 * nsrhs::kBlockSlots * sizeof(float);
+      auto kern = vreman ? nsrhs::fwd_block_kernel<float, true> : nsrhs::fwd_block_kernel<float, false>;
+      kern<<<grid, nsrhs::kBlockElems, smem, s>>>(N, E, nb, m->blk_node_off, m->blk_nodes,
+                                                  m->blk_runs, m->blk_slots, m->blk_lconn,
+                                                  m->geom_f, (const float*)up, P, rhs);
+    }
+    return cuda_status(cudaGetLastError());
+  }
   unsigned grid = grid_for(E, m->device, 16);
   if (p->precision == NSRHS_FP64) {
     auto P = elem_params<double>(p);

@@ -70,10 +70,12 @@ FWD_CASES = [
 def test_fp64_forward_matches_oracle(dev, n, jitter, order, mu, mag, cv):
     w = mg.make_workload(n, jitter=jitter, order=order, mu=mu, mag_max=mag, c_vreman=cv)
     ref = oracle.assemble(w.coords, w.conn, w.up, w.rho, w.mu, c_vreman=cv)
-    for scatter in ("auto", "atomic"):
+    for scatter in ("auto", "atomic", "block"):
         x, mesh = gpu_rhs(dev, w, ns.Params(rho=w.rho, mu=w.mu, c_vreman=cv, scatter=scatter))
         check_fp64(x, ref)
-    mesh.close()
+        info = mesh.info()
+        assert info["n_blocks"] == (w.n_elems + 255) // 256 and info["block_elems"] == 256
+        mesh.close()
 
 
 def test_fp64_forward_64cube_and_renumbering(dev):
@@ -96,12 +98,17 @@ def test_ragged_element_counts(dev):
     """Meshes of 1, 31, 127, 128, 129 and 1000 elements (prefixes of a mesh,
     with nodes left unused)."""
     w = mg.make_workload(6, jitter=0.2, order="random")
-    for E in (1, 31, 127, 128, 129, 1000):
+    for E in (1, 31, 127, 128, 129, 255, 256, 257, 1000):
         sub = mg.Workload("sub", 6, w.coords, np.ascontiguousarray(w.conn[:, :E]), w.up, 1.0, 1e-2)
         ref = oracle.assemble(sub.coords, sub.conn, sub.up, 1.0, 1e-2)
-        x, m = gpu_rhs(dev, sub)
-        check_fp64(x, ref)
-        m.close()
+        for scatter in ("atomic", "block"):
+            x, m = gpu_rhs(dev, sub, ns.Params(rho=1.0, mu=1e-2, scatter=scatter))
+            check_fp64(x, ref)
+            m.close()
+            x, m = gpu_rhs(dev, sub, ns.Params(rho=1.0, mu=1e-2, scatter=scatter,
+                                                precision="mixed"))
+            assert relerr(x, ref) <= TOL_MIXED
+            m.close()
 
 
 def test_single_reference_tet_closed_form(dev):
@@ -122,11 +129,13 @@ def test_single_reference_tet_closed_form(dev):
 def test_mixed_precision_error(dev, n, cv):
     w = mg.make_workload(n, jitter=0.3, order="rcm", mu=1e-4, mag_max=10.0, c_vreman=cv)
     ref = oracle.assemble(w.coords, w.conn, w.up, w.rho, w.mu, c_vreman=cv)
-    x, m = gpu_rhs(dev, w, ns.Params(rho=w.rho, mu=w.mu, c_vreman=cv, precision="mixed"))
-    info = m.info()
-    assert info["n_high_ar"] > 0            # the jitter-0.3 mesh has AR > 10 elements
-    assert relerr(x, ref) <= TOL_MIXED, relerr(x, ref)
-    m.close()
+    for scatter in ("auto", "atomic", "block"):
+        x, m = gpu_rhs(dev, w, ns.Params(rho=w.rho, mu=w.mu, c_vreman=cv, precision="mixed",
+                                         scatter=scatter))
+        info = m.info()
+        assert info["n_high_ar"] > 0            # the jitter-0.3 mesh has AR > 10 elements
+        assert relerr(x, ref) <= TOL_MIXED, (scatter, relerr(x, ref))
+        m.close()
 
 
 @pytest.mark.parametrize("n,order,cv", [(8, "lex", 0.0), (8, "lex", 0.07), (20, "random", 0.0),
