@@ -20,8 +20,8 @@ import torch
 from . import _abi
 from ._abi import NSRHSError, NativeLibraryMissing  # noqa: F401
 
-__all__ = ["Mesh", "Params", "assemble", "NSRHSFunction", "NSRHSError", "NativeLibraryMissing",
-           "load_library"]
+__all__ = ["Mesh", "Params", "assemble", "assemble_host", "StepPipeline", "NSRHSFunction",
+           "NSRHSError", "NativeLibraryMissing", "load_library"]
 
 _PREC = {"fp64": _abi.FP64, "mixed": _abi.MIXED}
 _SCAT = {"auto": _abi.SCATTER_AUTO, "atomic": _abi.SCATTER_ATOMIC, "block": _abi.SCATTER_BLOCK}
@@ -197,3 +197,70 @@ def assemble_host(mesh: Mesh, up_host: torch.Tensor, params: Params | None = Non
     out_host.copy_(rhs, non_blocking=True)
     torch.cuda.current_stream(mesh.device).synchronize()
     return out_host
+
+
+class StepPipeline:
+    """Repeated steps on HOST buffers — copy (u, p) and the cotangent in,
+    assemble, run the adjoint, copy the RHS and the gradient out — with the
+    copies of one step overlapped with the compute of its neighbours (two
+    device buffer sets, separate copy-in, compute and copy-out streams).
+
+        pipe = StepPipeline(mesh, params)
+        for k in range(n):
+            pipe.submit(k, up_host, cot_host, rhs_host[k % 2], grad_host[k % 2])
+        pipe.synchronize()
+
+    Host tensors should be pinned for the copies to be asynchronous. A host
+    output passed to step k may be read after step k + 2 has been submitted
+    or after synchronize(). cot_host / grad_host may be None (forward only).
+    """
+
+    def __init__(self, mesh: Mesh, params: Params | None = None, **kw):
+        self.mesh = mesh
+        self.params = mesh._params(params, kw)
+        if self.params.precision != "fp64":
+            raise ValueError("StepPipeline runs the fp64 forward and adjoint")
+        dev = mesh.device
+        self.s_in = torch.cuda.Stream(dev)
+        self.s_cmp = torch.cuda.Stream(dev)
+        self.s_out = torch.cuda.Stream(dev)
+        shape = (4, mesh.n_nodes)
+        self.sets = []
+        for _ in range(2):
+            self.sets.append({
+                "up": torch.empty(shape, dtype=torch.float64, device=dev),
+                "cot": torch.empty(shape, dtype=torch.float64, device=dev),
+                "rhs": torch.empty(shape, dtype=torch.float64, device=dev),
+                "grad": torch.empty(shape, dtype=torch.float64, device=dev),
+                "loaded": torch.cuda.Event(), "fwd": torch.cuda.Event(),
+                "done": torch.cuda.Event(), "free": torch.cuda.Event(), "used": False})
+
+    def submit(self, k: int, up_host: torch.Tensor, cot_host: torch.Tensor | None,
+               rhs_host: torch.Tensor, grad_host: torch.Tensor | None) -> None:
+        b = self.sets[k % 2]
+        with torch.cuda.stream(self.s_in):
+            if b["used"]:
+                self.s_in.wait_event(b["free"])
+            b["up"].copy_(up_host, non_blocking=True)
+            if cot_host is not None:
+                b["cot"].copy_(cot_host, non_blocking=True)
+            b["loaded"].record(self.s_in)
+        with torch.cuda.stream(self.s_cmp):
+            self.s_cmp.wait_event(b["loaded"])
+            self.mesh.assemble(b["up"], self.params, out=b["rhs"])
+            b["fwd"].record(self.s_cmp)
+            if cot_host is not None:
+                self.mesh.assemble_vjp(b["up"], b["cot"], self.params, out=b["grad"])
+            b["done"].record(self.s_cmp)
+        with torch.cuda.stream(self.s_out):
+            self.s_out.wait_event(b["fwd"])
+            rhs_host.copy_(b["rhs"], non_blocking=True)
+            self.s_out.wait_event(b["done"])
+            if cot_host is not None:
+                grad_host.copy_(b["grad"], non_blocking=True)
+            b["free"].record(self.s_out)
+        b["used"] = True
+
+    def synchronize(self) -> None:
+        for st in (self.s_in, self.s_cmp, self.s_out):
+            st.synchronize()
