@@ -227,8 +227,16 @@ struct NodeSum<float> {
 // Forward assembly with block-staged gathers and scatters; R is the element
 // arithmetic type (float: mixed form, double: FP64 form). Dynamic shared
 // memory: 8 * kBlockSlots * sizeof(R) bytes.
+// Resident CTAs per SM the compiler must allow (register cap): the float
+// kernel is latency-bound between its barrier-separated phases, so more CTAs
+// per SM help; the double kernel is bound by the FP64 pipe.
+template <class R>
+constexpr int block_kernel_min_ctas() {
+  return sizeof(R) == 4 ? 4 : 2;
+}
+
 template <class R, bool VREMAN>
-__global__ void __launch_bounds__(kBlockElems)
+__global__ void __launch_bounds__(kBlockElems, block_kernel_min_ctas<R>())
     fwd_block_kernel(int64_t N, int64_t E, int64_t n_blocks, const int64_t* __restrict__ node_off,
                      const int32_t* __restrict__ nodes, const uint16_t* __restrict__ runs,
                      const uint16_t* __restrict__ slots, const uint16_t* __restrict__ lconn,
