@@ -61,8 +61,8 @@ def _p(a):
     return a.ctypes.data_as(ctypes.c_void_p)
 
 
-def _params(rho, mu, c_vreman=0.0, c1=C1, c2=C2):
-    return np.array([rho, mu, c_vreman, c1, c2], np.float64)
+def _params(rho, mu, c_vreman=0.0, c1=C1, c2=C2, skew=False, tau_elem=False):
+    return np.array([rho, mu, c_vreman, c1, c2, float(skew), float(tau_elem)], np.float64)
 
 
 def _check(r, what):
@@ -70,30 +70,31 @@ def _check(r, what):
         raise ValueError(f"{what}: oracle status {r} ({'bad arguments' if r == 1 else 'bad mesh'})")
 
 
-def element(X, U, rho, mu, c_vreman=0.0, terms=T_ALL, c1=C1, c2=C2):
+def element(X, U, rho, mu, c_vreman=0.0, terms=T_ALL, c1=C1, c2=C2, skew=False, tau_elem=False):
     """Element RHS F [4][4] (local node, (mom x, y, z, continuity)) of one tet.
     X [4][3] node coordinates, U [4][4] nodal (u, v, w, p)."""
     X = np.ascontiguousarray(X, np.float64)
     U = np.ascontiguousarray(U, np.float64)
     F = np.empty((4, 4), np.float64)
-    pr = _params(rho, mu, c_vreman, c1, c2)
+    pr = _params(rho, mu, c_vreman, c1, c2, skew, tau_elem)
     _check(_load().or_element_f64(_p(X), _p(U), _p(pr), terms, _p(F)), "element")
     return F
 
 
-def element_complex(X, U, rho, mu, c_vreman=0.0, terms=T_ALL, c1=C1, c2=C2):
+def element_complex(X, U, rho, mu, c_vreman=0.0, terms=T_ALL, c1=C1, c2=C2, skew=False,
+                    tau_elem=False):
     X = np.ascontiguousarray(X, np.float64)
     U = np.asarray(U, np.complex128)
     ur, ui = np.ascontiguousarray(U.real), np.ascontiguousarray(U.imag)
     Fr, Fi = np.empty((4, 4)), np.empty((4, 4))
-    pr = _params(rho, mu, c_vreman, c1, c2)
+    pr = _params(rho, mu, c_vreman, c1, c2, skew, tau_elem)
     _check(_load().or_element_c128(_p(X), _p(ur), _p(ui), _p(pr), terms, _p(Fr), _p(Fi)),
            "element_complex")
     return Fr + 1j * Fi
 
 
 def assemble(coords, conn, up, rho, mu, c_vreman=0.0, terms=T_ALL, e0=0, e1=None,
-             c1=C1, c2=C2):
+             c1=C1, c2=C2, skew=False, tau_elem=False):
     """Global RHS [4][N] (float64) over elements [e0, e1)."""
     coords = np.ascontiguousarray(coords, np.float64)
     conn = np.ascontiguousarray(conn, np.int32)
@@ -101,26 +102,27 @@ def assemble(coords, conn, up, rho, mu, c_vreman=0.0, terms=T_ALL, e0=0, e1=None
     N, E = coords.shape[1], conn.shape[1]
     e1 = E if e1 is None else e1
     rhs = np.empty((4, N), np.float64)
-    pr = _params(rho, mu, c_vreman, c1, c2)
+    pr = _params(rho, mu, c_vreman, c1, c2, skew, tau_elem)
     _check(_load().or_assemble_f64(N, E, _p(coords), _p(conn), _p(up), _p(pr), terms, e0, e1,
                                    _p(rhs)), "assemble")
     return rhs
 
 
-def assemble_complex(coords, conn, up, rho, mu, c_vreman=0.0, terms=T_ALL, c1=C1, c2=C2):
+def assemble_complex(coords, conn, up, rho, mu, c_vreman=0.0, terms=T_ALL, c1=C1, c2=C2,
+                     skew=False, tau_elem=False):
     coords = np.ascontiguousarray(coords, np.float64)
     conn = np.ascontiguousarray(conn, np.int32)
     up = np.asarray(up, np.complex128)
     ur, ui = np.ascontiguousarray(up.real), np.ascontiguousarray(up.imag)
     N, E = coords.shape[1], conn.shape[1]
     rr, ri = np.empty((4, N)), np.empty((4, N))
-    pr = _params(rho, mu, c_vreman, c1, c2)
+    pr = _params(rho, mu, c_vreman, c1, c2, skew, tau_elem)
     _check(_load().or_assemble_c128(N, E, _p(coords), _p(conn), _p(ur), _p(ui), _p(pr), terms,
                                     _p(rr), _p(ri)), "assemble_complex")
     return rr + 1j * ri
 
 
-def vjp(coords, conn, up, w, rho, mu, c_vreman=0.0, c1=C1, c2=C2):
+def vjp(coords, conn, up, w, rho, mu, c_vreman=0.0, c1=C1, c2=C2, skew=False, tau_elem=False):
     """(dRHS/dup)^T w as [4][N], element Jacobians by complex step."""
     coords = np.ascontiguousarray(coords, np.float64)
     conn = np.ascontiguousarray(conn, np.int32)
@@ -128,7 +130,7 @@ def vjp(coords, conn, up, w, rho, mu, c_vreman=0.0, c1=C1, c2=C2):
     w = np.ascontiguousarray(w, np.float64)
     N, E = coords.shape[1], conn.shape[1]
     g = np.empty((4, N), np.float64)
-    pr = _params(rho, mu, c_vreman, c1, c2)
+    pr = _params(rho, mu, c_vreman, c1, c2, skew, tau_elem)
     _check(_load().or_vjp_f64(N, E, _p(coords), _p(conn), _p(up), _p(w), _p(pr), _p(g)), "vjp")
     return g
 

@@ -20,6 +20,11 @@
 //  * the element RHS computed directly, without an element matrix (Sec. V-A);
 //  * SUPG/PSPG stabilisation with tau = 1/(c1 mu_eff/h^2 + c2 rho |u|/h) per
 //    Gauss point, h = detJ^(1/3).
+// Variants (off by default): the skew-symmetric Galerkin convection
+//   -rho/2 int[ N_a (u.grad)u_i - (u.grad N_a) u_i ]
+// whose convective RHS does no work on the discrete velocity (the
+// "energy-preserving" property named in Sec. II), and one tau per element
+// evaluated with the element-mean velocity.
 // For test function N_a of element e (volume V, u_h, p_h linear):
 //   F_a,i = int[ -rho N_a (u.grad)u_i - mu_eff grad N_a . grad u_i + p dN_a/dx_i
 //                - tau rho (u . grad N_a) (rho (u.grad)u_i + dp/dx_i) ]
@@ -38,8 +43,10 @@
 
 namespace {
 
-struct Params {  // mirrors the layout passed from Python (5 doubles)
+struct Params {  // mirrors the layout passed from Python (7 doubles)
   double rho, mu, c_vreman, c1, c2;
+  double skew;     // 0: convective form, 1: skew-symmetric (energy-preserving) form
+  double tau_elem; // 0: tau at each Gauss point, 1: one tau per element (mean velocity)
 };
 
 inline double re(double x) { return x; }
@@ -136,6 +143,15 @@ bool element_rhs(const double X[4][3], const T U[4][4], const Params& P, unsigne
   for (int a = 0; a < 4; ++a)
     for (int k = 0; k < 4; ++k) F[a][k] = 0.0;
 
+  // Per-element tau (variant): mean nodal velocity.
+  T tau_e = 0.0;
+  if (P.tau_elem != 0.0) {
+    T ub[3];
+    for (int i = 0; i < 3; ++i) ub[i] = 0.25 * (U[0][i] + U[1][i] + U[2][i] + U[3][i]);
+    T un = std::sqrt(ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2]);
+    tau_e = 1.0 / (P.c1 * mu_eff / (h * h) + P.c2 * P.rho * un / h);
+  }
+
   // Gauss-point loop: every integrand evaluated at xi_g, weight V/4.
   for (int g = 0; g < 4; ++g) {
     double N[4];
@@ -153,6 +169,7 @@ bool element_rhs(const double X[4][3], const T U[4][4], const Params& P, unsigne
     }
     T unorm = std::sqrt(ug[0] * ug[0] + ug[1] * ug[1] + ug[2] * ug[2]);
     T tau = 1.0 / (P.c1 * mu_eff / (h * h) + P.c2 * P.rho * unorm / h);
+    if (P.tau_elem != 0.0) tau = tau_e;
     T r[3];  // strong momentum residual (the viscous part vanishes for P1)
     for (int i = 0; i < 3; ++i) r[i] = P.rho * cg[i] + gp[i];
     const double w = V / 4.0;
@@ -160,7 +177,12 @@ bool element_rhs(const double X[4][3], const T U[4][4], const Params& P, unsigne
       T ugradNa = ug[0] * dN[a][0] + ug[1] * dN[a][1] + ug[2] * dN[a][2];
       for (int i = 0; i < 3; ++i) {
         T f = 0.0;
-        if (terms & T_CONV) f += -P.rho * N[a] * cg[i];
+        if (terms & T_CONV) {
+          if (P.skew != 0.0)
+            f += -0.5 * P.rho * (N[a] * cg[i] - ugradNa * ug[i]);
+          else
+            f += -P.rho * N[a] * cg[i];
+        }
         if (terms & T_VISC) {
           T gg = 0.0;
           for (int j = 0; j < 3; ++j) gg += dN[a][j] * G[i][j];

@@ -358,3 +358,104 @@ def test_vjp_dot_product_identity(mesh6):
     g = oracle.vjp(coords, conn, up, w, 1.0, 1e-4)
     lhs, rhs = np.sum(w * jv), np.sum(g * v)
     assert abs(lhs - rhs) <= 1e-12 * np.sqrt(np.sum(w * w) * np.sum(jv * jv))
+
+
+# ---- formulation variants: skew-symmetric convection, per-element tau ----
+
+def closed_form_shear_variants(rho, mu, s, q, skew, tau_elem, c1=4, c2=2):
+    """As closed_form_shear, with the variants: the skew-symmetric Galerkin
+    convection -rho/2 int[N_a (u.grad)u_i - (u.grad N_a) u_i] (u.grad N_a at
+    Gauss point g: y_g dN_a/dx + dN_a/dy) and/or one tau from the mean
+    velocity (s/4, 1, 0)."""
+    rho, mu, s, q = D(rho), D(mu), D(s), D(q)
+    V, h, pbar = s ** 3 / 6, s, q * s / 4
+    ys = [s * (QA if g == 2 else QB) for g in range(4)]
+    Ng = [[(QA if a == g else QB) for a in range(4)] for g in range(4)]
+    if tau_elem:
+        te = 1 / (c1 * mu / h ** 2 + c2 * rho * ((s / 4) ** 2 + 1).sqrt() / h)
+        taus = [te] * 4
+    else:
+        taus = [1 / (c1 * mu / h ** 2 + c2 * rho * (y * y + 1).sqrt() / h) for y in ys]
+    F = [[D(0)] * 4 for _ in range(4)]
+    for a in range(4):
+        dN = [D(c) / s for c in REF_DN[a]]
+        adv = [ys[g] * dN[0] + dN[1] for g in range(4)]       # u_g . grad N_a
+        if skew:
+            conv_x = -rho / 2 * sum(V / 4 * (Ng[g][a] * 1 - adv[g] * ys[g]) for g in range(4))
+            conv_y = -rho / 2 * sum(V / 4 * (0 - adv[g] * 1) for g in range(4))
+        else:
+            conv_x, conv_y = -V * rho / 4, D(0)
+        supg = sum(taus[g] * rho * adv[g] * (rho + q) for g in range(4))
+        F[a][0] = conv_x - V * mu * dN[1] + V * pbar * dN[0] - V / 4 * supg
+        F[a][1] = conv_y + V * pbar * dN[1]
+        F[a][2] = V * pbar * dN[2]
+        F[a][3] = -V / 4 * sum(taus) * dN[0] * (rho + q)
+    return np.array([[float(x) for x in row] for row in F])
+
+
+@pytest.mark.parametrize("skew,tau_elem", [(True, False), (False, True), (True, True)])
+@pytest.mark.parametrize("rho,mu,s,q", [(1.0, 1e-2, 1.0, 0.0), (2.5, 0.3, 0.37, -1.7)])
+def test_closed_form_shear_variants(skew, tau_elem, rho, mu, s, q):
+    X, U = shear_inputs(s, q)
+    F = oracle.element(X, U, rho, mu, skew=skew, tau_elem=tau_elem)
+    ref = closed_form_shear_variants(rho, mu, s, q, skew, tau_elem)
+    assert np.abs(F - ref).max() <= 1e-14 * np.abs(ref).max()
+    # the default-form closed form is the same function with both flags off
+    base = closed_form_shear_variants(rho, mu, s, q, False, False)
+    assert np.abs(base - closed_form_shear(rho, mu, s, q)).max() <= 1e-15 * np.abs(base).max()
+
+
+def test_skew_convection_does_no_work(mesh6):
+    """Energy preservation: sum over nodes of u . F_conv = 0 for the
+    skew-symmetric form (pointwise skew integrand), and not for the
+    convective form."""
+    coords, conn, up = mesh6
+    for skew, expect_zero in ((True, True), (False, False)):
+        f = oracle.assemble(coords, conn, up, 1.3, 1e-2, terms=oracle.T_CONV, skew=skew)
+        work = float(np.sum(up[:3] * f[:3]))
+        scale = float(np.sum(np.abs(up[:3] * f[:3])))
+        if expect_zero:
+            assert abs(work) <= 1e-14 * scale
+        else:
+            assert abs(work) > 1e-6 * scale
+
+
+def test_variants_invariants_and_derivatives(mesh6):
+    coords, conn, up = mesh6
+    kw = dict(skew=True, tau_elem=True, c_vreman=0.07)
+    rhs = oracle.assemble(coords, conn, up, 1.0, 1e-2, **kw)
+    scale = np.abs(rhs).max()
+    # rigid rotation
+    Q, _ = np.linalg.qr(np.random.default_rng(4).normal(size=(3, 3)))
+    if np.linalg.det(Q) < 0:
+        Q[:, 0] *= -1
+    upr = up.copy()
+    upr[:3] = Q @ up[:3]
+    rr = oracle.assemble(Q @ coords, conn, upr, 1.0, 1e-2, **kw)
+    assert np.abs(rr[:3] - Q @ rhs[:3]).max() < 1e-13 * scale
+    # constant velocity u0: only the skew term's boundary flux remains,
+    # rho/2 u0_i (u0 . oint N_a n dS), zero at interior nodes
+    N = coords.shape[1]
+    u0 = np.array([0.3, -2.0, 1.1])
+    uc = np.zeros((4, N))
+    uc[:3] = u0[:, None]
+    got = oracle.assemble(coords, conn, uc, 1.3, 1e-2, **kw)
+    faces = boundary_faces(conn)
+    nA = outward_area_normals(coords, faces)
+    flux = np.zeros(N)
+    for k in range(3):
+        np.add.at(flux, faces[:, k], nA @ u0 / 3.0)
+    expect = 0.5 * 1.3 * u0[:, None] * flux[None, :]
+    assert np.abs(got[:3] - expect).max() < 1e-15
+    assert np.abs(got[3]).max() < 1e-16
+    # complex step agrees with central differences, and the element-Jacobian VJP
+    # satisfies the dot-product identity
+    d = mg.normal(up.shape, seed=mg.SEED_DIRS)
+    jv = oracle.assemble_complex(coords, conn, up + 1e-30j * d, 1.0, 1e-2, **kw).imag / 1e-30
+    eps = 1e-6
+    fd = (oracle.assemble(coords, conn, up + eps * d, 1.0, 1e-2, **kw) -
+          oracle.assemble(coords, conn, up - eps * d, 1.0, 1e-2, **kw)) / (2 * eps)
+    assert np.linalg.norm(jv - fd) <= 1e-7 * np.linalg.norm(jv)
+    w = mg.normal(up.shape, seed=mg.SEED_COT)
+    g = oracle.vjp(coords, conn, up, w, 1.0, 1e-2, **kw)
+    assert abs(np.sum(w * jv) - np.sum(g * d)) <= 1e-12 * np.sqrt(np.sum(w * w) * np.sum(jv * jv))
