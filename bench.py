@@ -366,6 +366,19 @@ def run_ours(args):
     forms["vjp_fp64"] = {"ms": vjp_med, "tets_per_s": w.n_elems / (vjp_med * 1e-3),
                          "tflops": flops["vjp"] * w.n_elems / (vjp_med * 1e-3) / 1e12,
                          "vs_fwd_fp64": fwd_med / vjp_med}
+    for name, kw in (("fwd_fp64_skew", {"convection": "skew"}),
+                     ("fwd_fp64_tau_element", {"tau": "element"})):
+        pv = ns.Params(rho=w.rho, mu=w.mu, c_vreman=w.c_vreman, **kw)
+        for _ in range(2):
+            mesh.assemble(up, pv, out=rhs)
+        va, vb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        va.record(stream)
+        for _ in range(max(2, args.steps // 2)):
+            mesh.assemble(up, pv, out=rhs)
+        vb.record(stream)
+        torch.cuda.synchronize(dev)
+        vms = va.elapsed_time(vb) / max(2, args.steps // 2)
+        forms[name] = {"ms": vms, "tets_per_s": w.n_elems / (vms * 1e-3), "variant": kw}
     if not args.no_mixed:
         forms["mixed_same_mesh"] = time_mixed(mesh, w, dev, stream, args, fwd_med)
         mesh.close()

@@ -73,14 +73,28 @@ typedef enum {
                                memory, one atomic per (block, node, component) */
 } nsrhs_scatter;
 
+typedef enum {
+  NSRHS_CONVECTIVE = 0, /* Galerkin convection -rho int N_a (u.grad)u_i */
+  NSRHS_SKEW = 1        /* skew-symmetric -rho/2 int [N_a (u.grad)u_i - (u.grad N_a) u_i]:
+                           the convective RHS does no work on the discrete
+                           velocity (the energy-preserving property of Sec. II) */
+} nsrhs_convection;
+
+typedef enum {
+  NSRHS_TAU_GAUSS = 0,  /* tau at each Gauss point from |u_g| */
+  NSRHS_TAU_ELEMENT = 1 /* one tau per element from |mean nodal velocity| */
+} nsrhs_tau_mode;
+
 /* Physical and numerical parameters (uniform over one call). */
 typedef struct {
-  double rho;        /* density, >= 0 */
-  double mu;         /* dynamic viscosity, > 0 */
-  double c_vreman;   /* Vreman constant (about 0.07); 0 switches the model off */
-  double c1, c2;     /* stabilisation constants of tau (4 and 2) */
-  int32_t precision; /* nsrhs_precision */
-  int32_t scatter;   /* nsrhs_scatter */
+  double rho;         /* density, >= 0 */
+  double mu;          /* dynamic viscosity, > 0 */
+  double c_vreman;    /* Vreman constant (about 0.07); 0 switches the model off */
+  double c1, c2;      /* stabilisation constants of tau (4 and 2) */
+  int32_t precision;  /* nsrhs_precision */
+  int32_t scatter;    /* nsrhs_scatter */
+  int32_t convection; /* nsrhs_convection */
+  int32_t tau_mode;   /* nsrhs_tau_mode */
 } nsrhs_params;
 
 /* Mesh options. */
@@ -101,7 +115,8 @@ typedef struct {
   double min_detj, max_ar;
 } nsrhs_mesh_info;
 
-/* Fill *p with rho=1, mu=1e-2, c_vreman=0, c1=4, c2=2, FP64, AUTO. */
+/* Fill *p with rho=1, mu=1e-2, c_vreman=0, c1=4, c2=2, FP64, AUTO,
+   convective form, tau at the Gauss points. */
 void nsrhs_params_default(nsrhs_params* p);
 
 /* Fill *o with ar_threshold = 10. */

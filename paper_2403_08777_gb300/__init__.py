@@ -25,6 +25,8 @@ __all__ = ["Mesh", "Params", "assemble", "assemble_host", "StepPipeline", "NSRHS
 
 _PREC = {"fp64": _abi.FP64, "mixed": _abi.MIXED}
 _SCAT = {"auto": _abi.SCATTER_AUTO, "atomic": _abi.SCATTER_ATOMIC, "block": _abi.SCATTER_BLOCK}
+_CONV = {"convective": _abi.CONVECTIVE, "skew": _abi.SKEW}
+_TAU = {"gauss": _abi.TAU_GAUSS, "element": _abi.TAU_ELEMENT}
 
 
 def load_library():
@@ -40,12 +42,16 @@ class Params:
     c2: float = 2.0
     precision: str = "fp64"
     scatter: str = "auto"
+    convection: str = "convective"   # or "skew" (energy-preserving)
+    tau: str = "gauss"               # or "element"
 
     def to_c(self) -> _abi.Params:
-        if self.precision not in _PREC or self.scatter not in _SCAT:
-            raise ValueError(f"bad precision/scatter {self.precision}/{self.scatter}")
+        if (self.precision not in _PREC or self.scatter not in _SCAT or
+                self.convection not in _CONV or self.tau not in _TAU):
+            raise ValueError(f"bad option in {self}")
         return _abi.Params(self.rho, self.mu, self.c_vreman, self.c1, self.c2,
-                           _PREC[self.precision], _SCAT[self.scatter])
+                           _PREC[self.precision], _SCAT[self.scatter], _CONV[self.convection],
+                           _TAU[self.tau])
 
 
 def _stream_handle(device: torch.device) -> ctypes.c_void_p:

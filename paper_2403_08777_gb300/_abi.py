@@ -9,6 +9,8 @@ from . import build as _build
 OK, EINVAL, ENOMEM, EMESH, ECUDA, EUNSUPPORTED = 0, 1, 2, 3, 4, 5
 FP64, MIXED = 0, 1
 SCATTER_AUTO, SCATTER_ATOMIC, SCATTER_BLOCK = 0, 1, 2
+CONVECTIVE, SKEW = 0, 1
+TAU_GAUSS, TAU_ELEMENT = 0, 1
 
 # Every symbol include/nsrhs.h declares.
 EXPORTED = ("nsrhs_params_default", "nsrhs_mesh_opts_default", "nsrhs_mesh_create",
@@ -20,7 +22,8 @@ EXPORTED = ("nsrhs_params_default", "nsrhs_mesh_opts_default", "nsrhs_mesh_creat
 class Params(ctypes.Structure):
     _fields_ = [("rho", ctypes.c_double), ("mu", ctypes.c_double), ("c_vreman", ctypes.c_double),
                 ("c1", ctypes.c_double), ("c2", ctypes.c_double), ("precision", ctypes.c_int32),
-                ("scatter", ctypes.c_int32)]
+                ("scatter", ctypes.c_int32), ("convection", ctypes.c_int32),
+                ("tau_mode", ctypes.c_int32)]
 
 
 class MeshOpts(ctypes.Structure):

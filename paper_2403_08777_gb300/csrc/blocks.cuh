@@ -235,7 +235,7 @@ constexpr int block_kernel_min_ctas() {
   return sizeof(R) == 4 ? 4 : 2;
 }
 
-template <class R, bool VREMAN>
+template <class R, int FLAGS>
 __global__ void __launch_bounds__(kBlockElems, block_kernel_min_ctas<R>())
     fwd_block_kernel(int64_t N, int64_t E, int64_t n_blocks, const int64_t* __restrict__ node_off,
                      const int32_t* __restrict__ nodes, const uint16_t* __restrict__ runs,
@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(kBlockElems, block_kernel_min_ctas<R>())
       inv_det = __ldg(geom + 9 * E + e);
       rh = __ldg(geom + 10 * E + e);
       R F[4][4];
-      element_rhs<R, VREMAN>(c, inv_det, rh, u, p, P, F);
+      element_rhs<R, FLAGS>(c, inv_det, rh, u, p, P, F);
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll

@@ -42,6 +42,11 @@ struct ElemParams {
   R rho, mu, c_vreman, c1, c2;
 };
 
+// Formulation flags (template parameter of the element routines).
+constexpr int kVreman = 1;    // Vreman eddy viscosity on
+constexpr int kSkew = 2;      // skew-symmetric (energy-preserving) Galerkin convection
+constexpr int kTauElem = 4;   // one tau per element from the mean velocity
+
 template <class R>
 struct MathOps;
 
@@ -102,11 +107,19 @@ __device__ __forceinline__ void element_geometry(const XT X[4][3], R c[3][3], R&
 }
 
 // Forward element RHS. u[a][i], p[a] nodal values; F[a][0..2] momentum,
-// F[a][3] continuity.
-template <class R, bool VREMAN>
+// F[a][3] continuity. FLAGS: kVreman | kSkew | kTauElem.
+// Skew-symmetric variant: the Galerkin convection becomes
+// -rho/2 int[N_a (u.grad)u_i - (u.grad N_a) u_i]: half the convective term plus
+// (rho/48) P c_a with P = sum_g u_g u_g^T, folded into K.
+// Per-element tau: tau from |S_u/4|; then sum_g tau = 4 tau, T = tau S_u
+// (sum_g u_g = S_u) and Q = tau P.
+template <class R, int FLAGS>
 __device__ __forceinline__ void element_rhs(const R c[3][3], R inv_det, R rh, const R u[4][3],
                                             const R p[4], const ElemParams<R>& P, R F[4][4]) {
   using M = MathOps<R>;
+  constexpr bool VREMAN = (FLAGS & kVreman) != 0;
+  constexpr bool SKEW = (FLAGS & kSkew) != 0;
+  constexpr bool TAUE = (FLAGS & kTauElem) != 0;
   // Gh = sum_k (u_k - u_0) c_k^T, gph = sum_k (p_k - p_0) c_k
   R G[3][3], gp[3];
 #pragma unroll
@@ -127,7 +140,7 @@ __device__ __forceinline__ void element_rhs(const R c[3][3], R inv_det, R rh, co
   const R trG = G[0][0] + G[1][1] + G[2][2];
 
   R mu_eff = P.mu;
-  if (VREMAN) {
+  if constexpr (VREMAN) {
     // alpha = G^T, beta = h^2 G G^T; B and A from Gh, rescaled by detJ and h.
     R A = (R)0;
 #pragma unroll
@@ -153,29 +166,56 @@ __device__ __forceinline__ void element_rhs(const R c[3][3], R inv_det, R rh, co
   // Gauss points: u_g = QB S_u + (QA - QB) u_g-node.
   R stau = (R)0, T[3] = {(R)0, (R)0, (R)0};
   R Q00 = 0, Q11 = 0, Q22 = 0, Q01 = 0, Q02 = 0, Q12 = 0;
+  R P00 = 0, P11 = 0, P22 = 0, P01 = 0, P02 = 0, P12 = 0;  // sum_g u_g u_g^T
   R bS[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) bS[i] = (R)kQB * S[i];
+  R tau_e = (R)0;
+  if constexpr (TAUE) {
+    const R sm = (S[0] * S[0] + S[1] * S[1] + S[2] * S[2]) * (R)0.0625;
+    tau_e = M::rcp(k1 + k2 * M::sqrt_(sm));
+  }
 #pragma unroll
   for (int g = 0; g < 4; ++g) {
     R ug[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) ug[i] = bS[i] + (R)(kQA - kQB) * u[g][i];
-    R s = ug[0] * ug[0] + ug[1] * ug[1] + ug[2] * ug[2];
-    R tau = M::rcp(k1 + k2 * M::sqrt_(s));
-    stau += tau;
-    R tu[3];
+    if constexpr (!TAUE) {
+      R s = ug[0] * ug[0] + ug[1] * ug[1] + ug[2] * ug[2];
+      R tau = M::rcp(k1 + k2 * M::sqrt_(s));
+      stau += tau;
+      R tu[3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      tu[i] = tau * ug[i];
-      T[i] += tu[i];
+      for (int i = 0; i < 3; ++i) {
+        tu[i] = tau * ug[i];
+        T[i] += tu[i];
+      }
+      Q00 += tu[0] * ug[0];
+      Q11 += tu[1] * ug[1];
+      Q22 += tu[2] * ug[2];
+      Q01 += tu[0] * ug[1];
+      Q02 += tu[0] * ug[2];
+      Q12 += tu[1] * ug[2];
     }
-    Q00 += tu[0] * ug[0];
-    Q11 += tu[1] * ug[1];
-    Q22 += tu[2] * ug[2];
-    Q01 += tu[0] * ug[1];
-    Q02 += tu[0] * ug[2];
-    Q12 += tu[1] * ug[2];
+    if constexpr (SKEW || TAUE) {
+      P00 += ug[0] * ug[0];
+      P11 += ug[1] * ug[1];
+      P22 += ug[2] * ug[2];
+      P01 += ug[0] * ug[1];
+      P02 += ug[0] * ug[2];
+      P12 += ug[1] * ug[2];
+    }
+  }
+  if constexpr (TAUE) {
+    stau = (R)4 * tau_e;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) T[i] = tau_e * S[i];
+    Q00 = tau_e * P00;
+    Q11 = tau_e * P11;
+    Q22 = tau_e * P22;
+    Q01 = tau_e * P01;
+    Q02 = tau_e * P02;
+    Q12 = tau_e * P12;
   }
   // K = pbar/6 I - inv_det/6 [Gh (mu_eff I + rho^2/4 Q) + rho/4 gph T^T], with the
   // scalar factors folded into Qp and gq before the 3x3 product so that each
@@ -188,6 +228,8 @@ __device__ __forceinline__ void element_rhs(const R c[3][3], R inv_det, R rh, co
                       {a2 * Q01, a2 * Q11 + a1, a2 * Q12},
                       {a2 * Q02, a2 * Q12, a2 * Q22 + a1}};
   const R pb6 = psum * (R)(1.0 / 24.0);
+  const R Pm[3][3] = {{P00, P01, P02}, {P01, P11, P12}, {P02, P12, P22}};
+  const R r48 = P.rho * (R)(1.0 / 48.0);
   R K[3][3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
@@ -195,6 +237,7 @@ __device__ __forceinline__ void element_rhs(const R c[3][3], R inv_det, R rh, co
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
       R acc = (i == j) ? gq * T[j] + pb6 : gq * T[j];
+      if constexpr (SKEW) acc = r48 * Pm[i][j] + acc;
       acc = G[i][0] * Qp[0][j] + acc;
       acc = G[i][1] * Qp[1][j] + acc;
       K[i][j] = G[i][2] * Qp[2][j] + acc;
@@ -214,7 +257,8 @@ __device__ __forceinline__ void element_rhs(const R c[3][3], R inv_det, R rh, co
   }
   const R cont0 = trG * (R)(-1.0 / 24.0);
   // Galerkin convection -(rho/120) Gh (S_u + u_a) = Gh v_a, v_a = m120 u_a + m120 S_u
-  const R m120 = P.rho * (R)(-1.0 / 120.0);
+  // (halved in the skew-symmetric form)
+  const R m120 = P.rho * (R)(SKEW ? -1.0 / 240.0 : -1.0 / 120.0);
   R mS[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) mS[i] = m120 * S[i];
@@ -261,11 +305,14 @@ __device__ __forceinline__ void element_rhs(const R c[3][3], R inv_det, R rh, co
 // It differentiates exactly the sequence of element_rhs (same intermediates),
 // recomputing the forward quantities; every product is written as a chain of
 // fused multiply-adds.
-template <class R, bool VREMAN>
+template <class R, int FLAGS>
 __device__ __forceinline__ void element_vjp(const R c[3][3], R inv_det, R rh, const R u[4][3],
                                             const R p[4], const R w[4][4], const ElemParams<R>& P,
                                             R gu[4][3], R gpo[4]) {
   using M = MathOps<R>;
+  constexpr bool VREMAN = (FLAGS & kVreman) != 0;
+  constexpr bool SKEW = (FLAGS & kSkew) != 0;
+  constexpr bool TAUE = (FLAGS & kTauElem) != 0;
   // ---- forward recompute ----
   R G[3][3], gp[3];
 #pragma unroll
@@ -287,7 +334,7 @@ __device__ __forceinline__ void element_vjp(const R c[3][3], R inv_det, R rh, co
   R vA = (R)0, vphi = (R)0, vscale = (R)0;  // Vreman intermediates
   R b00 = (R)0, b11 = (R)0, b22 = (R)0, b01 = (R)0, b02 = (R)0, b12 = (R)0;
   bool vactive = false;
-  if (VREMAN) {
+  if constexpr (VREMAN) {
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -316,27 +363,54 @@ __device__ __forceinline__ void element_vjp(const R c[3][3], R inv_det, R rh, co
   R tau[4], yr[4];  // tau_g and 1/|u_g| (0 where u_g = 0)
   R stau = (R)0, T[3] = {(R)0, (R)0, (R)0};
   R Q00 = (R)0, Q11 = (R)0, Q22 = (R)0, Q01 = (R)0, Q02 = (R)0, Q12 = (R)0;
+  R P00 = (R)0, P11 = (R)0, P22 = (R)0, P01 = (R)0, P02 = (R)0, P12 = (R)0;
+  R tau_e = (R)0, yr_e = (R)0;  // per-element tau and 1/|S_u/4|
+  if constexpr (TAUE) {
+    const R sm = (S[0] * S[0] + S[1] * S[1] + S[2] * S[2]) * (R)0.0625;
+    yr_e = M::rsqrt_(sm);
+    tau_e = M::rcp(k2 * (sm * yr_e) + k1);
+  }
 #pragma unroll
   for (int g = 0; g < 4; ++g) {
     R ug[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) ug[i] = bS[i] + (R)(kQA - kQB) * u[g][i];
-    R s = ug[0] * ug[0] + ug[1] * ug[1] + ug[2] * ug[2];
-    yr[g] = M::rsqrt_(s);
-    tau[g] = M::rcp(k2 * (s * yr[g]) + k1);
-    stau += tau[g];
-    R tu[3];
+    if constexpr (!TAUE) {
+      R s = ug[0] * ug[0] + ug[1] * ug[1] + ug[2] * ug[2];
+      yr[g] = M::rsqrt_(s);
+      tau[g] = M::rcp(k2 * (s * yr[g]) + k1);
+      stau += tau[g];
+      R tu[3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      tu[i] = tau[g] * ug[i];
-      T[i] += tu[i];
+      for (int i = 0; i < 3; ++i) {
+        tu[i] = tau[g] * ug[i];
+        T[i] += tu[i];
+      }
+      Q00 += tu[0] * ug[0];
+      Q11 += tu[1] * ug[1];
+      Q22 += tu[2] * ug[2];
+      Q01 += tu[0] * ug[1];
+      Q02 += tu[0] * ug[2];
+      Q12 += tu[1] * ug[2];
+    } else {
+      P00 += ug[0] * ug[0];
+      P11 += ug[1] * ug[1];
+      P22 += ug[2] * ug[2];
+      P01 += ug[0] * ug[1];
+      P02 += ug[0] * ug[2];
+      P12 += ug[1] * ug[2];
     }
-    Q00 += tu[0] * ug[0];
-    Q11 += tu[1] * ug[1];
-    Q22 += tu[2] * ug[2];
-    Q01 += tu[0] * ug[1];
-    Q02 += tu[0] * ug[2];
-    Q12 += tu[1] * ug[2];
+  }
+  if constexpr (TAUE) {
+    stau = (R)4 * tau_e;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) T[i] = tau_e * S[i];
+    Q00 = tau_e * P00;
+    Q11 = tau_e * P11;
+    Q22 = tau_e * P22;
+    Q01 = tau_e * P01;
+    Q02 = tau_e * P02;
+    Q12 = tau_e * P12;
   }
 
   // ---- reverse ----
@@ -429,7 +503,7 @@ __device__ __forceinline__ void element_vjp(const R c[3][3], R inv_det, R rh, co
     const R Qp[3][3] = {{a2 * Q00 + a1, a2 * Q01, a2 * Q02},
                         {a2 * Q01, a2 * Q11 + a1, a2 * Q12},
                         {a2 * Q02, a2 * Q12, a2 * Q22 + a1}};
-    const R m120 = P.rho * (R)(-1.0 / 120.0);
+    const R m120 = P.rho * (R)(SKEW ? -1.0 / 240.0 : -1.0 / 120.0);
     R v[4][3];
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
@@ -456,6 +530,36 @@ __device__ __forceinline__ void element_vjp(const R c[3][3], R inv_det, R rh, co
   R ugb[4][3];
   R Usum[3] = {(R)0, (R)0, (R)0};
   const R crh2 = P.c1 * rh2;
+  // skew-symmetric convection: K += (rho/48) P, P = sum_g u_g u_g^T, so
+  // d/du_g <Omega, (rho/48) P> = (rho/48) (Omega + Omega^T) u_g
+  R Os[3][3];
+  if constexpr (SKEW) {
+    const R r48 = P.rho * (R)(1.0 / 48.0);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) Os[i][j] = r48 * (Om[i][j] + Om[j][i]);
+  }
+  R Sb_tau[3] = {(R)0, (R)0, (R)0};  // S_u-bar from the per-element tau
+  if constexpr (TAUE) {
+    // tau-bar = 4 staub + Tb . S + <Qbar, P> ; T = tau S ; Q = tau P
+    const R Pm[3][3] = {{P00, P01, P02}, {P01, P11, P12}, {P02, P12, P22}};
+    R taub = (R)4 * staub;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) taub = Tb[i] * S[i] + taub;
+    R qp = (R)0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) qp = Qs[i][j] * Pm[i][j] + qp;
+    taub = (R)0.5 * qp + taub;
+    const R db = -(tau_e * tau_e) * taub;
+    mub = crh2 * db + mub;
+    // |S_u/4| = sqrt(S.S/16): d/dS = S / (16 |S_u/4|)
+    const R sc = (k2 * db) * (yr_e * (R)0.0625);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) Sb_tau[i] = tau_e * Tb[i] + sc * S[i];
+  }
 #pragma unroll
   for (int g = 0; g < 4; ++g) {
     R ug[3];
@@ -464,21 +568,33 @@ __device__ __forceinline__ void element_vjp(const R c[3][3], R inv_det, R rh, co
     R Qu[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) Qu[i] = Qs[i][0] * ug[0] + Qs[i][1] * ug[1] + Qs[i][2] * ug[2];
-    // tau-bar: Q enters as ug^T Qbar ug = ug . (Qs ug) / 2
-    R taub = Tb[0] * ug[0] + staub;
-    taub = Tb[1] * ug[1] + taub;
-    taub = Tb[2] * ug[2] + taub;
-    taub = (R)0.5 * (ug[0] * Qu[0] + ug[1] * Qu[1] + ug[2] * Qu[2]) + taub;
-    const R db = -(tau[g] * tau[g]) * taub;  // d(1/d)
-    mub = crh2 * db + mub;
-    const R sc = (k2 * yr[g]) * db;           // d|u_g| / du_g = u_g / |u_g|
+    if constexpr (!TAUE) {
+      // tau-bar: Q enters as ug^T Qbar ug = ug . (Qs ug) / 2
+      R taub = Tb[0] * ug[0] + staub;
+      taub = Tb[1] * ug[1] + taub;
+      taub = Tb[2] * ug[2] + taub;
+      taub = (R)0.5 * (ug[0] * Qu[0] + ug[1] * Qu[1] + ug[2] * Qu[2]) + taub;
+      const R db = -(tau[g] * tau[g]) * taub;  // d(1/d)
+      mub = crh2 * db + mub;
+      const R sc = (k2 * yr[g]) * db;           // d|u_g| / du_g = u_g / |u_g|
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      R acc = sc * ug[i];
-      acc = tau[g] * Tb[i] + acc;
-      ugb[g][i] = tau[g] * Qu[i] + acc;
-      Usum[i] += ugb[g][i];
+      for (int i = 0; i < 3; ++i) {
+        R acc = sc * ug[i];
+        acc = tau[g] * Tb[i] + acc;
+        ugb[g][i] = tau[g] * Qu[i] + acc;
+      }
+    } else {
+      // Q = tau P: d/du_g <Qbar, tau P> = tau Qs u_g
+#pragma unroll
+      for (int i = 0; i < 3; ++i) ugb[g][i] = tau_e * Qu[i];
     }
+    if constexpr (SKEW) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+        ugb[g][i] = Os[i][0] * ug[0] + (Os[i][1] * ug[1] + (Os[i][2] * ug[2] + ugb[g][i]));
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) Usum[i] += ugb[g][i];
   }
   // Vreman: mu_eff = mu + vscale sqrt(B/A):
   // d phi / d Gh = (P - phi^2 I) Gh / (phi A), P = tr(beta) I - beta
@@ -499,7 +615,7 @@ __device__ __forceinline__ void element_vjp(const R c[3][3], R inv_det, R rh, co
   // convection's -(rho/120) Gh (S + u_a): gu_a = Gb c_a + Sbar + Hm^T wm_a + (QA-QB) ugb_a
   // with Hm = -(rho/120) Gh and Sbar = Hm^T sum_a wm_a + QB sum_g ugb_g.
   {
-    const R m120 = P.rho * (R)(-1.0 / 120.0);
+    const R m120 = P.rho * (R)(SKEW ? -1.0 / 240.0 : -1.0 / 120.0);
     R Hm[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
@@ -509,6 +625,7 @@ __device__ __forceinline__ void element_vjp(const R c[3][3], R inv_det, R rh, co
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
       R acc = (R)kQB * Usum[j];
+      if constexpr (TAUE) acc = acc + Sb_tau[j];
 #pragma unroll
       for (int i = 0; i < 3; ++i) acc = Hm[i][j] * ((w[0][i] + w[1][i]) + (w[2][i] + w[3][i])) + acc;
       Sb[j] = acc;

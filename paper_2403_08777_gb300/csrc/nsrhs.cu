@@ -18,6 +18,7 @@
 #include <cstdint>
 #include <cstring>
 #include <mutex>
+#include <type_traits>
 #include <new>
 #include <unordered_set>
 #include <vector>
@@ -367,7 +368,7 @@ __device__ __forceinline__ void load_geometry(const R* __restrict__ geom, int64_
 // FP64 forward, one element per thread: streamed connectivity and cached
 // geometry, gathered nodal (u, p), register-resident element arithmetic,
 // immediate atomic scatter of the 16 entries.
-template <bool VREMAN>
+template <int FLAGS>
 __global__ void __launch_bounds__(kThreads)
     fwd_fp64_atomic_kernel(int64_t N, int64_t E, const int32_t* __restrict__ conn,
                            const double* __restrict__ geom, const double* __restrict__ up,
@@ -387,7 +388,7 @@ __global__ void __launch_bounds__(kThreads)
     double c[3][3], inv_det, rh;
     load_geometry(geom, E, e, c, inv_det, rh);
     double F[4][4];
-    nsrhs::element_rhs<double, VREMAN>(c, inv_det, rh, u, p, P, F);
+    nsrhs::element_rhs<double, FLAGS>(c, inv_det, rh, u, p, P, F);
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -399,7 +400,7 @@ __global__ void __launch_bounds__(kThreads)
 // geometry (computed in double for every element, so the determinant and
 // inverse of high-aspect-ratio elements are double-accurate), double global
 // accumulation; float results are widened to double with integer operations.
-template <bool VREMAN>
+template <int FLAGS>
 __global__ void __launch_bounds__(kThreads)
     fwd_mixed_atomic_kernel(int64_t N, int64_t E, const int32_t* __restrict__ conn,
                             const float* __restrict__ geom_f, const float* __restrict__ up,
@@ -419,7 +420,7 @@ __global__ void __launch_bounds__(kThreads)
     float c[3][3], inv_det, rh;
     load_geometry(geom_f, E, e, c, inv_det, rh);
     float F[4][4];
-    nsrhs::element_rhs<float, VREMAN>(c, inv_det, rh, u, p, P, F);
+    nsrhs::element_rhs<float, FLAGS>(c, inv_det, rh, u, p, P, F);
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -430,7 +431,7 @@ __global__ void __launch_bounds__(kThreads)
 // FP64 vector-Jacobian product: gather the cotangent at the element's nodes
 // (the reverse of the scatter), recompute the element, run the reverse sweep,
 // scatter-add the gradient (the reverse of the gather).
-template <bool VREMAN>
+template <int FLAGS>
 __global__ void __launch_bounds__(kThreads)
     vjp_fp64_atomic_kernel(int64_t N, int64_t E, const int32_t* __restrict__ conn,
                            const double* __restrict__ geom, const double* __restrict__ up,
@@ -453,7 +454,7 @@ __global__ void __launch_bounds__(kThreads)
     double c[3][3], inv_det, rh;
     load_geometry(geom, E, e, c, inv_det, rh);
     double gu[4][3], gp[4];
-    nsrhs::element_vjp<double, VREMAN>(c, inv_det, rh, u, p, w, P, gu, gp);
+    nsrhs::element_vjp<double, FLAGS>(c, inv_det, rh, u, p, w, P, gu, gp);
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
 #pragma unroll
@@ -464,6 +465,27 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 // ---------------------------------------------------------------------------
+
+// Calls f(std::integral_constant<int, FLAGS>) for the runtime formulation flags.
+template <class Fn>
+void with_flags(int flags, Fn&& f) {
+  switch (flags & 7) {
+    case 0: f(std::integral_constant<int, 0>{}); break;
+    case 1: f(std::integral_constant<int, 1>{}); break;
+    case 2: f(std::integral_constant<int, 2>{}); break;
+    case 3: f(std::integral_constant<int, 3>{}); break;
+    case 4: f(std::integral_constant<int, 4>{}); break;
+    case 5: f(std::integral_constant<int, 5>{}); break;
+    case 6: f(std::integral_constant<int, 6>{}); break;
+    default: f(std::integral_constant<int, 7>{}); break;
+  }
+}
+
+int formulation_flags(const nsrhs_params* p) {
+  return (p->c_vreman != 0.0 ? nsrhs::kVreman : 0) |
+         (p->convection == NSRHS_SKEW ? nsrhs::kSkew : 0) |
+         (p->tau_mode == NSRHS_TAU_ELEMENT ? nsrhs::kTauElem : 0);
+}
 
 nsrhs_status cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return NSRHS_OK;
@@ -485,6 +507,8 @@ nsrhs_status check_params(const nsrhs_params* p) {
     return NSRHS_EINVAL;
   if (p->precision != NSRHS_FP64 && p->precision != NSRHS_MIXED) return NSRHS_EINVAL;
   if (p->scatter < NSRHS_SCATTER_AUTO || p->scatter > NSRHS_SCATTER_BLOCK) return NSRHS_EINVAL;
+  if (p->convection != NSRHS_CONVECTIVE && p->convection != NSRHS_SKEW) return NSRHS_EINVAL;
+  if (p->tau_mode != NSRHS_TAU_GAUSS && p->tau_mode != NSRHS_TAU_ELEMENT) return NSRHS_EINVAL;
   return NSRHS_OK;
 }
 
@@ -684,6 +708,8 @@ void nsrhs_params_default(nsrhs_params* p) {
   p->c2 = 2.0;
   p->precision = NSRHS_FP64;
   p->scatter = NSRHS_SCATTER_AUTO;
+  p->convection = NSRHS_CONVECTIVE;
+  p->tau_mode = NSRHS_TAU_GAUSS;
 }
 
 void nsrhs_mesh_opts_default(nsrhs_mesh_opts* o) {
@@ -748,7 +774,7 @@ nsrhs_status nsrhs_assemble(const nsrhs_mesh* m, const nsrhs_params* p, const vo
   if (st != NSRHS_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t N = m->n_nodes, E = m->n_elems;
-  const bool vreman = p->c_vreman != 0.0;
+  const int flags = formulation_flags(p);
   NSRHS_TRY(cudaMemsetAsync(rhs, 0, sizeof(double) * 4 * N, s));
   // AUTO: atomics for the FP64 form (its FP64 pipe, not the scatter, is the
   // limit, and the block sums would add FP64 work); blocks for the mixed form
@@ -759,39 +785,44 @@ nsrhs_status nsrhs_assemble(const nsrhs_mesh* m, const nsrhs_params* p, const vo
     const int64_t nb = m->n_blocks;
     const unsigned grid = (unsigned)std::max<int64_t>(
         1, std::min<int64_t>(nb, (int64_t)sm_count(m->device) * 4));
+    cudaError_t err = cudaSuccess;
     if (p->precision == NSRHS_FP64) {
       auto P = elem_params<double>(p);
       const size_t smem = 8 * nsrhs::kBlockSlots * sizeof(double);
-      auto kern = vreman ? nsrhs::fwd_block_kernel<double, true> : nsrhs::fwd_block_kernel<double, false>;
-      NSRHS_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      kern<<<grid, nsrhs::kBlockElems, smem, s>>>(N, E, nb, m->blk_node_off, m->blk_nodes,
-                                                  m->blk_runs, m->blk_slots, m->blk_lconn, m->geom,
-                                                  (const double*)up, P, rhs);
+      with_flags(flags, [&](auto fl) {
+        auto kern = nsrhs::fwd_block_kernel<double, decltype(fl)::value>;
+        err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err == cudaSuccess)
+          kern<<<grid, nsrhs::kBlockElems, smem, s>>>(N, E, nb, m->blk_node_off, m->blk_nodes,
+                                                      m->blk_runs, m->blk_slots, m->blk_lconn,
+                                                      m->geom, (const double*)up, P, rhs);
+      });
     } else {
       auto P = elem_params<float>(p);
       const size_t smem = 8 * nsrhs::kBlockSlots * sizeof(float);
-      auto kern = vreman ? nsrhs::fwd_block_kernel<float, true> : nsrhs::fwd_block_kernel<float, false>;
-      kern<<<grid, nsrhs::kBlockElems, smem, s>>>(N, E, nb, m->blk_node_off, m->blk_nodes,
-                                                  m->blk_runs, m->blk_slots, m->blk_lconn,
-                                                  m->geom_f, (const float*)up, P, rhs);
+      with_flags(flags, [&](auto fl) {
+        nsrhs::fwd_block_kernel<float, decltype(fl)::value>
+            <<<grid, nsrhs::kBlockElems, smem, s>>>(N, E, nb, m->blk_node_off, m->blk_nodes,
+                                                    m->blk_runs, m->blk_slots, m->blk_lconn,
+                                                    m->geom_f, (const float*)up, P, rhs);
+      });
     }
+    if (err != cudaSuccess) return cuda_status(err);
     return cuda_status(cudaGetLastError());
   }
-  unsigned grid = grid_for(E, m->device, 16);
+  const unsigned grid = grid_for(E, m->device, 16);
   if (p->precision == NSRHS_FP64) {
     auto P = elem_params<double>(p);
-    const double* u = (const double*)up;
-    if (vreman)
-      fwd_fp64_atomic_kernel<true><<<grid, kThreads, 0, s>>>(N, E, m->conn, m->geom, u, P, rhs);
-    else
-      fwd_fp64_atomic_kernel<false><<<grid, kThreads, 0, s>>>(N, E, m->conn, m->geom, u, P, rhs);
+    with_flags(flags, [&](auto fl) {
+      fwd_fp64_atomic_kernel<decltype(fl)::value>
+          <<<grid, kThreads, 0, s>>>(N, E, m->conn, m->geom, (const double*)up, P, rhs);
+    });
   } else {
     auto P = elem_params<float>(p);
-    const float* u = (const float*)up;
-    if (vreman)
-      fwd_mixed_atomic_kernel<true><<<grid, kThreads, 0, s>>>(N, E, m->conn, m->geom_f, u, P, rhs);
-    else
-      fwd_mixed_atomic_kernel<false><<<grid, kThreads, 0, s>>>(N, E, m->conn, m->geom_f, u, P, rhs);
+    with_flags(flags, [&](auto fl) {
+      fwd_mixed_atomic_kernel<decltype(fl)::value>
+          <<<grid, kThreads, 0, s>>>(N, E, m->conn, m->geom_f, (const float*)up, P, rhs);
+    });
   }
   return cuda_status(cudaGetLastError());
 }
@@ -806,11 +837,11 @@ nsrhs_status nsrhs_assemble_vjp(const nsrhs_mesh* m, const nsrhs_params* p, cons
   const int64_t N = m->n_nodes, E = m->n_elems;
   NSRHS_TRY(cudaMemsetAsync(grad, 0, sizeof(double) * 4 * N, s));
   auto P = elem_params<double>(p);
-  unsigned grid = grid_for(E, m->device, 16);
-  if (p->c_vreman != 0.0)
-    vjp_fp64_atomic_kernel<true><<<grid, kThreads, 0, s>>>(N, E, m->conn, m->geom, up, cot, P, grad);
-  else
-    vjp_fp64_atomic_kernel<false><<<grid, kThreads, 0, s>>>(N, E, m->conn, m->geom, up, cot, P, grad);
+  const unsigned grid = grid_for(E, m->device, 16);
+  with_flags(formulation_flags(p), [&](auto fl) {
+    vjp_fp64_atomic_kernel<decltype(fl)::value>
+        <<<grid, kThreads, 0, s>>>(N, E, m->conn, m->geom, up, cot, P, grad);
+  });
   return cuda_status(cudaGetLastError());
 }
 

@@ -71,12 +71,12 @@ int main() {
     element_geometry<Cnt, Cnt, Cnt>(X, c, inv_det, rh);
     long geo = total(), geo_sfu = g_sfu;
     reset();
-    if (vreman) element_rhs<Cnt, true>(c, inv_det, rh, u, p, P, F);
-    else element_rhs<Cnt, false>(c, inv_det, rh, u, p, P, F);
+    if (vreman) element_rhs<Cnt, kVreman>(c, inv_det, rh, u, p, P, F);
+    else element_rhs<Cnt, 0>(c, inv_det, rh, u, p, P, F);
     long fwd = total(), fwd_sfu = g_sfu, fwd_inst = total() - g_fused;
     reset();
-    if (vreman) element_vjp<Cnt, true>(c, inv_det, rh, u, p, w, P, gu, gp);
-    else element_vjp<Cnt, false>(c, inv_det, rh, u, p, w, P, gu, gp);
+    if (vreman) element_vjp<Cnt, kVreman>(c, inv_det, rh, u, p, w, P, gu, gp);
+    else element_vjp<Cnt, 0>(c, inv_det, rh, u, p, w, P, gu, gp);
     long vjp = total(), vjp_sfu = g_sfu, vjp_inst = total() - g_fused;
     // per call: the geometry is computed once per mesh and cached
     std::printf("%s fwd %ld sfu %ld vjp %ld sfu %ld geometry %ld sfu %ld\n",

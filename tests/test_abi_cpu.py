@@ -40,12 +40,12 @@ def test_status_strings_and_defaults(lib):
     assert b"unknown" in lib.nsrhs_status_string(99)
     p = _abi.Params()
     lib.nsrhs_params_default(ctypes.byref(p))
-    assert (p.rho, p.mu, p.c_vreman, p.c1, p.c2, p.precision, p.scatter) == (1.0, 1e-2, 0.0, 4.0,
-                                                                               2.0, 0, 0)
+    assert (p.rho, p.mu, p.c_vreman, p.c1, p.c2, p.precision, p.scatter, p.convection,
+            p.tau_mode) == (1.0, 1e-2, 0.0, 4.0, 2.0, 0, 0, 0, 0)
     o = _abi.MeshOpts()
     lib.nsrhs_mesh_opts_default(ctypes.byref(o))
     assert o.ar_threshold == 10.0
-    assert ctypes.sizeof(_abi.Params) == 48 and ctypes.sizeof(_abi.MeshInfo) == 64
+    assert ctypes.sizeof(_abi.Params) == 56 and ctypes.sizeof(_abi.MeshInfo) == 64
 
 
 def test_argument_errors_without_gpu(lib):
