@@ -157,6 +157,35 @@ nsrhs_status nsrhs_assemble(const nsrhs_mesh* m, const nsrhs_params* p, const vo
 nsrhs_status nsrhs_assemble_vjp(const nsrhs_mesh* m, const nsrhs_params* p, const double* up,
                                 const double* cot, double* grad, void* stream);
 
+/*
+ * ---- Explicit time stepping of the momentum equation ----
+ * The paper's kernel is the RHS of an explicit momentum step (Sec. II); these
+ * calls take that step. With the row-sum lumped P1 mass
+ *   m_a = sum over the elements containing node a of V_e / 4,
+ * the semi-discrete momentum equation is rho m_a du_a/dt = F_a (the first
+ * three rows of the assembled RHS). The pressure is held fixed (its
+ * fractional-step solve is outside this library).
+ */
+typedef enum {
+  NSRHS_EULER = 0, /* u' = u + dt L(u) */
+  NSRHS_SSPRK3 = 1 /* Shu-Osher three-stage strong-stability-preserving Runge-Kutta:
+                      u1 = u + dt L(u); u2 = 3/4 u + 1/4 (u1 + dt L(u1));
+                      u' = 1/3 u + 2/3 (u2 + dt L(u2)) */
+} nsrhs_time_scheme;
+
+/* Lumped mass of every node into mass_dev [n_nodes] double (overwritten). */
+nsrhs_status nsrhs_lumped_mass(const nsrhs_mesh* m, double* mass_dev, void* stream);
+
+/*
+ * One explicit step of length dt > 0 with L(u) = F(u, p) / (rho m), on
+ * up_dev [4][n_nodes] double in place (rows u, v, w advanced, row p kept).
+ * work_dev: caller-owned device scratch of 8 * n_nodes doubles (no
+ * allocation inside). Requires precision NSRHS_FP64 and rho > 0. Each
+ * Runge-Kutta stage runs one nsrhs_assemble on the stream.
+ */
+nsrhs_status nsrhs_explicit_step(const nsrhs_mesh* m, const nsrhs_params* p, double dt,
+                                 int32_t scheme, double* up_dev, double* work_dev, void* stream);
+
 /* Free the mesh and its device memory. NULL-safe. Synchronises the device
    memory it frees (cudaFree semantics). */
 void nsrhs_destroy(nsrhs_mesh* m);

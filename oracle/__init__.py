@@ -152,3 +152,40 @@ def submesh_for_nodes(conn, nodes):
     mark[np.asarray(nodes)] = True
     mask = mark[conn].any(axis=0)
     return np.ascontiguousarray(conn[:, mask])
+
+
+# ---- explicit time stepping of the momentum equation (numpy composition) ----
+
+def lumped_mass(coords, conn):
+    """Row-sum lumped P1 mass: m_a = sum over elements containing a of V_e/4."""
+    conn = np.asarray(conn)
+    v4 = detj(coords, conn) / 24.0
+    m = np.zeros(np.asarray(coords).shape[1])
+    for a in range(4):
+        np.add.at(m, conn[a], v4)
+    return m
+
+
+def euler(u, L, dt):
+    """u' = u + dt L(u)."""
+    return u + dt * L(u)
+
+
+def ssprk3(u, L, dt):
+    """Shu-Osher three-stage strong-stability-preserving Runge-Kutta."""
+    u1 = u + dt * L(u)
+    u2 = 0.75 * u + 0.25 * (u1 + dt * L(u1))
+    return u / 3.0 + 2.0 / 3.0 * (u2 + dt * L(u2))
+
+
+def explicit_step(coords, conn, up, rho, mu, dt, scheme="ssprk3", **kw):
+    """One step of rho m du/dt = F(u, p) (momentum rows, pressure fixed)."""
+    m = lumped_mass(coords, conn)
+    p = np.asarray(up)[3].copy()
+
+    def L(u):
+        full = np.vstack([u, p[None, :]])
+        return assemble(coords, conn, full, rho, mu, **kw)[:3] / (rho * m[None, :])
+
+    stepper = {"euler": euler, "ssprk3": ssprk3}[scheme]
+    return np.vstack([stepper(np.asarray(up)[:3].copy(), L, dt), p[None, :]])

@@ -151,6 +151,34 @@ class Mesh:
         _abi.check(st, "nsrhs_assemble_vjp")
         return out
 
+    def lumped_mass(self) -> torch.Tensor:
+        """Row-sum lumped P1 mass of every node, [N] float64."""
+        out = torch.empty(self.n_nodes, dtype=torch.float64, device=self.device)
+        with torch.cuda.device(self.device):
+            st = _abi.load().nsrhs_lumped_mass(self.handle, ctypes.c_void_p(out.data_ptr()),
+                                               _stream_handle(self.device))
+        _abi.check(st, "nsrhs_lumped_mass")
+        return out
+
+    def explicit_step(self, up: torch.Tensor, dt: float, scheme: str = "ssprk3",
+                      params: Params | None = None, *, work: torch.Tensor | None = None, **kw):
+        """Advance the velocity rows of up [4, N] (float64, in place) by one
+        explicit step of rho m du/dt = F (pressure row kept); returns up."""
+        p = self._params(params, kw)
+        _require(up, "up", torch.float64, (4, self.n_nodes), self.device)
+        if work is None:
+            work = torch.empty((8, self.n_nodes), dtype=torch.float64, device=self.device)
+        _require(work, "work", torch.float64, (8, self.n_nodes), self.device)
+        sch = {"euler": _abi.EULER, "ssprk3": _abi.SSPRK3}[scheme]
+        cp = p.to_c()
+        with torch.cuda.device(self.device):
+            st = _abi.load().nsrhs_explicit_step(self.handle, ctypes.byref(cp), float(dt), sch,
+                                                 ctypes.c_void_p(up.data_ptr()),
+                                                 ctypes.c_void_p(work.data_ptr()),
+                                                 _stream_handle(self.device))
+        _abi.check(st, "nsrhs_explicit_step")
+        return up
+
     def close(self) -> None:
         if getattr(self, "_h", None) is not None:
             _abi.load().nsrhs_destroy(self._h)

@@ -11,12 +11,13 @@ FP64, MIXED = 0, 1
 SCATTER_AUTO, SCATTER_ATOMIC, SCATTER_BLOCK = 0, 1, 2
 CONVECTIVE, SKEW = 0, 1
 TAU_GAUSS, TAU_ELEMENT = 0, 1
+EULER, SSPRK3 = 0, 1
 
 # Every symbol include/nsrhs.h declares.
 EXPORTED = ("nsrhs_params_default", "nsrhs_mesh_opts_default", "nsrhs_mesh_create",
             "nsrhs_mesh_get_info", "nsrhs_assemble", "nsrhs_assemble_vjp", "nsrhs_destroy",
             "nsrhs_status_string", "nsrhs_probe_fma", "nsrhs_mesh_check_noalloc",
-            "nsrhs_probe_special")
+            "nsrhs_probe_special", "nsrhs_lumped_mass", "nsrhs_explicit_step")
 
 
 class Params(ctypes.Structure):
@@ -82,6 +83,11 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.nsrhs_status_string.restype = ctypes.c_char_p
     lib.nsrhs_probe_fma.argtypes = [ctypes.c_int, I64, I64, P, P]
     lib.nsrhs_probe_fma.restype = ctypes.c_int
+    lib.nsrhs_lumped_mass.argtypes = [P, P, P]
+    lib.nsrhs_lumped_mass.restype = ctypes.c_int
+    lib.nsrhs_explicit_step.argtypes = [P, ctypes.POINTER(Params), ctypes.c_double, ctypes.c_int32,
+                                        P, P, P]
+    lib.nsrhs_explicit_step.restype = ctypes.c_int
     lib.nsrhs_probe_special.argtypes = [ctypes.c_int, I64, P, P, P, P]
     lib.nsrhs_probe_special.restype = ctypes.c_int
     lib.nsrhs_mesh_check_noalloc.argtypes = [I64, I64, P, P, ctypes.c_double, P, P]

@@ -49,6 +49,8 @@ struct nsrhs_mesh {
   uint16_t* blk_runs = nullptr;     // [blk_node_off[n_blocks] + n_blocks]
   uint16_t* blk_slots = nullptr;    // [n_blocks * kBlockSlots]
   uint16_t* blk_lconn = nullptr;    // [4][E]
+  double* inv_mass = nullptr;       // [N] 1 / lumped mass
+  double* mass = nullptr;           // [N] lumped mass sum_e V_e / 4
   nsrhs_mesh_info info{};
   std::vector<void*> allocations;
 };
@@ -343,6 +345,41 @@ __global__ void geometry_kernel(int64_t N, int64_t E, const double* __restrict__
       geom[q * E + e] = g[q];
       geom_f[q * E + e] = __double2float_rn(g[q]);
     }
+  }
+}
+
+// Lumped mass: every element adds V/4 = 1 / (24 inv_det) to its 4 nodes.
+__global__ void lumped_mass_kernel(int64_t E, const int32_t* __restrict__ conn,
+                                   const double* __restrict__ geom, double* __restrict__ mass) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const double v4 = 1.0 / (24.0 * geom[9 * E + e]);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) atomicAdd(mass + conn[a * E + e], v4);
+  }
+}
+
+__global__ void invert_kernel(int64_t n, const double* __restrict__ x, double* __restrict__ y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = 1.0 / x[i];
+}
+
+// Runge-Kutta stage combination on the velocity rows:
+// out = a0 u0 + a1 (uin + dt/rho F / m); the pressure row of out is u0's.
+__global__ void rk_combine_kernel(int64_t N, double a0, double a1, double dt_rho,
+                                  const double* __restrict__ u0, const double* __restrict__ uin,
+                                  const double* __restrict__ F,
+                                  const double* __restrict__ inv_mass, double* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double s = dt_rho * inv_mass[i];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const double stage = uin[k * N + i] + s * F[k * N + i];
+      out[k * N + i] = a0 == 0.0 ? a1 * stage : a0 * u0[k * N + i] + a1 * stage;
+    }
+    out[3 * N + i] = u0[3 * N + i];
   }
 }
 
@@ -687,6 +724,14 @@ nsrhs_status mesh_build(nsrhs_mesh* m, const double* coords, const int32_t* conn
                                                                  m->geom, m->geom_f);
   NSRHS_TRY(cudaGetLastError());
   if ((st = build_blocks(m, s)) != NSRHS_OK) return st;
+  // Lumped mass and its inverse (explicit time stepping).
+  if ((st = mesh_alloc(m, &m->mass, (size_t)N)) != NSRHS_OK) return st;
+  if ((st = mesh_alloc(m, &m->inv_mass, (size_t)N)) != NSRHS_OK) return st;
+  NSRHS_TRY(cudaMemsetAsync(m->mass, 0, sizeof(double) * N, s));
+  lumped_mass_kernel<<<grid_for(E, m->device, 8), kThreads, 0, s>>>(E, m->conn, m->geom, m->mass);
+  NSRHS_TRY(cudaGetLastError());
+  invert_kernel<<<grid_for(N, m->device, 8), kThreads, 0, s>>>(N, m->mass, m->inv_mass);
+  NSRHS_TRY(cudaGetLastError());
   NSRHS_TRY(cudaStreamSynchronize(s));
   m->info.n_nodes = N;
   m->info.n_elems = E;
@@ -864,6 +909,50 @@ nsrhs_status nsrhs_mesh_check_noalloc(int64_t n_nodes, int64_t n_elems, const do
                                                        ar_threshold, scratch);
   NSRHS_TRY(cudaGetLastError());
   check_reduce_kernel<<<1, kCheckThreads, 0, s>>>(grid, scratch, result_dev);
+  return cuda_status(cudaGetLastError());
+}
+
+nsrhs_status nsrhs_lumped_mass(const nsrhs_mesh* m, double* mass_dev, void* stream) {
+  if (!is_live(m) || !mass_dev) return NSRHS_EINVAL;
+  return cuda_status(cudaMemcpyAsync(mass_dev, m->mass, sizeof(double) * m->n_nodes,
+                                     cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+}
+
+nsrhs_status nsrhs_explicit_step(const nsrhs_mesh* m, const nsrhs_params* p, double dt,
+                                 int32_t scheme, double* up_dev, double* work_dev, void* stream) {
+  if (!is_live(m) || !up_dev || !work_dev) return NSRHS_EINVAL;
+  nsrhs_status st = check_params(p);
+  if (st != NSRHS_OK) return st;
+  if (!(dt > 0.0) || !std::isfinite(dt) || !(p->rho > 0.0)) return NSRHS_EINVAL;
+  if (scheme != NSRHS_EULER && scheme != NSRHS_SSPRK3) return NSRHS_EINVAL;
+  if (p->precision != NSRHS_FP64) return NSRHS_EUNSUPPORTED;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t N = m->n_nodes;
+  double* F = work_dev;              // [4][N] stage RHS
+  double* stage = work_dev + 4 * N;  // [4][N] stage state
+  const double dtr = dt / p->rho;
+  const unsigned grid = grid_for(N, m->device, 8);
+  auto rhs_of = [&](const double* u) { return nsrhs_assemble(m, p, u, F, stream); };
+  if (scheme == NSRHS_EULER) {
+    if ((st = rhs_of(up_dev)) != NSRHS_OK) return st;
+    rk_combine_kernel<<<grid, kThreads, 0, s>>>(N, 0.0, 1.0, dtr, up_dev, up_dev, F, m->inv_mass,
+                                                up_dev);
+    return cuda_status(cudaGetLastError());
+  }
+  // stage 1: stage = u + dt L(u)
+  if ((st = rhs_of(up_dev)) != NSRHS_OK) return st;
+  rk_combine_kernel<<<grid, kThreads, 0, s>>>(N, 0.0, 1.0, dtr, up_dev, up_dev, F, m->inv_mass,
+                                              stage);
+  NSRHS_TRY(cudaGetLastError());
+  // stage 2: stage = 3/4 u + 1/4 (stage + dt L(stage))
+  if ((st = rhs_of(stage)) != NSRHS_OK) return st;
+  rk_combine_kernel<<<grid, kThreads, 0, s>>>(N, 0.75, 0.25, dtr, up_dev, stage, F, m->inv_mass,
+                                              stage);
+  NSRHS_TRY(cudaGetLastError());
+  // stage 3: u = 1/3 u + 2/3 (stage + dt L(stage))
+  if ((st = rhs_of(stage)) != NSRHS_OK) return st;
+  rk_combine_kernel<<<grid, kThreads, 0, s>>>(N, 1.0 / 3.0, 2.0 / 3.0, dtr, up_dev, stage, F,
+                                              m->inv_mass, up_dev);
   return cuda_status(cudaGetLastError());
 }
 

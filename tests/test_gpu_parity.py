@@ -309,3 +309,32 @@ def test_skew_convection_does_no_work_on_gpu(dev):
     conv_gpu = full - rest
     assert abs(np.sum(up[:3] * conv_gpu[:3])) <= 1e-12 * np.sum(np.abs(up[:3] * conv_gpu[:3]))
     m.close()
+
+
+def test_lumped_mass_and_explicit_steps_match_oracle(dev):
+    w = mg.make_workload(10, jitter=0.2, order="rcm", mu=1e-3, mag_max=2.0)
+    coords, conn, up = on_dev(dev, w.coords, w.conn, w.up)
+    m = ns.Mesh(coords, conn)
+    mass = m.lumped_mass().cpu().numpy()
+    mref = oracle.lumped_mass(w.coords, w.conn)
+    assert relerr(mass, mref) <= 1e-14
+    dt = 2e-3
+    for scheme in ("euler", "ssprk3"):
+        for kw in ({}, {"convection": "skew", "c_vreman": 0.07}):
+            u = up.clone()
+            p = ns.Params(rho=w.rho, mu=w.mu, **{k: v for k, v in kw.items()})
+            okw = {"skew": kw.get("convection") == "skew", "c_vreman": kw.get("c_vreman", 0.0)}
+            ref = w.up.copy()
+            for _ in range(3):
+                m.explicit_step(u, dt, scheme, p)
+                ref = oracle.explicit_step(w.coords, w.conn, ref, w.rho, w.mu, dt, scheme, **okw)
+            got = u.cpu().numpy()
+            # compare the change of the state (the increments carry the RHS)
+            assert relerr(got - w.up, ref - w.up) <= 1e-12, (scheme, kw)
+            assert np.array_equal(got[3], w.up[3])
+    work = torch.empty((8, w.n_nodes), dtype=torch.float64, device=dev)
+    with pytest.raises(ns.NSRHSError):
+        m.explicit_step(up.clone(), -1.0, "euler", ns.Params(), work=work)
+    with pytest.raises(ns.NSRHSError):
+        m.explicit_step(up.clone(), 1e-3, "euler", ns.Params(rho=0.0), work=work)
+    m.close()

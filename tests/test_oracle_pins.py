@@ -459,3 +459,41 @@ def test_variants_invariants_and_derivatives(mesh6):
     w = mg.normal(up.shape, seed=mg.SEED_COT)
     g = oracle.vjp(coords, conn, up, w, 1.0, 1e-2, **kw)
     assert abs(np.sum(w * jv) - np.sum(g * d)) <= 1e-12 * np.sqrt(np.sum(w * w) * np.sum(jv * jv))
+
+
+# ---- explicit time stepping (oracle composition) ----
+
+def test_lumped_mass_sums_to_volume(mesh6):
+    coords, conn, _ = mesh6
+    m = oracle.lumped_mass(coords, conn)
+    assert abs(m.sum() - 1.0) < 1e-14 and (m > 0).all()
+    # an interior node of the undistorted mesh carries h^3 (24 tets of h^3/6, /4 each)
+    c0, cn0, _, _ = mg.box_mesh(4, 0.0)
+    m0 = oracle.lumped_mass(c0, cn0)
+    centre = 2 + 5 * (2 + 5 * 2)
+    assert abs(m0[centre] - 0.25 ** 3) < 1e-16
+
+
+@pytest.mark.parametrize("z", [-0.3, 0.5, -1.2 + 0.7j])
+def test_runge_kutta_amplification(z):
+    """On du/dt = lam u the schemes reproduce their amplification polynomials:
+    Euler 1 + z, SSP-RK3 1 + z + z^2/2 + z^3/6 (z = lam dt)."""
+    lam, dt = z / 0.1, 0.1
+    u0 = np.array([1.0 + 0j, -2.0])
+    L = lambda u: lam * u  # noqa: E731
+    assert np.allclose(oracle.euler(u0, L, dt), (1 + z) * u0, rtol=1e-15)
+    assert np.allclose(oracle.ssprk3(u0, L, dt), (1 + z + z * z / 2 + z ** 3 / 6) * u0,
+                       rtol=1e-15)
+
+
+def test_explicit_step_keeps_constant_velocity_and_pressure(mesh6):
+    coords, conn, up = mesh6
+    uc = np.zeros_like(up)
+    uc[:3] = np.array([0.3, -2.0, 1.1])[:, None]
+    uc[3] = up[3]  # pressure is frozen; constant velocity with variable p changes u
+    out = oracle.explicit_step(coords, conn, uc, 1.0, 1e-2, 1e-3, "ssprk3")
+    assert np.array_equal(out[3], uc[3])
+    up0 = uc.copy()
+    up0[3] = 0.0
+    out0 = oracle.explicit_step(coords, conn, up0, 1.0, 1e-2, 1e-3, "ssprk3")
+    assert np.abs(out0 - up0).max() < 1e-15
