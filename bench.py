@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--n", type=int, default=256, help="hexes per cube edge")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision lines")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--unstructured", type=int, default=64,
+                    help="also time a Delaunay mesh of an (n+1)^3 jittered lattice (0: skip)")
     ap.add_argument("--sample-fwd", type=int, default=1 << 20,
                     help="oracle forward elements per host process")
     ap.add_argument("--sample-vjp", type=int, default=1 << 16,
@@ -434,6 +436,9 @@ def run_ours(args):
         forms["mixed_jitter03"] = mixed
         mj.close()
 
+    if args.unstructured > 0:
+        forms["unstructured"] = time_unstructured(args.unstructured, dev, stream, args)
+
     dom = "vjp_fp64" if vjp_med >= fwd_med else "fwd_fp64"
     dom_ms = vjp_med if dom == "vjp_fp64" else fwd_med
     achieved = forms[dom]["tflops"]
@@ -497,6 +502,43 @@ def time_mixed(mesh, w, dev, stream, args, fp64_ms):
     ms = a.elapsed_time(b) / args.steps
     return {"ms": ms, "tets_per_s": w.n_elems / (ms * 1e-3), "fp64_ms": fp64_ms,
             "speedup_vs_fp64": fp64_ms / ms, "workload": w.name}
+
+
+def time_unstructured(n, dev, stream, args):
+    """FP64 forward and adjoint and the mixed forward on the Delaunay mesh of
+    an (n+1)^3 jittered lattice (RCM order): irregular valence, no hex blocks."""
+    import torch
+    import paper_2403_08777_gb300 as ns
+    w = mg.make_unstructured(n, order="rcm", mu=1e-4, mag_max=10.0)
+    m = ns.Mesh(torch.from_numpy(w.coords).to(dev), torch.from_numpy(w.conn).to(dev))
+    up = torch.from_numpy(w.up).to(dev)
+    cot = torch.from_numpy(mg.normal((4, w.n_nodes), seed=mg.SEED_COT)).to(dev)
+    p = ns.Params(rho=w.rho, mu=w.mu)
+    pm = ns.Params(rho=w.rho, mu=w.mu, precision="mixed")
+    up32 = up.float()
+    out = torch.empty_like(up)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b) / args.steps
+
+    fwd = timed(lambda: m.assemble(up, p, out=out))
+    vjp = timed(lambda: m.assemble_vjp(up, cot, p, out=out))
+    mix = timed(lambda: m.assemble(up32, pm, out=out))
+    info = m.info()
+    m.close()
+    return {"workload": w.name, "n_tets": w.n_elems, "n_nodes": w.n_nodes,
+            "fwd_fp64_tets_per_s": w.n_elems / (fwd * 1e-3),
+            "vjp_fp64_tets_per_s": w.n_elems / (vjp * 1e-3),
+            "mixed_tets_per_s": w.n_elems / (mix * 1e-3), "n_high_ar": info["n_high_ar"],
+            "max_ar": info["max_ar"]}
 
 
 def mixed_error_64() -> float:

@@ -141,6 +141,96 @@ def renumber(order: np.ndarray, coords: np.ndarray, conn: np.ndarray, *nodal):
     return (new_coords, new_conn) + tuple(np.ascontiguousarray(a[:, order]) for a in nodal)
 
 
+def delaunay_mesh(n: int, jitter: float = 0.3, seed: int = SEED_MESH):
+    """Unstructured tet mesh of the unit cube: Delaunay tetrahedralisation
+    (scipy / Qhull) of the (n+1)^3 lattice with interior points jittered by
+    U(-jitter h, jitter h). Node valences vary and there is no hex-block
+    structure. Zero-volume tets that Qhull leaves on the flat cube faces
+    (|detJ| < 1e-8 h^3) are dropped (they carry no volume); the others are
+    oriented so that detJ > 0. Returns (coords [3][N] f64, conn [4][E] i32)."""
+    from scipy.spatial import Delaunay
+
+    n1 = n + 1
+    idx = np.arange(n1 ** 3)
+    ijk = np.stack([idx % n1, (idx // n1) % n1, idx // (n1 * n1)], axis=1)
+    pts = ijk.astype(np.float64) / n
+    interior = np.all((ijk > 0) & (ijk < n), axis=1)
+    # seeded PCG64 stream (reproducible across machines)
+    off = np.random.default_rng(seed).uniform(-1.0, 1.0, (n1 ** 3, 3)) * jitter / n
+    pts[interior] += off[interior]
+    simp = Delaunay(pts).simplices.astype(np.int64)
+    X = pts[simp]
+    det = np.linalg.det(X[:, 1:] - X[:, :1])
+    keep = np.abs(det) > 1e-8 / n ** 3
+    simp, det = simp[keep], det[keep]
+    neg = det < 0
+    simp[neg, 1], simp[neg, 2] = simp[neg, 2].copy(), simp[neg, 1].copy()
+    coords = np.ascontiguousarray(pts.T)
+    conn = np.ascontiguousarray(simp.T.astype(np.int32))
+    return coords, conn
+
+
+def write_msh(path: str, coords: np.ndarray, conn: np.ndarray) -> None:
+    """Gmsh MSH 2.2 ASCII with 4-node tetrahedra (element type 4)."""
+    N, E = coords.shape[1], conn.shape[1]
+    with open(path, "w") as f:
+        f.write("$MeshFormat\n2.2 0 8\n$EndMeshFormat\n$Nodes\n%d\n" % N)
+        for i in range(N):
+            f.write("%d %.17g %.17g %.17g\n" % (i + 1, coords[0, i], coords[1, i], coords[2, i]))
+        f.write("$EndNodes\n$Elements\n%d\n" % E)
+        for e in range(E):
+            a = conn[:, e] + 1
+            f.write("%d 4 2 0 1 %d %d %d %d\n" % (e + 1, a[0], a[1], a[2], a[3]))
+        f.write("$EndElements\n")
+
+
+def read_msh(path: str):
+    """Read the nodes and the 4-node tetrahedra (type 4) of a Gmsh MSH 2.2
+    ASCII file; other element types are skipped. Node tags are mapped to
+    0-based indices in file order. Returns (coords [3][N] f64, conn [4][E] i32)."""
+    with open(path) as f:
+        lines = [ln.strip() for ln in f]
+    i = lines.index("$MeshFormat")
+    version = lines[i + 1].split()
+    if not version[0].startswith("2") or version[1] != "0":
+        raise ValueError("only MSH 2.x ASCII is supported")
+    i = lines.index("$Nodes")
+    n_nodes = int(lines[i + 1])
+    tags = np.empty(n_nodes, np.int64)
+    xyz = np.empty((n_nodes, 3))
+    for k in range(n_nodes):
+        parts = lines[i + 2 + k].split()
+        tags[k] = int(parts[0])
+        xyz[k] = [float(v) for v in parts[1:4]]
+    pos = {int(t): k for k, t in enumerate(tags)}
+    i = lines.index("$Elements")
+    n_el = int(lines[i + 1])
+    tets = []
+    for k in range(n_el):
+        parts = lines[i + 2 + k].split()
+        if int(parts[1]) != 4:
+            continue
+        n_tags = int(parts[2])
+        tets.append([pos[int(v)] for v in parts[3 + n_tags:7 + n_tags]])
+    coords = np.ascontiguousarray(xyz.T)
+    conn = np.ascontiguousarray(np.asarray(tets, np.int32).reshape(-1, 4).T)
+    return coords, conn
+
+
+def make_unstructured(n: int, *, jitter: float = 0.3, order: str = "rcm", rho: float = 1.0,
+                      mu: float = 1e-2, mag_max: float = 0.0, c_vreman: float = 0.0,
+                      noise_sigma: float = 1e-2) -> "Workload":
+    """Workload on the Delaunay mesh of an (n+1)^3 jittered lattice."""
+    coords, conn = delaunay_mesh(n, jitter)
+    up = fields(coords, noise_sigma=noise_sigma, mag_max=mag_max)
+    if order == "random":
+        coords, conn, up = renumber(random_order(coords.shape[1]), coords, conn, up)
+    elif order == "rcm":
+        coords, conn, up = renumber(rcm_order(conn, coords.shape[1]), coords, conn, up)
+    return Workload(f"delaunay{n}^3-{order}", n, coords, conn, up, rho, mu, c_vreman, order,
+                    jitter)
+
+
 @dataclass
 class Workload:
     """One synthetic assembly problem (host arrays)."""

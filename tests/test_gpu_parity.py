@@ -338,3 +338,24 @@ def test_lumped_mass_and_explicit_steps_match_oracle(dev):
     with pytest.raises(ns.NSRHSError):
         m.explicit_step(up.clone(), 1e-3, "euler", ns.Params(rho=0.0), work=work)
     m.close()
+
+
+@pytest.mark.parametrize("n,order", [(10, "rcm"), (16, "random")])
+def test_unstructured_delaunay_mesh(dev, n, order):
+    """Delaunay mesh of a jittered lattice (varying valence, no hex-block
+    structure): FP64 atomic and block, mixed, adjoint and a variant."""
+    w = mg.make_unstructured(n, order=order, mu=1e-3, mag_max=2.0)
+    coords, conn, up = on_dev(dev, w.coords, w.conn, w.up)
+    m = ns.Mesh(coords, conn)
+    ref = oracle.assemble(w.coords, w.conn, w.up, w.rho, w.mu)
+    for scatter in ("atomic", "block"):
+        check_fp64(m.assemble(up, ns.Params(rho=w.rho, mu=w.mu, scatter=scatter)).cpu().numpy(),
+                   ref)
+    x = m.assemble(up.float(), ns.Params(rho=w.rho, mu=w.mu, precision="mixed")).cpu().numpy()
+    assert relerr(x, ref) <= TOL_MIXED
+    cot = mg.normal((4, w.n_nodes), seed=mg.SEED_COT)
+    g = m.assemble_vjp(up, torch.from_numpy(cot).to(dev), rho=w.rho, mu=w.mu).cpu().numpy()
+    assert relerr(g, oracle.vjp(w.coords, w.conn, w.up, cot, w.rho, w.mu)) <= TOL_VJP_ORACLE
+    sk = m.assemble(up, ns.Params(rho=w.rho, mu=w.mu, convection="skew")).cpu().numpy()
+    check_fp64(sk, oracle.assemble(w.coords, w.conn, w.up, w.rho, w.mu, skew=True))
+    m.close()

@@ -115,3 +115,37 @@ def test_normal_stream():
     assert abs(a.mean()) < 0.01 and abs(a.std() - 1) < 0.01
     assert np.array_equal(a, mg.normal(200000, seed=4))
     assert not np.array_equal(a, mg.normal(200000, seed=5))
+
+
+def test_delaunay_mesh_is_valid_and_unstructured():
+    coords, conn = mg.delaunay_mesh(8, 0.3)
+    N = coords.shape[1]
+    assert np.unique(conn).size == N
+    det = oracle.detj(coords, conn)
+    assert (det > 0).all()
+    assert abs(det.sum() / 6.0 - 1.0) < 1e-13
+    f = _faces(conn)
+    _, counts = np.unique(f, axis=0, return_counts=True)
+    assert set(counts.tolist()) <= {1, 2}
+    # valences vary (no hex-block structure)
+    val = np.bincount(conn.ravel(), minlength=N)
+    assert val.max() - val.min() > 10
+    c2, cn2 = mg.delaunay_mesh(8, 0.3)
+    assert np.array_equal(conn, cn2) and np.array_equal(coords, c2)
+
+
+def test_msh_round_trip(tmp_path):
+    coords, conn = mg.delaunay_mesh(4, 0.2)
+    path = str(tmp_path / "m.msh")
+    mg.write_msh(path, coords, conn)
+    c2, cn2 = mg.read_msh(path)
+    assert np.array_equal(coords, c2) and np.array_equal(conn, cn2)
+    # non-tet elements are skipped, node tags need not be 1..N
+    with open(path) as f:
+        txt = f.read()
+    txt = txt.replace("$Elements\n%d\n" % conn.shape[1],
+                      "$Elements\n%d\n1 2 2 0 1 1 2 3\n" % (conn.shape[1] + 1))
+    with open(path, "w") as f:
+        f.write(txt)
+    c3, cn3 = mg.read_msh(path)
+    assert np.array_equal(cn3, conn)
