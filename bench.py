@@ -392,6 +392,18 @@ def run_ours(args):
         torch.cuda.synchronize(dev)
         vms = va.elapsed_time(vb) / max(2, args.steps // 2)
         forms[name] = {"ms": vms, "tets_per_s": w.n_elems / (vms * 1e-3), "variant": kw}
+    # element-matrix comparison path (the pre-restructuring form, Sec. V-A)
+    mesh.assemble_elmat(up, p, out=rhs)
+    ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n_em = max(2, args.steps // 4)
+    ea.record(stream)
+    for _ in range(n_em):
+        mesh.assemble_elmat(up, p, out=rhs)
+    eb.record(stream)
+    torch.cuda.synchronize(dev)
+    em_ms = ea.elapsed_time(eb) / n_em
+    forms["fwd_fp64_element_matrix"] = {"ms": em_ms, "tets_per_s": w.n_elems / (em_ms * 1e-3),
+                                        "direct_speedup": em_ms / fwd_med}
     # explicit SSP-RK3 momentum step (3 assemblies + stage updates), in place
     # on a copy of the fields; dt is a CFL-like 0.1 h / max|u|
     u_step = up.clone()

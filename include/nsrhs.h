@@ -158,6 +158,17 @@ nsrhs_status nsrhs_assemble_vjp(const nsrhs_mesh* m, const nsrhs_params* p, cons
                                 const double* cot, double* grad, void* stream);
 
 /*
+ * The same RHS (FP64, convective form, tau at the Gauss points) computed the
+ * way the paper's baseline did before its restructuring (Sec. V-A): with the
+ * nonlinear coefficients frozen at the current state, a full 16x16 element
+ * matrix per tet, multiplied by the element unknowns. A comparison path that
+ * measures the gain of the direct form; rhs is overwritten. Other precisions
+ * or variants: NSRHS_EUNSUPPORTED.
+ */
+nsrhs_status nsrhs_assemble_elmat(const nsrhs_mesh* m, const nsrhs_params* p, const double* up,
+                                  double* rhs, void* stream);
+
+/*
  * ---- Explicit time stepping of the momentum equation ----
  * The paper's kernel is the RHS of an explicit momentum step (Sec. II); these
  * calls take that step. With the row-sum lumped P1 mass

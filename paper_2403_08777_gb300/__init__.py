@@ -151,6 +151,21 @@ class Mesh:
         _abi.check(st, "nsrhs_assemble_vjp")
         return out
 
+    def assemble_elmat(self, up: torch.Tensor, params: Params | None = None, *, out=None, **kw):
+        """The FP64 RHS through full 16x16 element matrices (comparison path)."""
+        p = self._params(params, kw)
+        _require(up, "up", torch.float64, (4, self.n_nodes), self.device)
+        if out is None:
+            out = torch.empty((4, self.n_nodes), dtype=torch.float64, device=self.device)
+        cp = p.to_c()
+        with torch.cuda.device(self.device):
+            st = _abi.load().nsrhs_assemble_elmat(self.handle, ctypes.byref(cp),
+                                                  ctypes.c_void_p(up.data_ptr()),
+                                                  ctypes.c_void_p(out.data_ptr()),
+                                                  _stream_handle(self.device))
+        _abi.check(st, "nsrhs_assemble_elmat")
+        return out
+
     def lumped_mass(self) -> torch.Tensor:
         """Row-sum lumped P1 mass of every node, [N] float64."""
         out = torch.empty(self.n_nodes, dtype=torch.float64, device=self.device)

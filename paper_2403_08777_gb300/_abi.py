@@ -17,7 +17,8 @@ EULER, SSPRK3 = 0, 1
 EXPORTED = ("nsrhs_params_default", "nsrhs_mesh_opts_default", "nsrhs_mesh_create",
             "nsrhs_mesh_get_info", "nsrhs_assemble", "nsrhs_assemble_vjp", "nsrhs_destroy",
             "nsrhs_status_string", "nsrhs_probe_fma", "nsrhs_mesh_check_noalloc",
-            "nsrhs_probe_special", "nsrhs_lumped_mass", "nsrhs_explicit_step")
+            "nsrhs_probe_special", "nsrhs_lumped_mass", "nsrhs_explicit_step",
+            "nsrhs_assemble_elmat")
 
 
 class Params(ctypes.Structure):
@@ -83,6 +84,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.nsrhs_status_string.restype = ctypes.c_char_p
     lib.nsrhs_probe_fma.argtypes = [ctypes.c_int, I64, I64, P, P]
     lib.nsrhs_probe_fma.restype = ctypes.c_int
+    lib.nsrhs_assemble_elmat.argtypes = [P, ctypes.POINTER(Params), P, P, P]
+    lib.nsrhs_assemble_elmat.restype = ctypes.c_int
     lib.nsrhs_lumped_mass.argtypes = [P, P, P]
     lib.nsrhs_lumped_mass.restype = ctypes.c_int
     lib.nsrhs_explicit_step.argtypes = [P, ctypes.POINTER(Params), ctypes.c_double, ctypes.c_int32,

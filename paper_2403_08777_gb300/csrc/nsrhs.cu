@@ -28,6 +28,7 @@
 #include "../../include/nsrhs.h"
 #include "blocks.cuh"
 #include "element.cuh"
+#include "elmat.cuh"
 
 struct nsrhs_mesh {
   int64_t n_nodes = 0, n_elems = 0;
@@ -426,6 +427,36 @@ __global__ void __launch_bounds__(kThreads)
     load_geometry(geom, E, e, c, inv_det, rh);
     double F[4][4];
     nsrhs::element_rhs<double, FLAGS>(c, inv_det, rh, u, p, P, F);
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) atomicAdd(rhs + k * N + v[a], F[a][k]);
+  }
+}
+
+// Element-matrix comparison kernel: the same RHS through a full 16x16
+// element matrix per tet (elmat.cuh), then the same atomic scatter.
+template <bool VREMAN>
+__global__ void __launch_bounds__(kThreads)
+    fwd_fp64_elmat_kernel(int64_t N, int64_t E, const int32_t* __restrict__ conn,
+                          const double* __restrict__ geom, const double* __restrict__ up,
+                          ElemParams<double> P, double* __restrict__ rhs) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int32_t v[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) v[a] = ldg(conn + a * E + e);
+    double u[4][3], p[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) u[a][i] = ldg(up + i * N + v[a]);
+      p[a] = ldg(up + 3 * N + v[a]);
+    }
+    double c[3][3], inv_det, rh;
+    load_geometry(geom, E, e, c, inv_det, rh);
+    double F[4][4];
+    nsrhs::element_rhs_by_matrix<VREMAN>(c, inv_det, rh, u, p, P, F);
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -909,6 +940,26 @@ nsrhs_status nsrhs_mesh_check_noalloc(int64_t n_nodes, int64_t n_elems, const do
                                                        ar_threshold, scratch);
   NSRHS_TRY(cudaGetLastError());
   check_reduce_kernel<<<1, kCheckThreads, 0, s>>>(grid, scratch, result_dev);
+  return cuda_status(cudaGetLastError());
+}
+
+nsrhs_status nsrhs_assemble_elmat(const nsrhs_mesh* m, const nsrhs_params* p, const double* up,
+                                  double* rhs, void* stream) {
+  if (!is_live(m) || !up || !rhs) return NSRHS_EINVAL;
+  nsrhs_status st = check_params(p);
+  if (st != NSRHS_OK) return st;
+  if (p->precision != NSRHS_FP64 || p->convection != NSRHS_CONVECTIVE ||
+      p->tau_mode != NSRHS_TAU_GAUSS)
+    return NSRHS_EUNSUPPORTED;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t N = m->n_nodes, E = m->n_elems;
+  NSRHS_TRY(cudaMemsetAsync(rhs, 0, sizeof(double) * 4 * N, s));
+  auto P = elem_params<double>(p);
+  const unsigned grid = grid_for(E, m->device, 16);
+  if (p->c_vreman != 0.0)
+    fwd_fp64_elmat_kernel<true><<<grid, kThreads, 0, s>>>(N, E, m->conn, m->geom, up, P, rhs);
+  else
+    fwd_fp64_elmat_kernel<false><<<grid, kThreads, 0, s>>>(N, E, m->conn, m->geom, up, P, rhs);
   return cuda_status(cudaGetLastError());
 }
 

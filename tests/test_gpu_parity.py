@@ -359,3 +359,17 @@ def test_unstructured_delaunay_mesh(dev, n, order):
     sk = m.assemble(up, ns.Params(rho=w.rho, mu=w.mu, convection="skew")).cpu().numpy()
     check_fp64(sk, oracle.assemble(w.coords, w.conn, w.up, w.rho, w.mu, skew=True))
     m.close()
+
+
+@pytest.mark.parametrize("cv", [0.0, 0.07])
+def test_element_matrix_path_matches_oracle(dev, cv):
+    """The element-matrix comparison path computes the same RHS."""
+    w = mg.make_workload(12, jitter=0.2, order="random", mu=1e-3, mag_max=2.0, c_vreman=cv)
+    coords, conn, up = on_dev(dev, w.coords, w.conn, w.up)
+    m = ns.Mesh(coords, conn)
+    x = m.assemble_elmat(up, ns.Params(rho=w.rho, mu=w.mu, c_vreman=cv)).cpu().numpy()
+    check_fp64(x, oracle.assemble(w.coords, w.conn, w.up, w.rho, w.mu, c_vreman=cv))
+    with pytest.raises(ns.NSRHSError) as ei:
+        m.assemble_elmat(up, ns.Params(convection="skew"))
+    assert ei.value.status == _abi.EUNSUPPORTED
+    m.close()
