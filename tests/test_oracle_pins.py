@@ -79,22 +79,30 @@ def test_closed_form_shear_tet(rho, mu, s, q):
     assert np.abs(F - ref).max() <= 1e-14 * scale
 
 
-@pytest.mark.parametrize("mu,s", [(1e-2, 1.0), (0.7, 0.25)])
-def test_closed_form_pressure_only(mu, s):
-    """u = 0, p = 1 at node 1: F_a,i = V p_bar dN_a/dx_i with p_bar = 1/4,
-    tau = h^2/(c1 mu), F_a,4 = -(V/4) * 4 tau dN_a/dx."""
-    X = ref_tet(s)
-    U = np.zeros((4, 4))
-    U[1, 3] = 1.0
-    F = oracle.element(X, U, 1.0, mu)
+def closed_form_pressure_only(mu, s, k):
+    """u = 0, p = 1 at node k (k = 1, 2, 3): grad p = e_k / s along axis k-1,
+    p_bar = 1/4, tau = h^2/(c1 mu); F_a,i = V/4 dN_a/dx_i,
+    F_a,4 = -(V/4) * 4 tau dN_a . grad p."""
     sd = D(s)
     V, tau = sd ** 3 / 6, sd ** 2 / (4 * D(mu))
+    F = [[D(0)] * 4 for _ in range(4)]
     for a in range(4):
         dN = [D(c) / sd for c in REF_DN[a]]
         for i in range(3):
-            assert abs(D(F[a, i]) - V / 4 * dN[i]) <= D("1e-15") * V / sd
-        exp4 = -V * tau * dN[0] / sd          # grad p = (1/s, 0, 0)
-        assert abs(D(F[a, 3]) - exp4) <= D("1e-14") * V * tau / sd ** 2
+            F[a][i] = V / 4 * dN[i]
+        F[a][3] = -V * tau * dN[k - 1] / sd
+    return np.array([[float(x) for x in row] for row in F])
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+@pytest.mark.parametrize("mu,s", [(1e-2, 1.0), (0.7, 0.25)])
+def test_closed_form_pressure_only(mu, s, k):
+    X = ref_tet(s)
+    U = np.zeros((4, 4))
+    U[k, 3] = 1.0
+    F = oracle.element(X, U, 1.0, mu)
+    ref = closed_form_pressure_only(mu, s, k)
+    assert np.abs(F - ref).max() <= 1e-14 * np.abs(ref).max()
 
 
 def test_closed_form_viscous_linear_velocity():
