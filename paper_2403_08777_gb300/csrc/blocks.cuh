@@ -24,8 +24,14 @@
 
 namespace nsrhs {
 
-constexpr int kBlockElems = 256;
-constexpr int kBlockSlots = 4 * kBlockElems;  // at most this many distinct nodes
+#ifndef NSRHS_BLOCK_ELEMS
+#define NSRHS_BLOCK_ELEMS 256
+#endif
+#ifndef NSRHS_BLOCK_MIN_CTAS_F32
+#define NSRHS_BLOCK_MIN_CTAS_F32 4
+#endif
+constexpr int kBlockElems = NSRHS_BLOCK_ELEMS;  // elements per block = threads per CTA
+constexpr int kBlockSlots = 4 * kBlockElems;     // at most this many distinct nodes
 
 // ---- setup ----
 
@@ -232,7 +238,7 @@ struct NodeSum<float> {
 // per SM help; the double kernel is bound by the FP64 pipe.
 template <class R>
 constexpr int block_kernel_min_ctas() {
-  return sizeof(R) == 4 ? 4 : 2;
+  return sizeof(R) == 4 ? NSRHS_BLOCK_MIN_CTAS_F32 : 2;
 }
 
 template <class R, int FLAGS>

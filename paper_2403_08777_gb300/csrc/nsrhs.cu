@@ -71,6 +71,15 @@ bool is_live(const nsrhs_mesh* m) {
 constexpr int kThreads = 128;
 constexpr int kGeomRows = 11;
 
+// Minimum resident CTAs per SM requested from the compiler (register cap) for
+// the FP64 element kernels; measured choices, overridable at build time.
+#ifndef NSRHS_FWD_MIN_CTAS
+#define NSRHS_FWD_MIN_CTAS 1
+#endif
+#ifndef NSRHS_VJP_MIN_CTAS
+#define NSRHS_VJP_MIN_CTAS 1
+#endif
+
 int sm_count(int device) {
   int n = 0;
   if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || n <= 0)
@@ -407,7 +416,7 @@ __device__ __forceinline__ void load_geometry(const R* __restrict__ geom, int64_
 // geometry, gathered nodal (u, p), register-resident element arithmetic,
 // immediate atomic scatter of the 16 entries.
 template <int FLAGS>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, NSRHS_FWD_MIN_CTAS)
     fwd_fp64_atomic_kernel(int64_t N, int64_t E, const int32_t* __restrict__ conn,
                            const double* __restrict__ geom, const double* __restrict__ up,
                            ElemParams<double> P, double* __restrict__ rhs) {
@@ -500,7 +509,7 @@ __global__ void __launch_bounds__(kThreads)
 // (the reverse of the scatter), recompute the element, run the reverse sweep,
 // scatter-add the gradient (the reverse of the gather).
 template <int FLAGS>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, NSRHS_VJP_MIN_CTAS)
     vjp_fp64_atomic_kernel(int64_t N, int64_t E, const int32_t* __restrict__ conn,
                            const double* __restrict__ geom, const double* __restrict__ up,
                            const double* __restrict__ cot, ElemParams<double> P,
@@ -860,7 +869,7 @@ nsrhs_status nsrhs_assemble(const nsrhs_mesh* m, const nsrhs_params* p, const vo
   if (block) {
     const int64_t nb = m->n_blocks;
     const unsigned grid = (unsigned)std::max<int64_t>(
-        1, std::min<int64_t>(nb, (int64_t)sm_count(m->device) * 4));
+        1, std::min<int64_t>(nb, (int64_t)sm_count(m->device) * 8));
     cudaError_t err = cudaSuccess;
     if (p->precision == NSRHS_FP64) {
       auto P = elem_params<double>(p);
