@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--unstructured", type=int, default=64,
                     help="also time a Delaunay mesh of an (n+1)^3 jittered lattice (0: skip)")
+    ap.add_argument("--locality", type=int, default=128,
+                    help="also time random vs RCM node order on an n^3-hex mesh (0: skip)")
     ap.add_argument("--sample-fwd", type=int, default=1 << 20,
                     help="oracle forward elements per host process")
     ap.add_argument("--sample-vjp", type=int, default=1 << 16,
@@ -450,6 +452,9 @@ def run_ours(args):
 
     if args.unstructured > 0:
         forms["unstructured"] = time_unstructured(args.unstructured, dev, stream, args)
+    if args.locality > 0:
+        forms["locality"] = time_locality(args.locality, dev, stream, args)
+    forms["vjp_64cube"] = time_vjp_64(dev, stream, args)
 
     dom = "vjp_fp64" if vjp_med >= fwd_med else "fwd_fp64"
     dom_ms = vjp_med if dom == "vjp_fp64" else fwd_med
@@ -514,6 +519,62 @@ def time_mixed(mesh, w, dev, stream, args, fp64_ms):
     ms = a.elapsed_time(b) / args.steps
     return {"ms": ms, "tets_per_s": w.n_elems / (ms * 1e-3), "fp64_ms": fp64_ms,
             "speedup_vs_fp64": fp64_ms / ms, "workload": w.name}
+
+
+def _timed(fn, dev, stream, args):
+    import torch
+    for _ in range(args.warmup):
+        fn()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(args.steps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    return a.elapsed_time(b) / args.steps
+
+
+def time_locality(n, dev, stream, args):
+    """n^3 hexes (rho 1, mu 1e-2, Taylor-Green + noise) with a random and an
+    RCM node order: FP64 and mixed forward rates (gather/scatter locality)."""
+    import torch
+    import paper_2403_08777_gb300 as ns
+    out = {}
+    for order in ("random", "rcm"):
+        w = mg.medium(order=order, n=n)
+        m = ns.Mesh(torch.from_numpy(w.coords).to(dev), torch.from_numpy(w.conn).to(dev))
+        up = torch.from_numpy(w.up).to(dev)
+        up32 = up.float()
+        o = torch.empty_like(up)
+        p = ns.Params(rho=w.rho, mu=w.mu)
+        pm = ns.Params(rho=w.rho, mu=w.mu, precision="mixed")
+        f = _timed(lambda: m.assemble(up, p, out=o), dev, stream, args)
+        x = _timed(lambda: m.assemble(up32, pm, out=o), dev, stream, args)
+        xa = _timed(lambda: m.assemble(up32, ns.Params(rho=w.rho, mu=w.mu, precision="mixed",
+                                                       scatter="atomic"), out=o),
+                    dev, stream, args)
+        out[order] = {"fwd_fp64_tets_per_s": w.n_elems / (f * 1e-3),
+                      "mixed_block_tets_per_s": w.n_elems / (x * 1e-3),
+                      "mixed_atomic_tets_per_s": w.n_elems / (xa * 1e-3),
+                      "bandwidth": mg.bandwidth(w.conn)}
+        m.close()
+    out["workload"] = f"kuhn{n}^3 (random vs rcm)"
+    return out
+
+
+def time_vjp_64(dev, stream, args):
+    """Adjoint throughput on the 64^3-hex mesh (1,572,864 tets)."""
+    import torch
+    import paper_2403_08777_gb300 as ns
+    w = mg.paper_scale(n=64, order="rcm")
+    m = ns.Mesh(torch.from_numpy(w.coords).to(dev), torch.from_numpy(w.conn).to(dev))
+    up = torch.from_numpy(w.up).to(dev)
+    cot = torch.from_numpy(mg.normal((4, w.n_nodes), seed=mg.SEED_COT)).to(dev)
+    o = torch.empty_like(up)
+    p = ns.Params(rho=w.rho, mu=w.mu)
+    v = _timed(lambda: m.assemble_vjp(up, cot, p, out=o), dev, stream, args)
+    m.close()
+    return {"workload": w.name, "n_tets": w.n_elems, "tets_per_s": w.n_elems / (v * 1e-3)}
 
 
 def time_unstructured(n, dev, stream, args):
