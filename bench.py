@@ -394,6 +394,22 @@ def run_ours(args):
         torch.cuda.synchronize(dev)
         vms = va.elapsed_time(vb) / max(2, args.steps // 2)
         forms[name] = {"ms": vms, "tets_per_s": w.n_elems / (vms * 1e-3), "variant": kw}
+    # mixed-precision adjoint (float sweep, double accumulation)
+    up32, cot32 = up.float(), cot.float()
+    pmx = ns.Params(rho=w.rho, mu=w.mu, c_vreman=w.c_vreman, precision="mixed")
+    for _ in range(2):
+        mesh.assemble_vjp(up32, cot32, pmx, out=grad)
+    ma, mb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ma.record(stream)
+    for _ in range(args.steps):
+        mesh.assemble_vjp(up32, cot32, pmx, out=grad)
+    mb.record(stream)
+    torch.cuda.synchronize(dev)
+    mvjp = ma.elapsed_time(mb) / args.steps
+    forms["vjp_mixed"] = {"ms": mvjp, "tets_per_s": w.n_elems / (mvjp * 1e-3),
+                          "speedup_vs_fp64_vjp": vjp_med / mvjp,
+                          "err_vs_oracle_32cube": mixed_vjp_error_32()}
+    del up32, cot32
     # element-matrix comparison path (the pre-restructuring form, Sec. V-A)
     mesh.assemble_elmat(up, p, out=rhs)
     ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -612,6 +628,23 @@ def time_unstructured(n, dev, stream, args):
             "vjp_fp64_tets_per_s": w.n_elems / (vjp * 1e-3),
             "mixed_tets_per_s": w.n_elems / (mix * 1e-3), "n_high_ar": info["n_high_ar"],
             "max_ar": info["max_ar"]}
+
+
+def mixed_vjp_error_32() -> float:
+    """Norm-wise error of the mixed adjoint against the oracle (complex-step
+    element Jacobians) on the 32^3 paper-scale-settings mesh."""
+    import torch
+    import oracle
+    import paper_2403_08777_gb300 as ns
+    w = mg.paper_scale(n=32, order="rcm")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    cot = mg.normal((4, w.n_nodes), seed=mg.SEED_COT)
+    m = ns.Mesh(torch.from_numpy(w.coords).to(dev), torch.from_numpy(w.conn).to(dev))
+    g = m.assemble_vjp(torch.from_numpy(w.up).to(dev).float(), torch.from_numpy(cot).to(dev).float(),
+                       ns.Params(rho=w.rho, mu=w.mu, precision="mixed")).cpu().numpy()
+    m.close()
+    ref = oracle.vjp(w.coords, w.conn, w.up, cot, w.rho, w.mu)
+    return float(np.linalg.norm(g - ref) / np.linalg.norm(ref))
 
 
 def mixed_error_64() -> float:

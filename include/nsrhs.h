@@ -149,13 +149,14 @@ nsrhs_status nsrhs_assemble(const nsrhs_mesh* m, const nsrhs_params* p, const vo
 
 /*
  * Vector-Jacobian product of the assembly: grad = (d rhs / d up)^T cot,
- * all [4][n_nodes] double, for NSRHS_FP64 parameters (precision must be
- * NSRHS_FP64). The element quantities are recomputed, not stored. grad is
- * overwritten. This is the adjoint of nsrhs_assemble with respect to the
- * nodal velocity and pressure; the mesh and parameters are constants.
+ * the adjoint of nsrhs_assemble with respect to the nodal velocity and
+ * pressure (the mesh and parameters are constants). NSRHS_FP64: up and cot
+ * [4][n_nodes] double. NSRHS_MIXED: up and cot [4][n_nodes] float, float
+ * reverse sweep, double accumulation. grad [4][n_nodes] double is
+ * overwritten. The element quantities are recomputed, not stored.
  */
-nsrhs_status nsrhs_assemble_vjp(const nsrhs_mesh* m, const nsrhs_params* p, const double* up,
-                                const double* cot, double* grad, void* stream);
+nsrhs_status nsrhs_assemble_vjp(const nsrhs_mesh* m, const nsrhs_params* p, const void* up,
+                                const void* cot, double* grad, void* stream);
 
 /*
  * The same RHS (FP64, convective form, tau at the Gauss points) computed the

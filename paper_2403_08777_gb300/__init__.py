@@ -133,10 +133,12 @@ class Mesh:
 
     def assemble_vjp(self, up: torch.Tensor, cot: torch.Tensor, params: Params | None = None, *,
                      out=None, **kw):
-        """(d rhs / d up)^T cot, all [4, N] float64."""
+        """(d rhs / d up)^T cot, [4, N] float64; up and cot float64 (fp64) or
+        float32 (precision='mixed')."""
         p = self._params(params, kw)
-        _require(up, "up", torch.float64, (4, self.n_nodes), self.device)
-        _require(cot, "cot", torch.float64, (4, self.n_nodes), self.device)
+        dt = torch.float32 if p.precision == "mixed" else torch.float64
+        _require(up, "up", dt, (4, self.n_nodes), self.device)
+        _require(cot, "cot", dt, (4, self.n_nodes), self.device)
         if out is None:
             out = torch.empty((4, self.n_nodes), dtype=torch.float64, device=self.device)
         else:

@@ -541,7 +541,62 @@ __global__ void __launch_bounds__(kThreads, NSRHS_VJP_MIN_CTAS)
   }
 }
 
+// Mixed-precision vector-Jacobian product: float (u, p), float cotangent,
+// float reverse sweep on the float geometry, double accumulation of the
+// gradient (integer widening, no FP64 instructions per entry).
+template <int FLAGS>
+__global__ void __launch_bounds__(kThreads)
+    vjp_mixed_atomic_kernel(int64_t N, int64_t E, const int32_t* __restrict__ conn,
+                            const float* __restrict__ geom_f, const float* __restrict__ up,
+                            const float* __restrict__ cot, ElemParams<float> P,
+                            double* __restrict__ grad) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int32_t v[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) v[a] = ldg(conn + a * E + e);
+    float u[4][3], p[4], w[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) u[a][i] = ldg(up + i * N + v[a]);
+      p[a] = ldg(up + 3 * N + v[a]);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) w[a][k] = ldg(cot + k * N + v[a]);
+    }
+    float c[3][3], inv_det, rh;
+    load_geometry(geom_f, E, e, c, inv_det, rh);
+    float gu[4][3], gp[4];
+    nsrhs::element_vjp<float, FLAGS>(c, inv_det, rh, u, p, w, P, gu, gp);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) atomicAdd(grad + i * N + v[a], nsrhs::widen_f32(gu[a][i]));
+      atomicAdd(grad + 3 * N + v[a], nsrhs::widen_f32(gp[a]));
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
+
+// Makes the mesh's device current for the duration of a call and restores
+// the caller's device afterwards (launches and pointers belong to one device).
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int device) {
+    if (cudaGetDevice(&prev) != cudaSuccess) {
+      ok = false;
+      prev = -1;
+      return;
+    }
+    if (prev != device) ok = cudaSetDevice(device) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
 
 // Calls f(std::integral_constant<int, FLAGS>) for the runtime formulation flags.
 template <class Fn>
@@ -858,6 +913,8 @@ nsrhs_status nsrhs_assemble(const nsrhs_mesh* m, const nsrhs_params* p, const vo
   nsrhs_status st = check_params(p);
   if (st != NSRHS_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
+  DeviceGuard dg(m->device);
+  if (!dg.ok) return NSRHS_ECUDA;
   const int64_t N = m->n_nodes, E = m->n_elems;
   const int flags = formulation_flags(p);
   NSRHS_TRY(cudaMemsetAsync(rhs, 0, sizeof(double) * 4 * N, s));
@@ -912,21 +969,30 @@ nsrhs_status nsrhs_assemble(const nsrhs_mesh* m, const nsrhs_params* p, const vo
   return cuda_status(cudaGetLastError());
 }
 
-nsrhs_status nsrhs_assemble_vjp(const nsrhs_mesh* m, const nsrhs_params* p, const double* up,
-                                const double* cot, double* grad, void* stream) {
+nsrhs_status nsrhs_assemble_vjp(const nsrhs_mesh* m, const nsrhs_params* p, const void* up,
+                                const void* cot, double* grad, void* stream) {
   if (!is_live(m) || !up || !cot || !grad) return NSRHS_EINVAL;
   nsrhs_status st = check_params(p);
   if (st != NSRHS_OK) return st;
-  if (p->precision != NSRHS_FP64) return NSRHS_EUNSUPPORTED;
   cudaStream_t s = (cudaStream_t)stream;
+  DeviceGuard dg(m->device);
+  if (!dg.ok) return NSRHS_ECUDA;
   const int64_t N = m->n_nodes, E = m->n_elems;
   NSRHS_TRY(cudaMemsetAsync(grad, 0, sizeof(double) * 4 * N, s));
-  auto P = elem_params<double>(p);
   const unsigned grid = grid_for(E, m->device, 16);
-  with_flags(formulation_flags(p), [&](auto fl) {
-    vjp_fp64_atomic_kernel<decltype(fl)::value>
-        <<<grid, kThreads, 0, s>>>(N, E, m->conn, m->geom, up, cot, P, grad);
-  });
+  if (p->precision == NSRHS_FP64) {
+    auto P = elem_params<double>(p);
+    with_flags(formulation_flags(p), [&](auto fl) {
+      vjp_fp64_atomic_kernel<decltype(fl)::value><<<grid, kThreads, 0, s>>>(
+          N, E, m->conn, m->geom, (const double*)up, (const double*)cot, P, grad);
+    });
+  } else {
+    auto P = elem_params<float>(p);
+    with_flags(formulation_flags(p), [&](auto fl) {
+      vjp_mixed_atomic_kernel<decltype(fl)::value><<<grid, kThreads, 0, s>>>(
+          N, E, m->conn, m->geom_f, (const float*)up, (const float*)cot, P, grad);
+    });
+  }
   return cuda_status(cudaGetLastError());
 }
 
@@ -961,6 +1027,8 @@ nsrhs_status nsrhs_assemble_elmat(const nsrhs_mesh* m, const nsrhs_params* p, co
       p->tau_mode != NSRHS_TAU_GAUSS)
     return NSRHS_EUNSUPPORTED;
   cudaStream_t s = (cudaStream_t)stream;
+  DeviceGuard dg(m->device);
+  if (!dg.ok) return NSRHS_ECUDA;
   const int64_t N = m->n_nodes, E = m->n_elems;
   NSRHS_TRY(cudaMemsetAsync(rhs, 0, sizeof(double) * 4 * N, s));
   auto P = elem_params<double>(p);
@@ -974,6 +1042,8 @@ nsrhs_status nsrhs_assemble_elmat(const nsrhs_mesh* m, const nsrhs_params* p, co
 
 nsrhs_status nsrhs_lumped_mass(const nsrhs_mesh* m, double* mass_dev, void* stream) {
   if (!is_live(m) || !mass_dev) return NSRHS_EINVAL;
+  DeviceGuard dg(m->device);
+  if (!dg.ok) return NSRHS_ECUDA;
   return cuda_status(cudaMemcpyAsync(mass_dev, m->mass, sizeof(double) * m->n_nodes,
                                      cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
 }
@@ -987,6 +1057,8 @@ nsrhs_status nsrhs_explicit_step(const nsrhs_mesh* m, const nsrhs_params* p, dou
   if (scheme != NSRHS_EULER && scheme != NSRHS_SSPRK3) return NSRHS_EINVAL;
   if (p->precision != NSRHS_FP64) return NSRHS_EUNSUPPORTED;
   cudaStream_t s = (cudaStream_t)stream;
+  DeviceGuard dg(m->device);
+  if (!dg.ok) return NSRHS_ECUDA;
   const int64_t N = m->n_nodes;
   double* F = work_dev;              // [4][N] stage RHS
   double* stage = work_dev + 4 * N;  // [4][N] stage state

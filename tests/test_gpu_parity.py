@@ -215,9 +215,8 @@ def test_mesh_errors(dev):
     with pytest.raises(ns.NSRHSError) as ei:
         m.assemble(up, ns.Params(mu=-1.0))        # invalid parameter
     assert ei.value.status == _abi.EINVAL
-    with pytest.raises(ns.NSRHSError) as ei:
-        m.assemble_vjp(up, up, ns.Params(precision="mixed"))
-    assert ei.value.status == _abi.EUNSUPPORTED
+    with pytest.raises(TypeError):
+        m.assemble_vjp(up, up, ns.Params(precision="mixed"))   # mixed takes float32
     m.close()
     with pytest.raises(RuntimeError):
         m.assemble(up)
@@ -372,4 +371,19 @@ def test_element_matrix_path_matches_oracle(dev, cv):
     with pytest.raises(ns.NSRHSError) as ei:
         m.assemble_elmat(up, ns.Params(convection="skew"))
     assert ei.value.status == _abi.EUNSUPPORTED
+    m.close()
+
+
+@pytest.mark.parametrize("cv,conv", [(0.0, "convective"), (0.07, "skew")])
+def test_mixed_precision_adjoint(dev, cv, conv):
+    """Float reverse sweep with double accumulation: within the adjoint's
+    1e-6 tolerance against the oracle's complex-step element Jacobians."""
+    w = mg.make_workload(20, jitter=0.3, order="rcm", mu=1e-3, mag_max=3.0, c_vreman=cv)
+    cot = mg.normal((4, w.n_nodes), seed=mg.SEED_COT)
+    ref = oracle.vjp(w.coords, w.conn, w.up, cot, w.rho, w.mu, c_vreman=cv, skew=conv == "skew")
+    coords, conn, up, cot_d = on_dev(dev, w.coords, w.conn, w.up, cot)
+    m = ns.Mesh(coords, conn)
+    p = ns.Params(rho=w.rho, mu=w.mu, c_vreman=cv, convection=conv, precision="mixed")
+    g = m.assemble_vjp(up.float(), cot_d.float(), p).cpu().numpy()
+    assert relerr(g, ref) <= TOL_VJP_FD, relerr(g, ref)
     m.close()
