@@ -47,6 +47,23 @@ constexpr int kVreman = 1;    // Vreman eddy viscosity on
 constexpr int kSkew = 2;      // skew-symmetric (energy-preserving) Galerkin convection
 constexpr int kTauElem = 4;   // one tau per element from the mean velocity
 
+// a * b + c as one fused multiply-add (so that the FP64 instruction count is
+// what the source says; the generic form serves the host flop census).
+template <class R>
+__device__ __forceinline__ R fmac(R a, R b, R c) {
+  return a * b + c;
+}
+#if defined(__CUDA_ARCH__)
+template <>
+__device__ __forceinline__ double fmac<double>(double a, double b, double c) {
+  return __fma_rn(a, b, c);
+}
+template <>
+__device__ __forceinline__ float fmac<float>(float a, float b, float c) {
+  return __fmaf_rn(a, b, c);
+}
+#endif
+
 template <class R>
 struct MathOps;
 
@@ -124,14 +141,14 @@ __device__ __forceinline__ void element_rhs(const R c[3][3], R inv_det, R rh, co
   R G[3][3], gp[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    R d1 = u[1][i] - u[0][i], d2 = u[2][i] - u[0][i], d3 = u[3][i] - u[0][i];
+    const R d1 = u[1][i] - u[0][i], d2 = u[2][i] - u[0][i], d3 = u[3][i] - u[0][i];
 #pragma unroll
-    for (int j = 0; j < 3; ++j) G[i][j] = d1 * c[0][j] + d2 * c[1][j] + d3 * c[2][j];
+    for (int j = 0; j < 3; ++j) G[i][j] = fmac(d3, c[2][j], fmac(d2, c[1][j], d1 * c[0][j]));
   }
   {
-    R d1 = p[1] - p[0], d2 = p[2] - p[0], d3 = p[3] - p[0];
+    const R d1 = p[1] - p[0], d2 = p[2] - p[0], d3 = p[3] - p[0];
 #pragma unroll
-    for (int j = 0; j < 3; ++j) gp[j] = d1 * c[0][j] + d2 * c[1][j] + d3 * c[2][j];
+    for (int j = 0; j < 3; ++j) gp[j] = fmac(d3, c[2][j], fmac(d2, c[1][j], d1 * c[0][j]));
   }
   R S[3];
 #pragma unroll
@@ -142,26 +159,24 @@ __device__ __forceinline__ void element_rhs(const R c[3][3], R inv_det, R rh, co
   R mu_eff = P.mu;
   if constexpr (VREMAN) {
     // alpha = G^T, beta = h^2 G G^T; B and A from Gh, rescaled by detJ and h.
-    R A = (R)0;
+    R bm[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-      for (int j = 0; j < 3; ++j) A += G[i][j] * G[i][j];
-    R b00 = G[0][0] * G[0][0] + G[0][1] * G[0][1] + G[0][2] * G[0][2];
-    R b11 = G[1][0] * G[1][0] + G[1][1] * G[1][1] + G[1][2] * G[1][2];
-    R b22 = G[2][0] * G[2][0] + G[2][1] * G[2][1] + G[2][2] * G[2][2];
-    R b01 = G[0][0] * G[1][0] + G[0][1] * G[1][1] + G[0][2] * G[1][2];
-    R b02 = G[0][0] * G[2][0] + G[0][1] * G[2][1] + G[0][2] * G[2][2];
-    R b12 = G[1][0] * G[2][0] + G[1][1] * G[2][1] + G[1][2] * G[2][2];
-    R B = b00 * b11 - b01 * b01 + b00 * b22 - b02 * b02 + b11 * b22 - b12 * b12;
+      for (int j = i; j < 3; ++j)
+        bm[i][j] = fmac(G[i][2], G[j][2], fmac(G[i][1], G[j][1], G[i][0] * G[j][0]));
+    const R A = (bm[0][0] + bm[1][1]) + bm[2][2];
+    R B = fmac(bm[1][1], bm[2][2], -(bm[1][2] * bm[1][2]));
+    B = fmac(bm[0][0], bm[2][2], fmac(-bm[0][2], bm[0][2], B));
+    B = fmac(bm[0][0], bm[1][1], fmac(-bm[0][1], bm[0][1], B));
     if (A > (R)0 && B > (R)0) {
       // nu_t = c h^2 sqrt(B_G/A_G) = c h^2 inv_det sqrt(B/A)
-      R h2 = M::rcp(rh * rh);
-      mu_eff = P.mu + P.rho * P.c_vreman * h2 * inv_det * M::sqrt_(B * M::rcp(A));
+      const R h2 = M::rcp(rh * rh);
+      mu_eff = fmac(P.rho * P.c_vreman, h2 * inv_det * M::sqrt_(B * M::rcp(A)), P.mu);
     }
   }
-  const R k1 = P.c1 * mu_eff * rh * rh;
-  const R k2 = P.c2 * P.rho * rh;
+  const R k1 = (P.c1 * mu_eff) * (rh * rh);
+  const R k2 = (P.c2 * P.rho) * rh;
 
   // Gauss points: u_g = QB S_u + (QA - QB) u_g-node.
   R stau = (R)0, T[3] = {(R)0, (R)0, (R)0};
@@ -172,17 +187,17 @@ __device__ __forceinline__ void element_rhs(const R c[3][3], R inv_det, R rh, co
   for (int i = 0; i < 3; ++i) bS[i] = (R)kQB * S[i];
   R tau_e = (R)0;
   if constexpr (TAUE) {
-    const R sm = (S[0] * S[0] + S[1] * S[1] + S[2] * S[2]) * (R)0.0625;
-    tau_e = M::rcp(k1 + k2 * M::sqrt_(sm));
+    const R sm = fmac(S[2], S[2], fmac(S[1], S[1], S[0] * S[0])) * (R)0.0625;
+    tau_e = M::rcp(fmac(k2, M::sqrt_(sm), k1));
   }
 #pragma unroll
   for (int g = 0; g < 4; ++g) {
     R ug[3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) ug[i] = bS[i] + (R)(kQA - kQB) * u[g][i];
+    for (int i = 0; i < 3; ++i) ug[i] = fmac((R)(kQA - kQB), u[g][i], bS[i]);
     if constexpr (!TAUE) {
-      R s = ug[0] * ug[0] + ug[1] * ug[1] + ug[2] * ug[2];
-      R tau = M::rcp(k1 + k2 * M::sqrt_(s));
+      const R s = fmac(ug[2], ug[2], fmac(ug[1], ug[1], ug[0] * ug[0]));
+      const R tau = M::rcp(fmac(k2, M::sqrt_(s), k1));
       stau += tau;
       R tu[3];
 #pragma unroll
@@ -190,20 +205,20 @@ __device__ __forceinline__ void element_rhs(const R c[3][3], R inv_det, R rh, co
         tu[i] = tau * ug[i];
         T[i] += tu[i];
       }
-      Q00 += tu[0] * ug[0];
-      Q11 += tu[1] * ug[1];
-      Q22 += tu[2] * ug[2];
-      Q01 += tu[0] * ug[1];
-      Q02 += tu[0] * ug[2];
-      Q12 += tu[1] * ug[2];
+      Q00 = fmac(tu[0], ug[0], Q00);
+      Q11 = fmac(tu[1], ug[1], Q11);
+      Q22 = fmac(tu[2], ug[2], Q22);
+      Q01 = fmac(tu[0], ug[1], Q01);
+      Q02 = fmac(tu[0], ug[2], Q02);
+      Q12 = fmac(tu[1], ug[2], Q12);
     }
     if constexpr (SKEW || TAUE) {
-      P00 += ug[0] * ug[0];
-      P11 += ug[1] * ug[1];
-      P22 += ug[2] * ug[2];
-      P01 += ug[0] * ug[1];
-      P02 += ug[0] * ug[2];
-      P12 += ug[1] * ug[2];
+      P00 = fmac(ug[0], ug[0], P00);
+      P11 = fmac(ug[1], ug[1], P11);
+      P22 = fmac(ug[2], ug[2], P22);
+      P01 = fmac(ug[0], ug[1], P01);
+      P02 = fmac(ug[0], ug[2], P02);
+      P12 = fmac(ug[1], ug[2], P12);
     }
   }
   if constexpr (TAUE) {
@@ -224,9 +239,9 @@ __device__ __forceinline__ void element_rhs(const R c[3][3], R inv_det, R rh, co
   const R a2 = -s6 * (P.rho * P.rho * (R)0.25);
   const R a1 = -s6 * mu_eff;
   const R b4 = -s6 * (P.rho * (R)0.25);
-  const R Qp[3][3] = {{a2 * Q00 + a1, a2 * Q01, a2 * Q02},
-                      {a2 * Q01, a2 * Q11 + a1, a2 * Q12},
-                      {a2 * Q02, a2 * Q12, a2 * Q22 + a1}};
+  const R Qp[3][3] = {{fmac(a2, Q00, a1), a2 * Q01, a2 * Q02},
+                      {a2 * Q01, fmac(a2, Q11, a1), a2 * Q12},
+                      {a2 * Q02, a2 * Q12, fmac(a2, Q22, a1)}};
   const R pb6 = psum * (R)(1.0 / 24.0);
   const R Pm[3][3] = {{P00, P01, P02}, {P01, P11, P12}, {P02, P12, P22}};
   const R r48 = P.rho * (R)(1.0 / 48.0);
@@ -236,24 +251,29 @@ __device__ __forceinline__ void element_rhs(const R c[3][3], R inv_det, R rh, co
     const R gq = b4 * gp[i];
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-      R acc = (i == j) ? gq * T[j] + pb6 : gq * T[j];
-      if constexpr (SKEW) acc = r48 * Pm[i][j] + acc;
-      acc = G[i][0] * Qp[0][j] + acc;
-      acc = G[i][1] * Qp[1][j] + acc;
-      K[i][j] = G[i][2] * Qp[2][j] + acc;
+      R acc = (i == j) ? fmac(gq, T[j], pb6) : gq * T[j];
+      if constexpr (SKEW) acc = fmac(r48, Pm[i][j], acc);
+      acc = fmac(G[i][0], Qp[0][j], acc);
+      acc = fmac(G[i][1], Qp[1][j], acc);
+      K[i][j] = fmac(G[i][2], Qp[2][j], acc);
     }
   }
   // Rs = inv_det/24 (rho Gh T + stau gph)
   const R s24 = inv_det * (R)(1.0 / 24.0);
-  const R sT = s24 * P.rho;
   const R sg = s24 * stau;
+  R sTT[3];
+  {
+    const R sT = s24 * P.rho;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) sTT[j] = sT * T[j];
+  }
   R Rs[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     R acc = sg * gp[i];
-    acc = (sT * T[0]) * G[i][0] + acc;
-    acc = (sT * T[1]) * G[i][1] + acc;
-    Rs[i] = (sT * T[2]) * G[i][2] + acc;
+    acc = fmac(sTT[0], G[i][0], acc);
+    acc = fmac(sTT[1], G[i][1], acc);
+    Rs[i] = fmac(sTT[2], G[i][2], acc);
   }
   const R cont0 = trG * (R)(-1.0 / 24.0);
   // Galerkin convection -(rho/120) Gh (S_u + u_a) = Gh v_a, v_a = m120 u_a + m120 S_u
@@ -269,34 +289,25 @@ __device__ __forceinline__ void element_rhs(const R c[3][3], R inv_det, R rh, co
     const R* ca = c[a - 1];
     R v[3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) v[i] = m120 * u[a][i] + mS[i];
+    for (int i = 0; i < 3; ++i) v[i] = fmac(m120, u[a][i], mS[i]);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      R y = K[i][0] * ca[0];
-      y = K[i][1] * ca[1] + y;
-      y = K[i][2] * ca[2] + y;
+      const R y = fmac(K[i][2], ca[2], fmac(K[i][1], ca[1], K[i][0] * ca[0]));
       ysum[i] += y;
-      R f = G[i][0] * v[0] + y;
-      f = G[i][1] * v[1] + f;
-      F[a][i] = G[i][2] * v[2] + f;
+      F[a][i] = fmac(G[i][2], v[2], fmac(G[i][1], v[1], fmac(G[i][0], v[0], y)));
     }
-    R f3 = cont0 - ca[0] * Rs[0];
-    f3 = f3 - ca[1] * Rs[1];
-    F[a][3] = f3 - ca[2] * Rs[2];
+    F[a][3] = fmac(-ca[2], Rs[2], fmac(-ca[1], Rs[1], fmac(-ca[0], Rs[0], cont0)));
     csum += F[a][3];
   }
   {
     R v[3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) v[i] = m120 * u[0][i] + mS[i];
+    for (int i = 0; i < 3; ++i) v[i] = fmac(m120, u[0][i], mS[i]);
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      R f = G[i][0] * v[0] - ysum[i];
-      f = G[i][1] * v[1] + f;
-      F[0][i] = G[i][2] * v[2] + f;
-    }
+    for (int i = 0; i < 3; ++i)
+      F[0][i] = fmac(G[i][2], v[2], fmac(G[i][1], v[1], fmac(G[i][0], v[0], -ysum[i])));
     // sum_a c_a = 0: the continuity entries sum to 4 cont0
-    F[0][3] = (R)4 * cont0 - csum;
+    F[0][3] = fmac((R)4, cont0, -csum);
   }
 }
 

@@ -83,6 +83,15 @@ int main() {
                 vreman ? "vreman" : "plain", fwd, fwd_sfu, vjp, vjp_sfu, geo, geo_sfu);
     std::printf("%s instructions (FMA-contracted estimate): fwd %ld vjp %ld\n",
                 vreman ? "vreman" : "plain", fwd_inst, vjp_inst);
+    {
+      Cnt F2[4][4];
+      reset();
+      if (vreman) element_rhs<Cnt, kVreman>(c, inv_det, rh, u, p, P, F2);
+      else element_rhs<Cnt, 0>(c, inv_det, rh, u, p, P, F2);
+      std::printf("%s fwd detail: add %ld mul %ld fused %ld sfu %ld -> fma %ld, lone mul %ld, "
+                  "lone add %ld\n", vreman ? "vreman" : "plain", g_add, g_mul, g_fused, g_sfu,
+                  g_fused, g_mul - g_fused, g_add - g_fused);
+    }
   }
   return 0;
 }
