@@ -272,7 +272,10 @@ def run_ours(args):
     up = torch.from_numpy(w.up).to(dev)
     cot_h = mg.normal((4, w.n_nodes), seed=mg.SEED_COT)
     cot = torch.from_numpy(cot_h).to(dev)
-    mesh = ns.Mesh(coords, conn)
+    t_mesh = time.perf_counter()
+    mesh = ns.Mesh(coords, conn, colour=True)
+    torch.cuda.synchronize(dev)
+    t_mesh = time.perf_counter() - t_mesh
     del coords, conn
     p = ns.Params(rho=w.rho, mu=w.mu, c_vreman=w.c_vreman)
     rhs = torch.empty((4, w.n_nodes), dtype=torch.float64, device=dev)
@@ -439,6 +442,9 @@ def run_ours(args):
     forms["explicit_step_ssprk3"] = {"ms": rk_ms, "assemblies_per_step": 3,
                                      "overhead_vs_3_assemblies": rk_ms / (3 * fwd_med)}
     del u_step, work
+    forms["scatter_sweep"] = time_scatter_sweep(mesh, w, up, cot, dev, stream, args, fwd_med,
+                                                vjp_med)
+    forms["scatter_sweep"]["mesh_setup_s_with_colouring"] = t_mesh
     if not args.no_mixed:
         forms["mixed_same_mesh"] = time_mixed(mesh, w, dev, stream, args, fwd_med)
         mesh.close()
@@ -548,6 +554,49 @@ def _timed(fn, dev, stream, args):
     b.record(stream)
     torch.cuda.synchronize(dev)
     return a.elapsed_time(b) / args.steps
+
+
+def time_scatter_sweep(mesh, w, up, cot, dev, stream, args, fwd_ms, vjp_ms):
+    """Every scatter on the same mesh: the FP64 and mixed forward with
+    atomics, element blocks and element colouring (deterministic), the FP64
+    and mixed adjoint with atomics and colouring. Rates in tets/s."""
+    import torch
+    import paper_2403_08777_gb300 as ns
+
+    def mk(**kw):
+        return ns.Params(rho=w.rho, mu=w.mu, c_vreman=w.c_vreman, **kw)
+
+    def rate(ms):
+        return w.n_elems / (ms * 1e-3)
+
+    o = torch.empty_like(up)
+    up32, cot32 = up.float(), cot.float()
+    res = {"n_colours": mesh.info()["n_colours"],
+           "fwd_fp64": {"atomic": rate(fwd_ms)}, "fwd_mixed": {},
+           "vjp_fp64": {"atomic": rate(vjp_ms)}, "vjp_mixed": {}}
+    res["n_block_colours"] = mesh.info()["n_block_colours"]
+    for sc in ("block", "colour", "block_colour"):
+        res["fwd_fp64"][sc] = rate(_timed(lambda: mesh.assemble(up, mk(scatter=sc), out=o),
+                                          dev, stream, args))
+    for sc in ("atomic", "block", "colour", "block_colour"):
+        res["fwd_mixed"][sc] = rate(_timed(
+            lambda: mesh.assemble(up32, mk(scatter=sc, precision="mixed"), out=o),
+            dev, stream, args))
+    res["vjp_fp64"]["colour"] = rate(_timed(
+        lambda: mesh.assemble_vjp(up, cot, mk(scatter="colour"), out=o), dev, stream, args))
+    for sc in ("atomic", "colour"):
+        res["vjp_mixed"][sc] = rate(_timed(
+            lambda: mesh.assemble_vjp(up32, cot32, mk(scatter=sc, precision="mixed"), out=o),
+            dev, stream, args))
+    # the coloured paths are deterministic: two calls, bitwise equal
+    same = True
+    for sc in ("colour", "block_colour"):
+        for u in (up, up32):
+            pr = mk(scatter=sc, precision="fp64" if u is up else "mixed")
+            a = mesh.assemble(u, pr).clone()
+            same = same and bool(torch.equal(a, mesh.assemble(u, pr)))
+    res["colour_bitwise_reproducible"] = same
+    return res
 
 
 def time_locality(n, dev, stream, args):

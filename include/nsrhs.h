@@ -69,8 +69,21 @@ typedef enum {
 typedef enum {
   NSRHS_SCATTER_AUTO = 0,   /* the measured fastest for the precision */
   NSRHS_SCATTER_ATOMIC = 1, /* one double-precision atomic add per entry */
-  NSRHS_SCATTER_BLOCK = 2   /* per-block node-local accumulation in shared
-                               memory, one atomic per (block, node, component) */
+  NSRHS_SCATTER_BLOCK = 2,  /* per-block node-local accumulation in shared
+                               memory, one atomic per (block, node, component);
+                               forward only (the adjoint uses atomics) */
+  NSRHS_SCATTER_COLOUR = 3, /* element colouring: elements sharing a node have
+                               different colours; one launch per colour with
+                               plain read-modify-write adds, in a fixed order,
+                               so results are bitwise reproducible. Needs a mesh
+                               created with opts.colour = 1, else
+                               NSRHS_EUNSUPPORTED */
+  NSRHS_SCATTER_BLOCK_COLOUR = 4 /* BLOCK with its blocks coloured (blocks
+                               sharing a node differ): per-block node sums in a
+                               fixed order, then plain read-modify-write adds,
+                               one launch per block colour; bitwise
+                               reproducible. The adjoint uses the element
+                               colouring. Needs opts.colour = 1 */
 } nsrhs_scatter;
 
 typedef enum {
@@ -103,6 +116,14 @@ typedef struct {
                           geometry; 10 by default. AR = l_max S / (6 sqrt(6) V)
                           (l_max longest edge, S surface, V volume; 1 for the
                           regular tet). */
+  int32_t colour;      /* 1: also colour the elements and keep a colour-major
+                          copy of the connectivity and geometry (about 150
+                          bytes per element more) for NSRHS_SCATTER_COLOUR,
+                          and colour the element blocks for
+                          NSRHS_SCATTER_BLOCK_COLOUR; 0 (default): not. Greedy colouring, at most 128
+                          colours, else mesh creation returns
+                          NSRHS_EUNSUPPORTED. */
+  int32_t reserved;    /* must be 0 */
 } nsrhs_mesh_opts;
 
 /* Read-only facts about a created mesh. */
@@ -113,13 +134,15 @@ typedef struct {
   int64_t block_elems;    /* elements per block */
   int64_t device_bytes;   /* device memory held by the mesh */
   double min_detj, max_ar;
+  int64_t n_colours;      /* colours of the COLOUR scatter; 0 if not built */
+  int64_t n_block_colours; /* block colours of BLOCK_COLOUR; 0 if not built */
 } nsrhs_mesh_info;
 
 /* Fill *p with rho=1, mu=1e-2, c_vreman=0, c1=4, c2=2, FP64, AUTO,
    convective form, tau at the Gauss points. */
 void nsrhs_params_default(nsrhs_params* p);
 
-/* Fill *o with ar_threshold = 10. */
+/* Fill *o with ar_threshold = 10, colour = 0. */
 void nsrhs_mesh_opts_default(nsrhs_mesh_opts* o);
 
 /*
@@ -127,7 +150,9 @@ void nsrhs_mesh_opts_default(nsrhs_mesh_opts* o);
  * The library copies both (the caller may free them afterwards), checks on
  * the device that every index is in range and every element has detJ > 0,
  * classifies elements by aspect ratio, and builds the element blocks of the
- * BLOCK scatter. opts may be NULL (defaults). Synchronises `stream` once.
+ * BLOCK scatter (and, with opts->colour, the colouring of the COLOUR
+ * scatter). opts may be NULL (defaults). Synchronises `stream` (with
+ * colouring, once per colouring round).
  * 1 <= n_nodes < 2^31, 1 <= n_elems < 2^31.
  * On error *out is set to NULL and nothing is leaked.
  */
@@ -142,7 +167,9 @@ nsrhs_status nsrhs_mesh_get_info(const nsrhs_mesh* m, nsrhs_mesh_info* info);
  * up is [4][n_nodes] double for NSRHS_FP64 and [4][n_nodes] float for
  * NSRHS_MIXED; rhs [4][n_nodes] double is overwritten (zeroed, then summed
  * into). up and rhs must not overlap. The summation order of the atomic
- * adds is unspecified, so results agree with a serial sum to rounding only.
+ * adds is unspecified, so results agree with a serial sum to rounding only;
+ * with NSRHS_SCATTER_COLOUR the order is fixed and repeated calls give
+ * bitwise identical results.
  */
 nsrhs_status nsrhs_assemble(const nsrhs_mesh* m, const nsrhs_params* p, const void* up,
                             double* rhs, void* stream);
@@ -197,6 +224,29 @@ nsrhs_status nsrhs_lumped_mass(const nsrhs_mesh* m, double* mass_dev, void* stre
  */
 nsrhs_status nsrhs_explicit_step(const nsrhs_mesh* m, const nsrhs_params* p, double dt,
                                  int32_t scheme, double* up_dev, double* work_dev, void* stream);
+
+/*
+ * Per element, in the caller's element order, into out_dev [n_elems] int32
+ * (device memory, overwritten):
+ *   NSRHS_ELEMENT_COLOUR        its colour in the COLOUR scatter, 0 .. n_colours - 1
+ *                               (two elements that share a node never have the
+ *                               same colour);
+ *   NSRHS_ELEMENT_BLOCK_COLOUR  the colour of its block in the BLOCK_COLOUR
+ *                               scatter, 0 .. n_block_colours - 1 (elements of
+ *                               two different blocks of the same colour never
+ *                               share a node);
+ *   NSRHS_ELEMENT_BLOCK         the index of its block.
+ * Only for a mesh created with opts.colour = 1, else NSRHS_EUNSUPPORTED;
+ * another `which`: NSRHS_EINVAL. For checking and inspection.
+ */
+typedef enum {
+  NSRHS_ELEMENT_COLOUR = 0,
+  NSRHS_ELEMENT_BLOCK_COLOUR = 1,
+  NSRHS_ELEMENT_BLOCK = 2
+} nsrhs_element_property;
+
+nsrhs_status nsrhs_mesh_element_colours(const nsrhs_mesh* m, int32_t which, int32_t* out_dev,
+                                        void* stream);
 
 /* Free the mesh and its device memory. NULL-safe. Synchronises the device
    memory it frees (cudaFree semantics). */

@@ -24,7 +24,8 @@ __all__ = ["Mesh", "Params", "assemble", "assemble_host", "StepPipeline", "NSRHS
            "NSRHSError", "NativeLibraryMissing", "load_library"]
 
 _PREC = {"fp64": _abi.FP64, "mixed": _abi.MIXED}
-_SCAT = {"auto": _abi.SCATTER_AUTO, "atomic": _abi.SCATTER_ATOMIC, "block": _abi.SCATTER_BLOCK}
+_SCAT = {"auto": _abi.SCATTER_AUTO, "atomic": _abi.SCATTER_ATOMIC, "block": _abi.SCATTER_BLOCK,
+         "colour": _abi.SCATTER_COLOUR, "block_colour": _abi.SCATTER_BLOCK_COLOUR}
 _CONV = {"convective": _abi.CONVECTIVE, "skew": _abi.SKEW}
 _TAU = {"gauss": _abi.TAU_GAUSS, "element": _abi.TAU_ELEMENT}
 
@@ -76,7 +77,10 @@ def _require(t: torch.Tensor, name: str, dtype, shape, device=None):
 class Mesh:
     """A tetrahedral mesh resident on one GPU (library-owned device copies)."""
 
-    def __init__(self, coords: torch.Tensor, conn: torch.Tensor, ar_threshold: float = 10.0):
+    def __init__(self, coords: torch.Tensor, conn: torch.Tensor, ar_threshold: float = 10.0,
+                 colour: bool = False):
+        """colour=True also colours the elements for scatter='colour'
+        (deterministic, bitwise reproducible assembly)."""
         lib = _abi.load()
         if coords.dim() != 2 or coords.shape[0] != 3 or conn.dim() != 2 or conn.shape[0] != 4:
             raise ValueError("coords must be [3, N] and conn [4, E]")
@@ -84,7 +88,7 @@ class Mesh:
         _require(conn, "conn", torch.int32, conn.shape, coords.device)
         self.device = coords.device
         self.n_nodes, self.n_elems = int(coords.shape[1]), int(conn.shape[1])
-        opts = _abi.MeshOpts(float(ar_threshold))
+        opts = _abi.MeshOpts(float(ar_threshold), 1 if colour else 0, 0)
         handle = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             st = lib.nsrhs_mesh_create(self.n_nodes, self.n_elems, ctypes.c_void_p(coords.data_ptr()),
@@ -104,6 +108,23 @@ class Mesh:
         _abi.check(_abi.load().nsrhs_mesh_get_info(self.handle, ctypes.byref(inf)),
                    "nsrhs_mesh_get_info")
         return {f: getattr(inf, f) for f, _ in _abi.MeshInfo._fields_}
+
+    def element_colours(self, which: str = "element") -> torch.Tensor:
+        """Per element in the caller's element order, [E] int32 (a mesh created
+        with colour=True): which='element' its colour (COLOUR scatter),
+        'block_colour' its block's colour (BLOCK_COLOUR scatter), 'block' its
+        block index."""
+        kinds = {"element": _abi.ELEMENT_COLOUR, "block_colour": _abi.ELEMENT_BLOCK_COLOUR,
+                 "block": _abi.ELEMENT_BLOCK}
+        if which not in kinds:
+            raise ValueError(f"which must be one of {sorted(kinds)}")
+        out = torch.empty(self.n_elems, dtype=torch.int32, device=self.device)
+        with torch.cuda.device(self.device):
+            st = _abi.load().nsrhs_mesh_element_colours(self.handle, kinds[which],
+                                                         ctypes.c_void_p(out.data_ptr()),
+                                                         _stream_handle(self.device))
+        _abi.check(st, "nsrhs_mesh_element_colours")
+        return out
 
     def _params(self, params: Params | None, kw) -> Params:
         if params is None:

@@ -8,17 +8,18 @@ from . import build as _build
 
 OK, EINVAL, ENOMEM, EMESH, ECUDA, EUNSUPPORTED = 0, 1, 2, 3, 4, 5
 FP64, MIXED = 0, 1
-SCATTER_AUTO, SCATTER_ATOMIC, SCATTER_BLOCK = 0, 1, 2
+SCATTER_AUTO, SCATTER_ATOMIC, SCATTER_BLOCK, SCATTER_COLOUR, SCATTER_BLOCK_COLOUR = 0, 1, 2, 3, 4
 CONVECTIVE, SKEW = 0, 1
 TAU_GAUSS, TAU_ELEMENT = 0, 1
 EULER, SSPRK3 = 0, 1
+ELEMENT_COLOUR, ELEMENT_BLOCK_COLOUR, ELEMENT_BLOCK = 0, 1, 2
 
 # Every symbol include/nsrhs.h declares.
 EXPORTED = ("nsrhs_params_default", "nsrhs_mesh_opts_default", "nsrhs_mesh_create",
             "nsrhs_mesh_get_info", "nsrhs_assemble", "nsrhs_assemble_vjp", "nsrhs_destroy",
             "nsrhs_status_string", "nsrhs_probe_fma", "nsrhs_mesh_check_noalloc",
             "nsrhs_probe_special", "nsrhs_lumped_mass", "nsrhs_explicit_step",
-            "nsrhs_assemble_elmat")
+            "nsrhs_assemble_elmat", "nsrhs_mesh_element_colours")
 
 
 class Params(ctypes.Structure):
@@ -29,7 +30,8 @@ class Params(ctypes.Structure):
 
 
 class MeshOpts(ctypes.Structure):
-    _fields_ = [("ar_threshold", ctypes.c_double)]
+    _fields_ = [("ar_threshold", ctypes.c_double), ("colour", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class MeshCheckResult(ctypes.Structure):
@@ -42,7 +44,8 @@ class MeshInfo(ctypes.Structure):
     _fields_ = [("n_nodes", ctypes.c_int64), ("n_elems", ctypes.c_int64),
                 ("n_high_ar", ctypes.c_int64), ("n_blocks", ctypes.c_int64),
                 ("block_elems", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
-                ("min_detj", ctypes.c_double), ("max_ar", ctypes.c_double)]
+                ("min_detj", ctypes.c_double), ("max_ar", ctypes.c_double),
+                ("n_colours", ctypes.c_int64), ("n_block_colours", ctypes.c_int64)]
 
 
 _lib = None
@@ -95,6 +98,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.nsrhs_probe_special.restype = ctypes.c_int
     lib.nsrhs_mesh_check_noalloc.argtypes = [I64, I64, P, P, ctypes.c_double, P, P]
     lib.nsrhs_mesh_check_noalloc.restype = ctypes.c_int
+    lib.nsrhs_mesh_element_colours.argtypes = [P, ctypes.c_int32, P, P]
+    lib.nsrhs_mesh_element_colours.restype = ctypes.c_int
     _lib = lib
     return lib
 

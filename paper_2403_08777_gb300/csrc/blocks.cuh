@@ -232,33 +232,58 @@ struct NodeSum<float> {
 
 // Forward assembly with block-staged gathers and scatters; R is the element
 // arithmetic type (float: mixed form, double: FP64 form). Dynamic shared
-// memory: 8 * kBlockSlots * sizeof(R) bytes.
+// memory: block_kernel_smem<R, COLOUR>() bytes.
 // Resident CTAs per SM the compiler must allow (register cap): the float
 // kernel is latency-bound between its barrier-separated phases, so more CTAs
 // per SM help; the double kernel is bound by the FP64 pipe.
+template <class R, bool COLOUR>
+constexpr size_t block_kernel_smem() {
+  return 8 * kBlockSlots * sizeof(R) + (COLOUR ? 4 * kBlockElems * sizeof(double) : 0);
+}
+
 template <class R>
 constexpr int block_kernel_min_ctas() {
   return sizeof(R) == 4 ? NSRHS_BLOCK_MIN_CTAS_F32 : 2;
 }
 
-template <class R, int FLAGS>
+//
+// COLOUR: the CTAs process the blocks order[i0 .. i1) of one block colour (no
+// two share a node), and each node's sums are added with a plain
+// read-modify-write; otherwise blocks 0 .. n_blocks - 1 with atomics.
+template <class R, int FLAGS, bool COLOUR = false>
 __global__ void __launch_bounds__(kBlockElems, block_kernel_min_ctas<R>())
     fwd_block_kernel(int64_t N, int64_t E, int64_t n_blocks, const int64_t* __restrict__ node_off,
                      const int32_t* __restrict__ nodes, const uint16_t* __restrict__ runs,
                      const uint16_t* __restrict__ slots, const uint16_t* __restrict__ lconn,
                      const R* __restrict__ geom, const R* __restrict__ up, ElemParams<R> P,
-                     double* __restrict__ rhs) {
+                     double* __restrict__ rhs, const int32_t* __restrict__ order = nullptr,
+                     int64_t i0 = 0, int64_t i1 = 0) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R* su = reinterpret_cast<R*>(smem_raw);  // [4][kBlockSlots] nodal u, v, w, p
   R* sF = su + 4 * kBlockSlots;             // [4][kBlockSlots] element entries by slot
+  // COLOUR only: [4][kBlockElems] prefetched RHS of each thread's first node
+  double* sold = reinterpret_cast<double*>(sF + 4 * kBlockSlots);
   const int tid = threadIdx.x;
-  for (int64_t b = blockIdx.x; b < n_blocks; b += gridDim.x) {
+  const int64_t first = COLOUR ? i0 : 0, last = COLOUR ? i1 : n_blocks;
+  for (int64_t i = first + blockIdx.x; i < last; i += gridDim.x) {
+    const int64_t b = COLOUR ? (int64_t)__ldg(order + i) : i;
     const int64_t off = node_off[b];
     const int nb = (int)(node_off[b + 1] - off);
     for (int j = tid; j < nb; j += kBlockElems) {
       const int64_t v = __ldg(nodes + off + j);
 #pragma unroll
       for (int k = 0; k < 4; ++k) su[k * kBlockSlots + j] = __ldg(up + k * N + v);
+    }
+    // COLOUR: the current RHS of this thread's first node, loaded into shared
+    // memory now so that the loads overlap the element arithmetic (no other
+    // CTA of this launch writes it, and earlier colours' launches have
+    // completed).
+    if constexpr (COLOUR) {
+      if (tid < nb) {
+        const int64_t v = __ldg(nodes + off + tid);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) sold[k * kBlockElems + tid] = rhs[k * N + v];
+      }
     }
     __syncthreads();
     const int64_t e = b * kBlockElems + tid;
@@ -299,7 +324,13 @@ __global__ void __launch_bounds__(kBlockElems, block_kernel_min_ctas<R>())
         for (int k = 0; k < 4; ++k) acc[k].add(sF[k * kBlockSlots + sl]);
       }
 #pragma unroll
-      for (int k = 0; k < 4; ++k) atomicAdd(rhs + k * N + v, acc[k].value());
+      for (int k = 0; k < 4; ++k) {
+        if constexpr (COLOUR)
+          rhs[k * N + v] = (j == tid ? sold[k * kBlockElems + tid] : rhs[k * N + v]) +
+                           acc[k].value();
+        else
+          atomicAdd(rhs + k * N + v, acc[k].value());
+      }
     }
     __syncthreads();
   }

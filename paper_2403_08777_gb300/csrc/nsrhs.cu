@@ -27,6 +27,7 @@
 
 #include "../../include/nsrhs.h"
 #include "blocks.cuh"
+#include "colour.cuh"
 #include "element.cuh"
 #include "elmat.cuh"
 
@@ -52,6 +53,20 @@ struct nsrhs_mesh {
   uint16_t* blk_lconn = nullptr;    // [4][E]
   double* inv_mass = nullptr;       // [N] 1 / lumped mass
   double* mass = nullptr;           // [N] lumped mass sum_e V_e / 4
+  // Colour-major copy for the COLOUR scatter (colour.cuh), built when the
+  // mesh options ask for it: the elements stably sorted by colour, colour k
+  // at [col_off[k], col_off[k + 1]).
+  std::vector<int64_t> col_off;
+  int32_t* col_conn = nullptr;      // [4][E]
+  double* col_geom = nullptr;       // [kGeomRows][E]
+  float* col_geom_f = nullptr;      // [kGeomRows][E]
+  uint8_t* colour = nullptr;        // [E] colour of each element (Morton order)
+  int32_t* elem_order = nullptr;    // [E] caller's index of each element (Morton order)
+  // Block colouring for the BLOCK_COLOUR scatter: block colour k is the
+  // blocks bcol_order[bcol_off[k] .. bcol_off[k + 1]).
+  std::vector<int64_t> bcol_off;
+  int32_t* bcol_order = nullptr;    // [n_blocks]
+  uint8_t* bcolour = nullptr;       // [n_blocks] colour of each block
   nsrhs_mesh_info info{};
   std::vector<void*> allocations;
 };
@@ -412,35 +427,69 @@ __device__ __forceinline__ void load_geometry(const R* __restrict__ geom, int64_
   rh = ldg(geom + 10 * E + e);
 }
 
-// FP64 forward, one element per thread: streamed connectivity and cached
-// geometry, gathered nodal (u, p), register-resident element arithmetic,
-// immediate atomic scatter of the 16 entries.
+// One element's entry into the global sum: an atomic add, or, in a coloured
+// launch (no other thread of the launch touches this node), a plain
+// read-modify-write.
+template <bool COLOUR>
+__device__ __forceinline__ void scatter_add(double* p, double x) {
+  if constexpr (COLOUR)
+    *p += x;
+  else
+    atomicAdd(p, x);
+}
+
+// FP64 forward of element e: streamed connectivity and cached geometry,
+// gathered nodal (u, p), register-resident element arithmetic, immediate
+// scatter of the 16 entries.
+template <int FLAGS, bool COLOUR>
+__device__ __forceinline__ void fwd_fp64_element(int64_t N, int64_t E, int64_t e,
+                                                 const int32_t* __restrict__ conn,
+                                                 const double* __restrict__ geom,
+                                                 const double* __restrict__ up,
+                                                 const ElemParams<double>& P,
+                                                 double* __restrict__ rhs) {
+  int32_t v[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) v[a] = ldg(conn + a * E + e);
+  double u[4][3], p[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) u[a][i] = ldg(up + i * N + v[a]);
+    p[a] = ldg(up + 3 * N + v[a]);
+  }
+  double c[3][3], inv_det, rh;
+  load_geometry(geom, E, e, c, inv_det, rh);
+  double F[4][4];
+  nsrhs::element_rhs<double, FLAGS>(c, inv_det, rh, u, p, P, F);
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) scatter_add<COLOUR>(rhs + k * N + v[a], F[a][k]);
+}
+
+// FP64 forward, one element per thread over all elements, atomic scatter.
 template <int FLAGS>
 __global__ void __launch_bounds__(kThreads, NSRHS_FWD_MIN_CTAS)
     fwd_fp64_atomic_kernel(int64_t N, int64_t E, const int32_t* __restrict__ conn,
                            const double* __restrict__ geom, const double* __restrict__ up,
                            ElemParams<double> P, double* __restrict__ rhs) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    int32_t v[4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) v[a] = ldg(conn + a * E + e);
-    double u[4][3], p[4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-#pragma unroll
-      for (int i = 0; i < 3; ++i) u[a][i] = ldg(up + i * N + v[a]);
-      p[a] = ldg(up + 3 * N + v[a]);
-    }
-    double c[3][3], inv_det, rh;
-    load_geometry(geom, E, e, c, inv_det, rh);
-    double F[4][4];
-    nsrhs::element_rhs<double, FLAGS>(c, inv_det, rh, u, p, P, F);
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int k = 0; k < 4; ++k) atomicAdd(rhs + k * N + v[a], F[a][k]);
-  }
+       e += (int64_t)gridDim.x * blockDim.x)
+    fwd_fp64_element<FLAGS, false>(N, E, e, conn, geom, up, P, rhs);
+}
+
+// FP64 forward over the elements [e0, e1) of one colour of the colour-major
+// copy (row stride E), plain read-modify-write scatter.
+template <int FLAGS>
+__global__ void __launch_bounds__(kThreads, NSRHS_FWD_MIN_CTAS)
+    fwd_fp64_colour_kernel(int64_t N, int64_t E, int64_t e0, int64_t e1,
+                           const int32_t* __restrict__ conn, const double* __restrict__ geom,
+                           const double* __restrict__ up, ElemParams<double> P,
+                           double* __restrict__ rhs) {
+  for (int64_t e = e0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < e1;
+       e += (int64_t)gridDim.x * blockDim.x)
+    fwd_fp64_element<FLAGS, true>(N, E, e, conn, geom, up, P, rhs);
 }
 
 // Element-matrix comparison kernel: the same RHS through a full 16x16
@@ -473,41 +522,94 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
-// Mixed form: float (u, p) and float element arithmetic on the cached
-// geometry (computed in double for every element, so the determinant and
-// inverse of high-aspect-ratio elements are double-accurate), double global
-// accumulation; float results are widened to double with integer operations.
+// Mixed form of element e: float (u, p) and float element arithmetic on the
+// cached geometry (computed in double for every element, so the determinant
+// and inverse of high-aspect-ratio elements are double-accurate), double
+// global accumulation; float results are widened to double with integer
+// operations.
+template <int FLAGS, bool COLOUR>
+__device__ __forceinline__ void fwd_mixed_element(int64_t N, int64_t E, int64_t e,
+                                                  const int32_t* __restrict__ conn,
+                                                  const float* __restrict__ geom_f,
+                                                  const float* __restrict__ up,
+                                                  const ElemParams<float>& P,
+                                                  double* __restrict__ rhs) {
+  int32_t v[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) v[a] = ldg(conn + a * E + e);
+  float u[4][3], p[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) u[a][i] = ldg(up + i * N + v[a]);
+    p[a] = ldg(up + 3 * N + v[a]);
+  }
+  float c[3][3], inv_det, rh;
+  load_geometry(geom_f, E, e, c, inv_det, rh);
+  float F[4][4];
+  nsrhs::element_rhs<float, FLAGS>(c, inv_det, rh, u, p, P, F);
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) scatter_add<COLOUR>(rhs + k * N + v[a], nsrhs::widen_f32(F[a][k]));
+}
+
 template <int FLAGS>
 __global__ void __launch_bounds__(kThreads)
     fwd_mixed_atomic_kernel(int64_t N, int64_t E, const int32_t* __restrict__ conn,
                             const float* __restrict__ geom_f, const float* __restrict__ up,
                             ElemParams<float> P, double* __restrict__ rhs) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    int32_t v[4];
+       e += (int64_t)gridDim.x * blockDim.x)
+    fwd_mixed_element<FLAGS, false>(N, E, e, conn, geom_f, up, P, rhs);
+}
+
+template <int FLAGS>
+__global__ void __launch_bounds__(kThreads)
+    fwd_mixed_colour_kernel(int64_t N, int64_t E, int64_t e0, int64_t e1,
+                            const int32_t* __restrict__ conn, const float* __restrict__ geom_f,
+                            const float* __restrict__ up, ElemParams<float> P,
+                            double* __restrict__ rhs) {
+  for (int64_t e = e0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < e1;
+       e += (int64_t)gridDim.x * blockDim.x)
+    fwd_mixed_element<FLAGS, true>(N, E, e, conn, geom_f, up, P, rhs);
+}
+
+// FP64 vector-Jacobian product of element e: gather the cotangent at the
+// element's nodes (the reverse of the scatter), recompute the element, run
+// the reverse sweep, scatter-add the gradient (the reverse of the gather).
+template <int FLAGS, bool COLOUR>
+__device__ __forceinline__ void vjp_fp64_element(int64_t N, int64_t E, int64_t e,
+                                                 const int32_t* __restrict__ conn,
+                                                 const double* __restrict__ geom,
+                                                 const double* __restrict__ up,
+                                                 const double* __restrict__ cot,
+                                                 const ElemParams<double>& P,
+                                                 double* __restrict__ grad) {
+  int32_t v[4];
 #pragma unroll
-    for (int a = 0; a < 4; ++a) v[a] = ldg(conn + a * E + e);
-    float u[4][3], p[4];
+  for (int a = 0; a < 4; ++a) v[a] = ldg(conn + a * E + e);
+  double u[4][3], p[4], w[4][4];
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
+  for (int a = 0; a < 4; ++a) {
 #pragma unroll
-      for (int i = 0; i < 3; ++i) u[a][i] = ldg(up + i * N + v[a]);
-      p[a] = ldg(up + 3 * N + v[a]);
-    }
-    float c[3][3], inv_det, rh;
-    load_geometry(geom_f, E, e, c, inv_det, rh);
-    float F[4][4];
-    nsrhs::element_rhs<float, FLAGS>(c, inv_det, rh, u, p, P, F);
+    for (int i = 0; i < 3; ++i) u[a][i] = ldg(up + i * N + v[a]);
+    p[a] = ldg(up + 3 * N + v[a]);
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int k = 0; k < 4; ++k) w[a][k] = ldg(cot + k * N + v[a]);
+  }
+  double c[3][3], inv_det, rh;
+  load_geometry(geom, E, e, c, inv_det, rh);
+  double gu[4][3], gp[4];
+  nsrhs::element_vjp<double, FLAGS>(c, inv_det, rh, u, p, w, P, gu, gp);
 #pragma unroll
-      for (int k = 0; k < 4; ++k) atomicAdd(rhs + k * N + v[a], nsrhs::widen_f32(F[a][k]));
+  for (int a = 0; a < 4; ++a) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) scatter_add<COLOUR>(grad + i * N + v[a], gu[a][i]);
+    scatter_add<COLOUR>(grad + 3 * N + v[a], gp[a]);
   }
 }
 
-// FP64 vector-Jacobian product: gather the cotangent at the element's nodes
-// (the reverse of the scatter), recompute the element, run the reverse sweep,
-// scatter-add the gradient (the reverse of the gather).
 template <int FLAGS>
 __global__ void __launch_bounds__(kThreads, NSRHS_VJP_MIN_CTAS)
     vjp_fp64_atomic_kernel(int64_t N, int64_t E, const int32_t* __restrict__ conn,
@@ -515,35 +617,57 @@ __global__ void __launch_bounds__(kThreads, NSRHS_VJP_MIN_CTAS)
                            const double* __restrict__ cot, ElemParams<double> P,
                            double* __restrict__ grad) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    int32_t v[4];
+       e += (int64_t)gridDim.x * blockDim.x)
+    vjp_fp64_element<FLAGS, false>(N, E, e, conn, geom, up, cot, P, grad);
+}
+
+template <int FLAGS>
+__global__ void __launch_bounds__(kThreads, NSRHS_VJP_MIN_CTAS)
+    vjp_fp64_colour_kernel(int64_t N, int64_t E, int64_t e0, int64_t e1,
+                           const int32_t* __restrict__ conn, const double* __restrict__ geom,
+                           const double* __restrict__ up, const double* __restrict__ cot,
+                           ElemParams<double> P, double* __restrict__ grad) {
+  for (int64_t e = e0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < e1;
+       e += (int64_t)gridDim.x * blockDim.x)
+    vjp_fp64_element<FLAGS, true>(N, E, e, conn, geom, up, cot, P, grad);
+}
+
+// Mixed-precision vector-Jacobian product of element e: float (u, p), float
+// cotangent, float reverse sweep on the float geometry, double accumulation
+// of the gradient.
+template <int FLAGS, bool COLOUR>
+__device__ __forceinline__ void vjp_mixed_element(int64_t N, int64_t E, int64_t e,
+                                                  const int32_t* __restrict__ conn,
+                                                  const float* __restrict__ geom_f,
+                                                  const float* __restrict__ up,
+                                                  const float* __restrict__ cot,
+                                                  const ElemParams<float>& P,
+                                                  double* __restrict__ grad) {
+  int32_t v[4];
 #pragma unroll
-    for (int a = 0; a < 4; ++a) v[a] = ldg(conn + a * E + e);
-    double u[4][3], p[4], w[4][4];
+  for (int a = 0; a < 4; ++a) v[a] = ldg(conn + a * E + e);
+  float u[4][3], p[4], w[4][4];
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
+  for (int a = 0; a < 4; ++a) {
 #pragma unroll
-      for (int i = 0; i < 3; ++i) u[a][i] = ldg(up + i * N + v[a]);
-      p[a] = ldg(up + 3 * N + v[a]);
+    for (int i = 0; i < 3; ++i) u[a][i] = ldg(up + i * N + v[a]);
+    p[a] = ldg(up + 3 * N + v[a]);
 #pragma unroll
-      for (int k = 0; k < 4; ++k) w[a][k] = ldg(cot + k * N + v[a]);
-    }
-    double c[3][3], inv_det, rh;
-    load_geometry(geom, E, e, c, inv_det, rh);
-    double gu[4][3], gp[4];
-    nsrhs::element_vjp<double, FLAGS>(c, inv_det, rh, u, p, w, P, gu, gp);
+    for (int k = 0; k < 4; ++k) w[a][k] = ldg(cot + k * N + v[a]);
+  }
+  float c[3][3], inv_det, rh;
+  load_geometry(geom_f, E, e, c, inv_det, rh);
+  float gu[4][3], gp[4];
+  nsrhs::element_vjp<float, FLAGS>(c, inv_det, rh, u, p, w, P, gu, gp);
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
+  for (int a = 0; a < 4; ++a) {
 #pragma unroll
-      for (int i = 0; i < 3; ++i) atomicAdd(grad + i * N + v[a], gu[a][i]);
-      atomicAdd(grad + 3 * N + v[a], gp[a]);
-    }
+    for (int i = 0; i < 3; ++i)
+      scatter_add<COLOUR>(grad + i * N + v[a], nsrhs::widen_f32(gu[a][i]));
+    scatter_add<COLOUR>(grad + 3 * N + v[a], nsrhs::widen_f32(gp[a]));
   }
 }
 
-// Mixed-precision vector-Jacobian product: float (u, p), float cotangent,
-// float reverse sweep on the float geometry, double accumulation of the
-// gradient (integer widening, no FP64 instructions per entry).
 template <int FLAGS>
 __global__ void __launch_bounds__(kThreads)
     vjp_mixed_atomic_kernel(int64_t N, int64_t E, const int32_t* __restrict__ conn,
@@ -551,30 +675,19 @@ __global__ void __launch_bounds__(kThreads)
                             const float* __restrict__ cot, ElemParams<float> P,
                             double* __restrict__ grad) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    int32_t v[4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) v[a] = ldg(conn + a * E + e);
-    float u[4][3], p[4], w[4][4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-#pragma unroll
-      for (int i = 0; i < 3; ++i) u[a][i] = ldg(up + i * N + v[a]);
-      p[a] = ldg(up + 3 * N + v[a]);
-#pragma unroll
-      for (int k = 0; k < 4; ++k) w[a][k] = ldg(cot + k * N + v[a]);
-    }
-    float c[3][3], inv_det, rh;
-    load_geometry(geom_f, E, e, c, inv_det, rh);
-    float gu[4][3], gp[4];
-    nsrhs::element_vjp<float, FLAGS>(c, inv_det, rh, u, p, w, P, gu, gp);
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-#pragma unroll
-      for (int i = 0; i < 3; ++i) atomicAdd(grad + i * N + v[a], nsrhs::widen_f32(gu[a][i]));
-      atomicAdd(grad + 3 * N + v[a], nsrhs::widen_f32(gp[a]));
-    }
-  }
+       e += (int64_t)gridDim.x * blockDim.x)
+    vjp_mixed_element<FLAGS, false>(N, E, e, conn, geom_f, up, cot, P, grad);
+}
+
+template <int FLAGS>
+__global__ void __launch_bounds__(kThreads)
+    vjp_mixed_colour_kernel(int64_t N, int64_t E, int64_t e0, int64_t e1,
+                            const int32_t* __restrict__ conn, const float* __restrict__ geom_f,
+                            const float* __restrict__ up, const float* __restrict__ cot,
+                            ElemParams<float> P, double* __restrict__ grad) {
+  for (int64_t e = e0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < e1;
+       e += (int64_t)gridDim.x * blockDim.x)
+    vjp_mixed_element<FLAGS, true>(N, E, e, conn, geom_f, up, cot, P, grad);
 }
 
 // ---------------------------------------------------------------------------
@@ -638,7 +751,8 @@ nsrhs_status check_params(const nsrhs_params* p) {
       !std::isfinite(p->c_vreman) || !std::isfinite(p->c1) || !std::isfinite(p->c2))
     return NSRHS_EINVAL;
   if (p->precision != NSRHS_FP64 && p->precision != NSRHS_MIXED) return NSRHS_EINVAL;
-  if (p->scatter < NSRHS_SCATTER_AUTO || p->scatter > NSRHS_SCATTER_BLOCK) return NSRHS_EINVAL;
+  if (p->scatter < NSRHS_SCATTER_AUTO || p->scatter > NSRHS_SCATTER_BLOCK_COLOUR)
+    return NSRHS_EINVAL;
   if (p->convection != NSRHS_CONVECTIVE && p->convection != NSRHS_SKEW) return NSRHS_EINVAL;
   if (p->tau_mode != NSRHS_TAU_GAUSS && p->tau_mode != NSRHS_TAU_ELEMENT) return NSRHS_EINVAL;
   return NSRHS_OK;
@@ -687,7 +801,10 @@ struct DevBuf {
   }
 };
 
-nsrhs_status morton_reorder(nsrhs_mesh* m, cudaStream_t s) {
+// Sorts the elements by the Morton code of their centroids (conn is permuted
+// in place); if keep_order is not NULL it receives the caller's index of
+// each element in the new order.
+nsrhs_status morton_reorder(nsrhs_mesh* m, int32_t* keep_order, cudaStream_t s) {
   const int64_t N = m->n_nodes, E = m->n_elems;
   DevBuf box, keys, keys2, ids, ids2, tmp, conn2;
   NSRHS_TRY(box.alloc(6 * sizeof(unsigned long long)));
@@ -726,6 +843,8 @@ nsrhs_status morton_reorder(nsrhs_mesh* m, cudaStream_t s) {
       E, m->conn, ids2.as<int32_t>(), conn2.as<int32_t>());
   NSRHS_TRY(cudaGetLastError());
   NSRHS_TRY(cudaMemcpyAsync(m->conn, conn2.p, 4 * E * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+  if (keep_order)
+    NSRHS_TRY(cudaMemcpyAsync(keep_order, ids2.p, E * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
   NSRHS_TRY(cudaStreamSynchronize(s));
   return NSRHS_OK;
 }
@@ -764,6 +883,159 @@ nsrhs_status build_blocks(nsrhs_mesh* m, cudaStream_t s) {
       1, E, m->conn, nullptr, m->blk_node_off, m->blk_nodes, m->blk_runs, m->blk_slots,
       m->blk_lconn);
   NSRHS_TRY(cudaGetLastError());
+  return NSRHS_OK;
+}
+
+// Colours the elements (colour.cuh), checks the colouring independently and
+// builds the colour-major copy of the connectivity and cached geometry.
+nsrhs_status build_colouring(nsrhs_mesh* m, cudaStream_t s) {
+  using ull = unsigned long long;
+  const int64_t N = m->n_nodes, E = m->n_elems;
+  nsrhs_status st;
+  if ((st = mesh_alloc(m, &m->colour, (size_t)E)) != NSRHS_OK) return st;
+  DevBuf claim, used, counters, counts, ids, ids_sorted, keys_sorted, tmp;
+  NSRHS_TRY(claim.alloc(N * sizeof(ull)));
+  NSRHS_TRY(used.alloc(2 * N * sizeof(ull)));
+  NSRHS_TRY(counters.alloc(2 * sizeof(ull)));
+  NSRHS_TRY(cudaMemsetAsync(m->colour, nsrhs::kUncoloured, (size_t)E, s));
+  NSRHS_TRY(cudaMemsetAsync(used.p, 0, 2 * N * sizeof(ull), s));
+  NSRHS_TRY(cudaMemsetAsync(counters.p, 0, 2 * sizeof(ull), s));
+  const unsigned grid = grid_for(E, m->device, 8);
+  ull hc[2] = {0, 0};
+  while (hc[0] < (ull)E) {
+    const ull before = hc[0];
+    NSRHS_TRY(cudaMemsetAsync(claim.p, 0xFF, N * sizeof(ull), s));
+    nsrhs::colour_claim_kernel<<<grid, kThreads, 0, s>>>(E, m->conn, m->colour, claim.as<ull>());
+    NSRHS_TRY(cudaGetLastError());
+    nsrhs::colour_accept_kernel<<<grid, kThreads, 0, s>>>(E, m->conn, claim.as<ull>(),
+                                                          used.as<ull>(), m->colour,
+                                                          counters.as<ull>());
+    NSRHS_TRY(cudaGetLastError());
+    NSRHS_TRY(cudaMemcpyAsync(hc, counters.p, sizeof(hc), cudaMemcpyDeviceToHost, s));
+    NSRHS_TRY(cudaStreamSynchronize(s));
+    if (hc[1] != 0) return NSRHS_EUNSUPPORTED;  // needs more than kMaxColours colours
+    if (hc[0] == before) return NSRHS_ECUDA;    // no progress: cannot happen
+  }
+  // independent check: no colour twice at a node
+  NSRHS_TRY(cudaMemsetAsync(used.p, 0, 2 * N * sizeof(ull), s));
+  NSRHS_TRY(cudaMemsetAsync(counters.p, 0, 2 * sizeof(ull), s));
+  nsrhs::colour_check_kernel<<<grid, kThreads, 0, s>>>(E, m->conn, m->colour, used.as<ull>(),
+                                                       counters.as<ull>());
+  NSRHS_TRY(cudaGetLastError());
+  NSRHS_TRY(counts.alloc(nsrhs::kMaxColours * sizeof(ull)));
+  NSRHS_TRY(cudaMemsetAsync(counts.p, 0, nsrhs::kMaxColours * sizeof(ull), s));
+  nsrhs::colour_count_kernel<<<grid, kThreads, 0, s>>>(E, m->colour, counts.as<ull>());
+  NSRHS_TRY(cudaGetLastError());
+  ull hcount[nsrhs::kMaxColours];
+  NSRHS_TRY(cudaMemcpyAsync(hc, counters.p, sizeof(hc), cudaMemcpyDeviceToHost, s));
+  NSRHS_TRY(cudaMemcpyAsync(hcount, counts.p, sizeof(hcount), cudaMemcpyDeviceToHost, s));
+  NSRHS_TRY(cudaStreamSynchronize(s));
+  if (hc[0] != 0) return NSRHS_ECUDA;
+  int n_col = 0;
+  for (int k = 0; k < nsrhs::kMaxColours; ++k)
+    if (hcount[k]) n_col = k + 1;
+  m->col_off.assign(n_col + 1, 0);
+  for (int k = 0; k < n_col; ++k) m->col_off[k + 1] = m->col_off[k] + (int64_t)hcount[k];
+  if (m->col_off[n_col] != E) return NSRHS_ECUDA;
+  // colour-major order: a stable sort of the element indices by colour
+  NSRHS_TRY(ids.alloc(E * sizeof(int32_t)));
+  NSRHS_TRY(ids_sorted.alloc(E * sizeof(int32_t)));
+  NSRHS_TRY(keys_sorted.alloc((size_t)E));
+  nsrhs::iota_kernel<<<grid, kThreads, 0, s>>>(E, ids.as<int32_t>());
+  NSRHS_TRY(cudaGetLastError());
+  size_t tmp_bytes = 0;
+  NSRHS_TRY(cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, m->colour, keys_sorted.as<uint8_t>(),
+                                            ids.as<int32_t>(), ids_sorted.as<int32_t>(), (int)E, 0,
+                                            8, s));
+  NSRHS_TRY(tmp.alloc(tmp_bytes));
+  NSRHS_TRY(cub::DeviceRadixSort::SortPairs(tmp.p, tmp_bytes, m->colour, keys_sorted.as<uint8_t>(),
+                                            ids.as<int32_t>(), ids_sorted.as<int32_t>(), (int)E, 0,
+                                            8, s));
+  if ((st = mesh_alloc(m, &m->col_conn, 4 * (size_t)E)) != NSRHS_OK) return st;
+  if ((st = mesh_alloc(m, &m->col_geom, kGeomRows * (size_t)E)) != NSRHS_OK) return st;
+  if ((st = mesh_alloc(m, &m->col_geom_f, kGeomRows * (size_t)E)) != NSRHS_OK) return st;
+  const int32_t* perm = ids_sorted.as<int32_t>();
+  nsrhs::permute_rows_kernel<int32_t><<<grid, kThreads, 0, s>>>(4, E, perm, m->conn, m->col_conn);
+  NSRHS_TRY(cudaGetLastError());
+  nsrhs::permute_rows_kernel<double><<<grid, kThreads, 0, s>>>(kGeomRows, E, perm, m->geom,
+                                                               m->col_geom);
+  NSRHS_TRY(cudaGetLastError());
+  nsrhs::permute_rows_kernel<float><<<grid, kThreads, 0, s>>>(kGeomRows, E, perm, m->geom_f,
+                                                              m->col_geom_f);
+  NSRHS_TRY(cudaGetLastError());
+  NSRHS_TRY(cudaStreamSynchronize(s));
+  m->info.n_colours = n_col;
+  return NSRHS_OK;
+}
+
+// Colours the element blocks (colour.cuh), checks the colouring and lists the
+// blocks of each colour.
+nsrhs_status build_block_colouring(nsrhs_mesh* m, cudaStream_t s) {
+  using ull = unsigned long long;
+  const int64_t N = m->n_nodes, nb = m->n_blocks;
+  nsrhs_status st;
+  if ((st = mesh_alloc(m, &m->bcolour, (size_t)nb)) != NSRHS_OK) return st;
+  DevBuf claim, used, counters, counts, ids, keys_sorted, tmp;
+  NSRHS_TRY(claim.alloc(N * sizeof(ull)));
+  NSRHS_TRY(used.alloc(2 * N * sizeof(ull)));
+  NSRHS_TRY(counters.alloc(2 * sizeof(ull)));
+  NSRHS_TRY(cudaMemsetAsync(m->bcolour, nsrhs::kUncoloured, (size_t)nb, s));
+  NSRHS_TRY(cudaMemsetAsync(used.p, 0, 2 * N * sizeof(ull), s));
+  NSRHS_TRY(cudaMemsetAsync(counters.p, 0, 2 * sizeof(ull), s));
+  // one warp per block
+  const unsigned grid = grid_for(32 * nb, m->device, 8);
+  ull hc[2] = {0, 0};
+  while (hc[0] < (ull)nb) {
+    const ull before = hc[0];
+    NSRHS_TRY(cudaMemsetAsync(claim.p, 0xFF, N * sizeof(ull), s));
+    nsrhs::block_colour_claim_kernel<<<grid, kThreads, 0, s>>>(
+        nb, m->blk_node_off, m->blk_nodes, m->bcolour, claim.as<ull>());
+    NSRHS_TRY(cudaGetLastError());
+    nsrhs::block_colour_accept_kernel<<<grid, kThreads, 0, s>>>(
+        nb, m->blk_node_off, m->blk_nodes, claim.as<ull>(), used.as<ull>(), m->bcolour,
+        counters.as<ull>());
+    NSRHS_TRY(cudaGetLastError());
+    NSRHS_TRY(cudaMemcpyAsync(hc, counters.p, sizeof(hc), cudaMemcpyDeviceToHost, s));
+    NSRHS_TRY(cudaStreamSynchronize(s));
+    if (hc[1] != 0) return NSRHS_EUNSUPPORTED;  // needs more than kMaxColours colours
+    if (hc[0] == before) return NSRHS_ECUDA;    // no progress: cannot happen
+  }
+  NSRHS_TRY(cudaMemsetAsync(used.p, 0, 2 * N * sizeof(ull), s));
+  NSRHS_TRY(cudaMemsetAsync(counters.p, 0, 2 * sizeof(ull), s));
+  nsrhs::block_colour_check_kernel<<<grid, kThreads, 0, s>>>(
+      nb, m->blk_node_off, m->blk_nodes, m->bcolour, used.as<ull>(), counters.as<ull>());
+  NSRHS_TRY(cudaGetLastError());
+  NSRHS_TRY(counts.alloc(nsrhs::kMaxColours * sizeof(ull)));
+  NSRHS_TRY(cudaMemsetAsync(counts.p, 0, nsrhs::kMaxColours * sizeof(ull), s));
+  const unsigned grid1 = grid_for(nb, m->device, 8);
+  nsrhs::colour_count_kernel<<<grid1, kThreads, 0, s>>>(nb, m->bcolour, counts.as<ull>());
+  NSRHS_TRY(cudaGetLastError());
+  ull hcount[nsrhs::kMaxColours];
+  NSRHS_TRY(cudaMemcpyAsync(hc, counters.p, sizeof(hc), cudaMemcpyDeviceToHost, s));
+  NSRHS_TRY(cudaMemcpyAsync(hcount, counts.p, sizeof(hcount), cudaMemcpyDeviceToHost, s));
+  NSRHS_TRY(cudaStreamSynchronize(s));
+  if (hc[0] != 0) return NSRHS_ECUDA;
+  int n_col = 0;
+  for (int k = 0; k < nsrhs::kMaxColours; ++k)
+    if (hcount[k]) n_col = k + 1;
+  m->bcol_off.assign(n_col + 1, 0);
+  for (int k = 0; k < n_col; ++k) m->bcol_off[k + 1] = m->bcol_off[k] + (int64_t)hcount[k];
+  if (m->bcol_off[n_col] != nb) return NSRHS_ECUDA;
+  if ((st = mesh_alloc(m, &m->bcol_order, (size_t)nb)) != NSRHS_OK) return st;
+  NSRHS_TRY(ids.alloc(nb * sizeof(int32_t)));
+  NSRHS_TRY(keys_sorted.alloc((size_t)nb));
+  nsrhs::iota_kernel<<<grid1, kThreads, 0, s>>>(nb, ids.as<int32_t>());
+  NSRHS_TRY(cudaGetLastError());
+  size_t tmp_bytes = 0;
+  NSRHS_TRY(cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, m->bcolour,
+                                            keys_sorted.as<uint8_t>(), ids.as<int32_t>(),
+                                            m->bcol_order, (int)nb, 0, 8, s));
+  NSRHS_TRY(tmp.alloc(tmp_bytes));
+  NSRHS_TRY(cub::DeviceRadixSort::SortPairs(tmp.p, tmp_bytes, m->bcolour,
+                                            keys_sorted.as<uint8_t>(), ids.as<int32_t>(),
+                                            m->bcol_order, (int)nb, 0, 8, s));
+  NSRHS_TRY(cudaStreamSynchronize(s));
+  m->info.n_block_colours = n_col;
   return NSRHS_OK;
 }
 
@@ -811,7 +1083,8 @@ nsrhs_status mesh_build(nsrhs_mesh* m, const double* coords, const int32_t* conn
 
   // Morton order of the element centroids (the RHS does not depend on the
   // element order, up to rounding).
-  if ((st = morton_reorder(m, s)) != NSRHS_OK) return st;
+  if (opts.colour && (st = mesh_alloc(m, &m->elem_order, (size_t)E)) != NSRHS_OK) return st;
+  if ((st = morton_reorder(m, m->elem_order, s)) != NSRHS_OK) return st;
   // Cached geometry (double and float) of every element.
   if ((st = mesh_alloc(m, &m->geom, kGeomRows * (size_t)E)) != NSRHS_OK) return st;
   if ((st = mesh_alloc(m, &m->geom_f, kGeomRows * (size_t)E)) != NSRHS_OK) return st;
@@ -819,6 +1092,8 @@ nsrhs_status mesh_build(nsrhs_mesh* m, const double* coords, const int32_t* conn
                                                                  m->geom, m->geom_f);
   NSRHS_TRY(cudaGetLastError());
   if ((st = build_blocks(m, s)) != NSRHS_OK) return st;
+  if (opts.colour && (st = build_colouring(m, s)) != NSRHS_OK) return st;
+  if (opts.colour && (st = build_block_colouring(m, s)) != NSRHS_OK) return st;
   // Lumped mass and its inverse (explicit time stepping).
   if ((st = mesh_alloc(m, &m->mass, (size_t)N)) != NSRHS_OK) return st;
   if ((st = mesh_alloc(m, &m->inv_mass, (size_t)N)) != NSRHS_OK) return st;
@@ -855,6 +1130,8 @@ void nsrhs_params_default(nsrhs_params* p) {
 void nsrhs_mesh_opts_default(nsrhs_mesh_opts* o) {
   if (!o) return;
   o->ar_threshold = 10.0;
+  o->colour = 0;
+  o->reserved = 0;
 }
 
 const char* nsrhs_status_string(nsrhs_status s) {
@@ -879,7 +1156,8 @@ nsrhs_status nsrhs_mesh_create(int64_t n_nodes, int64_t n_elems, const double* c
   nsrhs_mesh_opts o;
   nsrhs_mesh_opts_default(&o);
   if (opts) o = *opts;
-  if (!(o.ar_threshold > 0.0)) return NSRHS_EINVAL;
+  if (!(o.ar_threshold > 0.0) || (o.colour != 0 && o.colour != 1) || o.reserved != 0)
+    return NSRHS_EINVAL;
   nsrhs_mesh* m = new (std::nothrow) nsrhs_mesh();
   if (!m) return NSRHS_ENOMEM;
   if (cudaGetDevice(&m->device) != cudaSuccess) {
@@ -917,7 +1195,67 @@ nsrhs_status nsrhs_assemble(const nsrhs_mesh* m, const nsrhs_params* p, const vo
   if (!dg.ok) return NSRHS_ECUDA;
   const int64_t N = m->n_nodes, E = m->n_elems;
   const int flags = formulation_flags(p);
+  if ((p->scatter == NSRHS_SCATTER_COLOUR && m->col_conn == nullptr) ||
+      (p->scatter == NSRHS_SCATTER_BLOCK_COLOUR && m->bcol_order == nullptr))
+    return NSRHS_EUNSUPPORTED;
   NSRHS_TRY(cudaMemsetAsync(rhs, 0, sizeof(double) * 4 * N, s));
+  if (p->scatter == NSRHS_SCATTER_BLOCK_COLOUR) {
+    // one launch per block colour, in colour order
+    const int64_t nb = m->n_blocks;
+    cudaError_t err = cudaSuccess;
+    for (size_t k = 0; k + 1 < m->bcol_off.size() && err == cudaSuccess; ++k) {
+      const int64_t i0 = m->bcol_off[k], i1 = m->bcol_off[k + 1];
+      const unsigned grid = (unsigned)std::max<int64_t>(
+          1, std::min<int64_t>(i1 - i0, (int64_t)sm_count(m->device) * 8));
+      if (p->precision == NSRHS_FP64) {
+        auto P = elem_params<double>(p);
+        const size_t smem = nsrhs::block_kernel_smem<double, true>();
+        with_flags(flags, [&](auto fl) {
+          auto kern = nsrhs::fwd_block_kernel<double, decltype(fl)::value, true>;
+          err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+          if (err == cudaSuccess)
+            kern<<<grid, nsrhs::kBlockElems, smem, s>>>(
+                N, E, nb, m->blk_node_off, m->blk_nodes, m->blk_runs, m->blk_slots, m->blk_lconn,
+                m->geom, (const double*)up, P, rhs, m->bcol_order, i0, i1);
+        });
+      } else {
+        auto P = elem_params<float>(p);
+        const size_t smem = nsrhs::block_kernel_smem<float, true>();
+        with_flags(flags, [&](auto fl) {
+          auto kern = nsrhs::fwd_block_kernel<float, decltype(fl)::value, true>;
+          err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+          if (err == cudaSuccess)
+            kern<<<grid, nsrhs::kBlockElems, smem, s>>>(
+                N, E, nb, m->blk_node_off, m->blk_nodes, m->blk_runs, m->blk_slots, m->blk_lconn,
+                m->geom_f, (const float*)up, P, rhs, m->bcol_order, i0, i1);
+        });
+      }
+      if (err == cudaSuccess) err = cudaGetLastError();
+    }
+    return cuda_status(err);
+  }
+  if (p->scatter == NSRHS_SCATTER_COLOUR) {
+    // one launch per colour, in colour order
+    for (size_t k = 0; k + 1 < m->col_off.size(); ++k) {
+      const int64_t e0 = m->col_off[k], e1 = m->col_off[k + 1];
+      const unsigned grid = grid_for(e1 - e0, m->device, 16);
+      if (p->precision == NSRHS_FP64) {
+        auto P = elem_params<double>(p);
+        with_flags(flags, [&](auto fl) {
+          fwd_fp64_colour_kernel<decltype(fl)::value><<<grid, kThreads, 0, s>>>(
+              N, E, e0, e1, m->col_conn, m->col_geom, (const double*)up, P, rhs);
+        });
+      } else {
+        auto P = elem_params<float>(p);
+        with_flags(flags, [&](auto fl) {
+          fwd_mixed_colour_kernel<decltype(fl)::value><<<grid, kThreads, 0, s>>>(
+              N, E, e0, e1, m->col_conn, m->col_geom_f, (const float*)up, P, rhs);
+        });
+      }
+      NSRHS_TRY(cudaGetLastError());
+    }
+    return NSRHS_OK;
+  }
   // AUTO: atomics for the FP64 form (its FP64 pipe, not the scatter, is the
   // limit, and the block sums would add FP64 work); blocks for the mixed form
   // (bound by L2 atomics and gathers).
@@ -930,18 +1268,19 @@ nsrhs_status nsrhs_assemble(const nsrhs_mesh* m, const nsrhs_params* p, const vo
     cudaError_t err = cudaSuccess;
     if (p->precision == NSRHS_FP64) {
       auto P = elem_params<double>(p);
-      const size_t smem = 8 * nsrhs::kBlockSlots * sizeof(double);
+      const size_t smem = nsrhs::block_kernel_smem<double, false>();
       with_flags(flags, [&](auto fl) {
         auto kern = nsrhs::fwd_block_kernel<double, decltype(fl)::value>;
         err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err == cudaSuccess)
           kern<<<grid, nsrhs::kBlockElems, smem, s>>>(N, E, nb, m->blk_node_off, m->blk_nodes,
                                                       m->blk_runs, m->blk_slots, m->blk_lconn,
-                                                      m->geom, (const double*)up, P, rhs);
+                                                      m->geom, (const double*)up, P, rhs,
+                                                      nullptr, 0, 0);
       });
     } else {
       auto P = elem_params<float>(p);
-      const size_t smem = 8 * nsrhs::kBlockSlots * sizeof(float);
+      const size_t smem = nsrhs::block_kernel_smem<float, false>();
       with_flags(flags, [&](auto fl) {
         nsrhs::fwd_block_kernel<float, decltype(fl)::value>
             <<<grid, nsrhs::kBlockElems, smem, s>>>(N, E, nb, m->blk_node_off, m->blk_nodes,
@@ -978,7 +1317,34 @@ nsrhs_status nsrhs_assemble_vjp(const nsrhs_mesh* m, const nsrhs_params* p, cons
   DeviceGuard dg(m->device);
   if (!dg.ok) return NSRHS_ECUDA;
   const int64_t N = m->n_nodes, E = m->n_elems;
+  // the adjoint has no block kernel: BLOCK means atomics and BLOCK_COLOUR the
+  // element colouring (both deterministic colourings are built together)
+  const bool colour = p->scatter == NSRHS_SCATTER_COLOUR || p->scatter == NSRHS_SCATTER_BLOCK_COLOUR;
+  if (colour && m->col_conn == nullptr) return NSRHS_EUNSUPPORTED;
   NSRHS_TRY(cudaMemsetAsync(grad, 0, sizeof(double) * 4 * N, s));
+  if (colour) {
+    for (size_t k = 0; k + 1 < m->col_off.size(); ++k) {
+      const int64_t e0 = m->col_off[k], e1 = m->col_off[k + 1];
+      const unsigned grid = grid_for(e1 - e0, m->device, 16);
+      if (p->precision == NSRHS_FP64) {
+        auto P = elem_params<double>(p);
+        with_flags(formulation_flags(p), [&](auto fl) {
+          vjp_fp64_colour_kernel<decltype(fl)::value><<<grid, kThreads, 0, s>>>(
+              N, E, e0, e1, m->col_conn, m->col_geom, (const double*)up, (const double*)cot, P,
+              grad);
+        });
+      } else {
+        auto P = elem_params<float>(p);
+        with_flags(formulation_flags(p), [&](auto fl) {
+          vjp_mixed_colour_kernel<decltype(fl)::value><<<grid, kThreads, 0, s>>>(
+              N, E, e0, e1, m->col_conn, m->col_geom_f, (const float*)up, (const float*)cot, P,
+              grad);
+        });
+      }
+      NSRHS_TRY(cudaGetLastError());
+    }
+    return NSRHS_OK;
+  }
   const unsigned grid = grid_for(E, m->device, 16);
   if (p->precision == NSRHS_FP64) {
     auto P = elem_params<double>(p);
@@ -1037,6 +1403,19 @@ nsrhs_status nsrhs_assemble_elmat(const nsrhs_mesh* m, const nsrhs_params* p, co
     fwd_fp64_elmat_kernel<true><<<grid, kThreads, 0, s>>>(N, E, m->conn, m->geom, up, P, rhs);
   else
     fwd_fp64_elmat_kernel<false><<<grid, kThreads, 0, s>>>(N, E, m->conn, m->geom, up, P, rhs);
+  return cuda_status(cudaGetLastError());
+}
+
+nsrhs_status nsrhs_mesh_element_colours(const nsrhs_mesh* m, int32_t which, int32_t* out_dev,
+                                        void* stream) {
+  if (!is_live(m) || !out_dev) return NSRHS_EINVAL;
+  if (which < NSRHS_ELEMENT_COLOUR || which > NSRHS_ELEMENT_BLOCK) return NSRHS_EINVAL;
+  if (m->colour == nullptr || m->bcolour == nullptr) return NSRHS_EUNSUPPORTED;
+  DeviceGuard dg(m->device);
+  if (!dg.ok) return NSRHS_ECUDA;
+  const int64_t E = m->n_elems;
+  nsrhs::colour_export_kernel<<<grid_for(E, m->device, 8), kThreads, 0, (cudaStream_t)stream>>>(
+      E, which, nsrhs::kBlockElems, m->elem_order, m->colour, m->bcolour, out_dev);
   return cuda_status(cudaGetLastError());
 }
 

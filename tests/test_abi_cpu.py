@@ -44,8 +44,9 @@ def test_status_strings_and_defaults(lib):
             p.tau_mode) == (1.0, 1e-2, 0.0, 4.0, 2.0, 0, 0, 0, 0)
     o = _abi.MeshOpts()
     lib.nsrhs_mesh_opts_default(ctypes.byref(o))
-    assert o.ar_threshold == 10.0
-    assert ctypes.sizeof(_abi.Params) == 56 and ctypes.sizeof(_abi.MeshInfo) == 64
+    assert (o.ar_threshold, o.colour, o.reserved) == (10.0, 0, 0)
+    assert ctypes.sizeof(_abi.Params) == 56 and ctypes.sizeof(_abi.MeshInfo) == 80
+    assert ctypes.sizeof(_abi.MeshOpts) == 16
 
 
 def test_argument_errors_without_gpu(lib):
@@ -60,9 +61,9 @@ def test_argument_errors_without_gpu(lib):
     assert lib.nsrhs_mesh_create(10, -1, fake, fake, None, None, ctypes.byref(out)) == _abi.EINVAL
     assert lib.nsrhs_mesh_create(2**31, 1, fake, fake, None, None,
                                  ctypes.byref(out)) == _abi.EINVAL
-    bad = _abi.MeshOpts(-1.0)
-    assert lib.nsrhs_mesh_create(10, 10, fake, fake, ctypes.byref(bad), None,
-                                 ctypes.byref(out)) == _abi.EINVAL
+    for bad in (_abi.MeshOpts(-1.0, 0, 0), _abi.MeshOpts(10.0, 2, 0), _abi.MeshOpts(10.0, 1, 7)):
+        assert lib.nsrhs_mesh_create(10, 10, fake, fake, ctypes.byref(bad), None,
+                                     ctypes.byref(out)) == _abi.EINVAL
     # unknown / destroyed mesh handles are rejected, destroy is NULL-safe
     p = _abi.Params()
     lib.nsrhs_params_default(ctypes.byref(p))
@@ -71,6 +72,7 @@ def test_argument_errors_without_gpu(lib):
     assert lib.nsrhs_assemble_vjp(fake, ctypes.byref(p), fake, fake, fake, None) == _abi.EINVAL
     info = _abi.MeshInfo()
     assert lib.nsrhs_mesh_get_info(fake, ctypes.byref(info)) == _abi.EINVAL
+    assert lib.nsrhs_mesh_element_colours(fake, 0, fake, None) == _abi.EINVAL
     lib.nsrhs_destroy(None)
     lib.nsrhs_destroy(fake)
 
