@@ -582,9 +582,10 @@ def time_scatter_sweep(mesh, w, up, cot, dev, stream, args, fwd_ms, vjp_ms):
         res["fwd_mixed"][sc] = rate(_timed(
             lambda: mesh.assemble(up32, mk(scatter=sc, precision="mixed"), out=o),
             dev, stream, args))
-    res["vjp_fp64"]["colour"] = rate(_timed(
-        lambda: mesh.assemble_vjp(up, cot, mk(scatter="colour"), out=o), dev, stream, args))
-    for sc in ("atomic", "colour"):
+    for sc in ("block", "colour", "block_colour"):
+        res["vjp_fp64"][sc] = rate(_timed(
+            lambda: mesh.assemble_vjp(up, cot, mk(scatter=sc), out=o), dev, stream, args))
+    for sc in ("atomic", "block", "colour", "block_colour"):
         res["vjp_mixed"][sc] = rate(_timed(
             lambda: mesh.assemble_vjp(up32, cot32, mk(scatter=sc, precision="mixed"), out=o),
             dev, stream, args))

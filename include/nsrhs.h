@@ -71,7 +71,7 @@ typedef enum {
   NSRHS_SCATTER_ATOMIC = 1, /* one double-precision atomic add per entry */
   NSRHS_SCATTER_BLOCK = 2,  /* per-block node-local accumulation in shared
                                memory, one atomic per (block, node, component);
-                               forward only (the adjoint uses atomics) */
+                               forward and adjoint */
   NSRHS_SCATTER_COLOUR = 3, /* element colouring: elements sharing a node have
                                different colours; one launch per colour with
                                plain read-modify-write adds, in a fixed order,
@@ -82,8 +82,8 @@ typedef enum {
                                sharing a node differ): per-block node sums in a
                                fixed order, then plain read-modify-write adds,
                                one launch per block colour; bitwise
-                               reproducible. The adjoint uses the element
-                               colouring. Needs opts.colour = 1 */
+                               reproducible; forward and adjoint. Needs
+                               opts.colour = 1 */
 } nsrhs_scatter;
 
 typedef enum {

@@ -336,4 +336,113 @@ __global__ void __launch_bounds__(kBlockElems, block_kernel_min_ctas<R>())
   }
 }
 
+// Adjoint with block-staged gathers and scatters: the reverse of the forward
+// block kernel. Per block the nodal (u, p) and the cotangent of its distinct
+// nodes are staged in shared memory, each thread runs one element's reverse
+// sweep, the 16 gradient entries go back to shared memory (over the staged
+// nodal values, after a barrier), and each node's entries are summed in a
+// fixed order and added with one atomic per component (COLOUR: with a plain
+// read-modify-write, blocks of one colour per launch). Dynamic shared memory:
+// block_vjp_smem<R, COLOUR>() bytes.
+template <class R, bool COLOUR>
+constexpr size_t block_vjp_smem() {
+  return 8 * kBlockSlots * sizeof(R) + (COLOUR ? 4 * kBlockElems * sizeof(double) : 0);
+}
+
+template <class R>
+constexpr int block_vjp_min_ctas() {
+  return sizeof(R) == 4 ? 2 : 1;
+}
+
+template <class R, int FLAGS, bool COLOUR = false>
+__global__ void __launch_bounds__(kBlockElems, block_vjp_min_ctas<R>())
+    vjp_block_kernel(int64_t N, int64_t E, int64_t n_blocks, const int64_t* __restrict__ node_off,
+                     const int32_t* __restrict__ nodes, const uint16_t* __restrict__ runs,
+                     const uint16_t* __restrict__ slots, const uint16_t* __restrict__ lconn,
+                     const R* __restrict__ geom, const R* __restrict__ up,
+                     const R* __restrict__ cot, ElemParams<R> P, double* __restrict__ grad,
+                     const int32_t* __restrict__ order, int64_t i0, int64_t i1) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R* su = reinterpret_cast<R*>(smem_raw);  // [4][kBlockSlots] nodal u, v, w, p; then entries
+  R* sw = su + 4 * kBlockSlots;             // [4][kBlockSlots] cotangent
+  double* sold = reinterpret_cast<double*>(sw + 4 * kBlockSlots);  // COLOUR: [4][kBlockElems]
+  const int tid = threadIdx.x;
+  const int64_t first = COLOUR ? i0 : 0, last = COLOUR ? i1 : n_blocks;
+  for (int64_t i = first + blockIdx.x; i < last; i += gridDim.x) {
+    const int64_t b = COLOUR ? (int64_t)__ldg(order + i) : i;
+    const int64_t off = node_off[b];
+    const int nb = (int)(node_off[b + 1] - off);
+    for (int j = tid; j < nb; j += kBlockElems) {
+      const int64_t v = __ldg(nodes + off + j);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        su[k * kBlockSlots + j] = __ldg(up + k * N + v);
+        sw[k * kBlockSlots + j] = __ldg(cot + k * N + v);
+      }
+    }
+    if constexpr (COLOUR) {
+      if (tid < nb) {
+        const int64_t v = __ldg(nodes + off + tid);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) sold[k * kBlockElems + tid] = grad[k * N + v];
+      }
+    }
+    __syncthreads();
+    const int64_t e = b * kBlockElems + tid;
+    R gu[4][3], gp[4];
+    if (e < E) {
+      int lc[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) lc[a] = __ldg(lconn + a * E + e);
+      R u[4][3], p[4], w[4][4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) u[a][k] = su[k * kBlockSlots + lc[a]];
+        p[a] = su[3 * kBlockSlots + lc[a]];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) w[a][k] = sw[k * kBlockSlots + lc[a]];
+      }
+      R c[3][3], inv_det, rh;
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) c[k][d] = __ldg(geom + (3 * k + d) * E + e);
+      inv_det = __ldg(geom + 9 * E + e);
+      rh = __ldg(geom + 10 * E + e);
+      element_vjp<R, FLAGS>(c, inv_det, rh, u, p, w, P, gu, gp);
+    }
+    __syncthreads();  // the staged values are no longer read: reuse su for the entries
+    if (e < E) {
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) su[k * kBlockSlots + 4 * tid + a] = gu[a][k];
+        su[3 * kBlockSlots + 4 * tid + a] = gp[a];
+      }
+    }
+    __syncthreads();
+    const uint16_t* bslots = slots + b * kBlockSlots;
+    for (int j = tid; j < nb; j += kBlockElems) {
+      const int r0 = __ldg(runs + off + b + j), r1 = __ldg(runs + off + b + j + 1);
+      const int64_t v = __ldg(nodes + off + j);
+      NodeSum<R> acc[4];
+      for (int q = r0; q < r1; ++q) {
+        const int sl = __ldg(bslots + q);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc[k].add(su[k * kBlockSlots + sl]);
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if constexpr (COLOUR)
+          grad[k * N + v] = (j == tid ? sold[k * kBlockElems + tid] : grad[k * N + v]) +
+                            acc[k].value();
+        else
+          atomicAdd(grad + k * N + v, acc[k].value());
+      }
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace nsrhs

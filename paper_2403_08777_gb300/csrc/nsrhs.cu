@@ -1317,12 +1317,59 @@ nsrhs_status nsrhs_assemble_vjp(const nsrhs_mesh* m, const nsrhs_params* p, cons
   DeviceGuard dg(m->device);
   if (!dg.ok) return NSRHS_ECUDA;
   const int64_t N = m->n_nodes, E = m->n_elems;
-  // the adjoint has no block kernel: BLOCK means atomics and BLOCK_COLOUR the
-  // element colouring (both deterministic colourings are built together)
-  const bool colour = p->scatter == NSRHS_SCATTER_COLOUR || p->scatter == NSRHS_SCATTER_BLOCK_COLOUR;
-  if (colour && m->col_conn == nullptr) return NSRHS_EUNSUPPORTED;
+  if ((p->scatter == NSRHS_SCATTER_COLOUR && m->col_conn == nullptr) ||
+      (p->scatter == NSRHS_SCATTER_BLOCK_COLOUR && m->bcol_order == nullptr))
+    return NSRHS_EUNSUPPORTED;
   NSRHS_TRY(cudaMemsetAsync(grad, 0, sizeof(double) * 4 * N, s));
-  if (colour) {
+  const int flags = formulation_flags(p);
+  if (p->scatter == NSRHS_SCATTER_BLOCK || p->scatter == NSRHS_SCATTER_BLOCK_COLOUR) {
+    // BLOCK: one grid over all blocks, atomics; BLOCK_COLOUR: one launch per
+    // block colour, plain read-modify-write
+    const bool coloured = p->scatter == NSRHS_SCATTER_BLOCK_COLOUR;
+    const int64_t nb = m->n_blocks;
+    std::vector<int64_t> ranges = coloured ? m->bcol_off : std::vector<int64_t>{0, nb};
+    cudaError_t err = cudaSuccess;
+    for (size_t k = 0; k + 1 < ranges.size() && err == cudaSuccess; ++k) {
+      const int64_t i0 = ranges[k], i1 = ranges[k + 1];
+      const unsigned grid = (unsigned)std::max<int64_t>(
+          1, std::min<int64_t>(i1 - i0, (int64_t)sm_count(m->device) * 8));
+      auto launch = [&](auto kern, size_t smem, const auto* geom, const auto* u, const auto* c,
+                        const auto& P) {
+        err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err == cudaSuccess)
+          kern<<<grid, nsrhs::kBlockElems, smem, s>>>(
+              N, E, nb, m->blk_node_off, m->blk_nodes, m->blk_runs, m->blk_slots, m->blk_lconn,
+              geom, u, c, P, grad, coloured ? m->bcol_order : nullptr, i0, i1);
+      };
+      if (p->precision == NSRHS_FP64) {
+        auto P = elem_params<double>(p);
+        with_flags(flags, [&](auto fl) {
+          constexpr int F = decltype(fl)::value;
+          if (coloured)
+            launch(nsrhs::vjp_block_kernel<double, F, true>, nsrhs::block_vjp_smem<double, true>(),
+                   m->geom, (const double*)up, (const double*)cot, P);
+          else
+            launch(nsrhs::vjp_block_kernel<double, F, false>,
+                   nsrhs::block_vjp_smem<double, false>(), m->geom, (const double*)up,
+                   (const double*)cot, P);
+        });
+      } else {
+        auto P = elem_params<float>(p);
+        with_flags(flags, [&](auto fl) {
+          constexpr int F = decltype(fl)::value;
+          if (coloured)
+            launch(nsrhs::vjp_block_kernel<float, F, true>, nsrhs::block_vjp_smem<float, true>(),
+                   m->geom_f, (const float*)up, (const float*)cot, P);
+          else
+            launch(nsrhs::vjp_block_kernel<float, F, false>, nsrhs::block_vjp_smem<float, false>(),
+                   m->geom_f, (const float*)up, (const float*)cot, P);
+        });
+      }
+      if (err == cudaSuccess) err = cudaGetLastError();
+    }
+    return cuda_status(err);
+  }
+  if (p->scatter == NSRHS_SCATTER_COLOUR) {
     for (size_t k = 0; k + 1 < m->col_off.size(); ++k) {
       const int64_t e0 = m->col_off[k], e1 = m->col_off[k + 1];
       const unsigned grid = grid_for(e1 - e0, m->device, 16);

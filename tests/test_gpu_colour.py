@@ -124,11 +124,12 @@ def test_colour_scatter_matches_oracle(dev, kind, n, order):
     cot = mg.normal((4, w.n_nodes), seed=mg.SEED_COT)
     gref = oracle.vjp(w.coords, w.conn, w.up, cot, w.rho, w.mu)
     cot_d = torch.from_numpy(cot).to(dev)
-    g = m.assemble_vjp(up, cot_d, ns.Params(rho=w.rho, mu=w.mu, scatter="colour")).cpu().numpy()
-    assert relerr(g, gref) <= TOL_VJP_ORACLE, relerr(g, gref)
-    gm = m.assemble_vjp(up.float(), cot_d.float(),
-                        ns.Params(rho=w.rho, mu=w.mu, scatter="colour", precision="mixed"))
-    assert relerr(gm.cpu().numpy(), gref) <= TOL_VJP_FD
+    for sc in ("colour", "block", "block_colour"):
+        g = m.assemble_vjp(up, cot_d, ns.Params(rho=w.rho, mu=w.mu, scatter=sc)).cpu().numpy()
+        assert relerr(g, gref) <= TOL_VJP_ORACLE, (sc, relerr(g, gref))
+        gm = m.assemble_vjp(up.float(), cot_d.float(),
+                            ns.Params(rho=w.rho, mu=w.mu, scatter=sc, precision="mixed"))
+        assert relerr(gm.cpu().numpy(), gref) <= TOL_VJP_FD, sc
     m.close()
 
 
@@ -146,8 +147,10 @@ def test_colour_scatter_variants(dev, cv, conv, tau):
                    scatter="block_colour")
     check_fp64(m.assemble(up, pb).cpu().numpy(), ref)
     cot = mg.normal((4, w.n_nodes), seed=mg.SEED_COT)
-    g = m.assemble_vjp(up, torch.from_numpy(cot).to(dev), p).cpu().numpy()
-    assert relerr(g, oracle.vjp(w.coords, w.conn, w.up, cot, w.rho, w.mu, **okw)) <= TOL_VJP_ORACLE
+    gref = oracle.vjp(w.coords, w.conn, w.up, cot, w.rho, w.mu, **okw)
+    for pp in (p, pb):
+        g = m.assemble_vjp(up, torch.from_numpy(cot).to(dev), pp).cpu().numpy()
+        assert relerr(g, gref) <= TOL_VJP_ORACLE
     m.close()
 
 
@@ -192,8 +195,14 @@ def test_colour_scatter_ragged_element_counts(dev):
         check_block_colouring(m.element_colours("block_colour").cpu().numpy(),
                               m.element_colours("block").cpu().numpy(), conn,
                               info["n_block_colours"], info["n_blocks"])
+        cot = mg.normal((4, w.n_nodes), seed=mg.SEED_COT)
+        gref = oracle.vjp(w.coords, conn, w.up, cot, 1.0, 1e-2)
+        cot_d = torch.from_numpy(cot).to(dev)
         for sc in ("colour", "block_colour"):
             check_fp64(m.assemble(up, ns.Params(rho=1.0, mu=1e-2, scatter=sc)).cpu().numpy(), ref)
+        for sc in ("colour", "block", "block_colour"):
+            g = m.assemble_vjp(up, cot_d, ns.Params(rho=1.0, mu=1e-2, scatter=sc)).cpu().numpy()
+            assert relerr(g, gref) <= TOL_VJP_ORACLE, (E, sc)
         m.close()
 
 

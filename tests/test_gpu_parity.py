@@ -146,8 +146,10 @@ def test_vjp_matches_oracle(dev, n, order, cv):
     ref = oracle.vjp(w.coords, w.conn, w.up, cot, w.rho, w.mu, c_vreman=cv)
     coords, conn, up, cot_d = on_dev(dev, w.coords, w.conn, w.up, cot)
     m = ns.Mesh(coords, conn)
-    g = m.assemble_vjp(up, cot_d, rho=w.rho, mu=w.mu, c_vreman=cv).cpu().numpy()
-    assert relerr(g, ref) <= TOL_VJP_ORACLE, relerr(g, ref)
+    for scatter in ("auto", "atomic", "block"):
+        g = m.assemble_vjp(up, cot_d, rho=w.rho, mu=w.mu, c_vreman=cv,
+                           scatter=scatter).cpu().numpy()
+        assert relerr(g, ref) <= TOL_VJP_ORACLE, (scatter, relerr(g, ref))
     m.close()
 
 
@@ -282,9 +284,10 @@ def test_formulation_variants_match_oracle(dev, cv, conv, tau):
     assert relerr(m.assemble(up.float(), pm).cpu().numpy(), ref) <= TOL_MIXED
     cot = mg.normal((4, w.n_nodes), seed=mg.SEED_COT)
     gref = oracle.vjp(w.coords, w.conn, w.up, cot, w.rho, w.mu, **okw)
-    p = ns.Params(rho=w.rho, mu=w.mu, c_vreman=cv, convection=conv, tau=tau)
-    g = m.assemble_vjp(up, torch.from_numpy(cot).to(dev), p).cpu().numpy()
-    assert relerr(g, gref) <= TOL_VJP_ORACLE, relerr(g, gref)
+    for scatter in ("atomic", "block"):
+        p = ns.Params(rho=w.rho, mu=w.mu, c_vreman=cv, convection=conv, tau=tau, scatter=scatter)
+        g = m.assemble_vjp(up, torch.from_numpy(cot).to(dev), p).cpu().numpy()
+        assert relerr(g, gref) <= TOL_VJP_ORACLE, (scatter, relerr(g, gref))
     m.close()
 
 
@@ -383,7 +386,9 @@ def test_mixed_precision_adjoint(dev, cv, conv):
     ref = oracle.vjp(w.coords, w.conn, w.up, cot, w.rho, w.mu, c_vreman=cv, skew=conv == "skew")
     coords, conn, up, cot_d = on_dev(dev, w.coords, w.conn, w.up, cot)
     m = ns.Mesh(coords, conn)
-    p = ns.Params(rho=w.rho, mu=w.mu, c_vreman=cv, convection=conv, precision="mixed")
-    g = m.assemble_vjp(up.float(), cot_d.float(), p).cpu().numpy()
-    assert relerr(g, ref) <= TOL_VJP_FD, relerr(g, ref)
+    for scatter in ("atomic", "block"):
+        p = ns.Params(rho=w.rho, mu=w.mu, c_vreman=cv, convection=conv, precision="mixed",
+                      scatter=scatter)
+        g = m.assemble_vjp(up.float(), cot_d.float(), p).cpu().numpy()
+        assert relerr(g, ref) <= TOL_VJP_FD, (scatter, relerr(g, ref))
     m.close()
