@@ -43,8 +43,8 @@ UNIT = "tets/s"
 # (tests/test_flop_count.py keeps these numbers in step with the source).
 # The element geometry (43 flops per tet) is computed once per mesh and
 # cached, so it is not part of a call.
-FLOPS_PER_TET = {"fwd": 518, "vjp": 1107}
-FLOPS_PER_TET_VREMAN = {"fwd": 571, "vjp": 1252}
+FLOPS_PER_TET = {"fwd": 518, "vjp": 1107, "rhs_vjp": 1402}
+FLOPS_PER_TET_VREMAN = {"fwd": 571, "vjp": 1252, "rhs_vjp": 1547}
 
 # DRAM bytes per tet (dram__bytes_read.sum + dram__bytes_write.sum) from one
 # ncu capture of each kernel on the 128^3-hex RCM mesh, scaled to a launch by
@@ -397,6 +397,13 @@ def run_ours(args):
         torch.cuda.synchronize(dev)
         vms = va.elapsed_time(vb) / max(2, args.steps // 2)
         forms[name] = {"ms": vms, "tets_per_s": w.n_elems / (vms * 1e-3), "variant": kw}
+    # the RHS and the adjoint at the same state in one pass (one-pass call)
+    out2 = (rhs, grad)
+    op_ms = _timed(lambda: mesh.assemble_rhs_vjp(up, cot, p, out=out2), dev, stream, args)
+    forms["rhs_vjp_one_pass"] = {
+        "ms": op_ms, "tets_per_s": w.n_elems / (op_ms * 1e-3),
+        "tflops": flops["rhs_vjp"] * w.n_elems / (op_ms * 1e-3) / 1e12,
+        "vs_separate_calls": (fwd_med + vjp_med) / op_ms}
     # mixed-precision adjoint (float sweep, double accumulation)
     up32, cot32 = up.float(), cot.float()
     pmx = ns.Params(rho=w.rho, mu=w.mu, c_vreman=w.c_vreman, precision="mixed")

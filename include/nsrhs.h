@@ -186,6 +186,20 @@ nsrhs_status nsrhs_assemble_vjp(const nsrhs_mesh* m, const nsrhs_params* p, cons
                                 const void* cot, double* grad, void* stream);
 
 /*
+ * Both of the above at the same state in one pass: rhs = assembled RHS of up
+ * and grad = (d rhs / d up)^T cot, with one gather of up and cot per element
+ * and the element's forward intermediates computed once (the adjoint's
+ * recomputation of them is shared with the RHS). For callers that hold the
+ * cotangent before the RHS is needed: residual and adjoint-residual sweeps
+ * of steady adjoint solvers, one-shot optimisation, Newton-Krylov with a
+ * transposed product. Types and layouts as nsrhs_assemble / _vjp; rhs and
+ * grad must be distinct and are overwritten. Scatter AUTO or ATOMIC only
+ * (others: NSRHS_EUNSUPPORTED).
+ */
+nsrhs_status nsrhs_assemble_rhs_vjp(const nsrhs_mesh* m, const nsrhs_params* p, const void* up,
+                                    const void* cot, double* rhs, double* grad, void* stream);
+
+/*
  * The same RHS (FP64, convective form, tau at the Gauss points) computed the
  * way the paper's baseline did before its restructuring (Sec. V-A): with the
  * nonlinear coefficients frozen at the current state, a full 16x16 element

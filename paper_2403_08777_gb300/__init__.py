@@ -174,6 +174,32 @@ class Mesh:
         _abi.check(st, "nsrhs_assemble_vjp")
         return out
 
+    def assemble_rhs_vjp(self, up: torch.Tensor, cot: torch.Tensor,
+                         params: Params | None = None, *, out=None, **kw):
+        """(rhs, (d rhs / d up)^T cot) at the same state in one pass; both
+        [4, N] float64. out: optional pair of [4, N] float64 tensors."""
+        p = self._params(params, kw)
+        dt = torch.float32 if p.precision == "mixed" else torch.float64
+        _require(up, "up", dt, (4, self.n_nodes), self.device)
+        _require(cot, "cot", dt, (4, self.n_nodes), self.device)
+        if out is None:
+            out = tuple(torch.empty((4, self.n_nodes), dtype=torch.float64, device=self.device)
+                        for _ in range(2))
+        else:
+            for t, name in zip(out, ("out[0]", "out[1]")):
+                _require(t, name, torch.float64, (4, self.n_nodes), self.device)
+        rhs, grad = out
+        cp = p.to_c()
+        with torch.cuda.device(self.device):
+            st = _abi.load().nsrhs_assemble_rhs_vjp(self.handle, ctypes.byref(cp),
+                                                    ctypes.c_void_p(up.data_ptr()),
+                                                    ctypes.c_void_p(cot.data_ptr()),
+                                                    ctypes.c_void_p(rhs.data_ptr()),
+                                                    ctypes.c_void_p(grad.data_ptr()),
+                                                    _stream_handle(self.device))
+        _abi.check(st, "nsrhs_assemble_rhs_vjp")
+        return rhs, grad
+
     def assemble_elmat(self, up: torch.Tensor, params: Params | None = None, *, out=None, **kw):
         """The FP64 RHS through full 16x16 element matrices (comparison path)."""
         p = self._params(params, kw)

@@ -19,7 +19,7 @@ EXPORTED = ("nsrhs_params_default", "nsrhs_mesh_opts_default", "nsrhs_mesh_creat
             "nsrhs_mesh_get_info", "nsrhs_assemble", "nsrhs_assemble_vjp", "nsrhs_destroy",
             "nsrhs_status_string", "nsrhs_probe_fma", "nsrhs_mesh_check_noalloc",
             "nsrhs_probe_special", "nsrhs_lumped_mass", "nsrhs_explicit_step",
-            "nsrhs_assemble_elmat", "nsrhs_mesh_element_colours")
+            "nsrhs_assemble_elmat", "nsrhs_mesh_element_colours", "nsrhs_assemble_rhs_vjp")
 
 
 class Params(ctypes.Structure):
@@ -100,6 +100,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.nsrhs_mesh_check_noalloc.restype = ctypes.c_int
     lib.nsrhs_mesh_element_colours.argtypes = [P, ctypes.c_int32, P, P]
     lib.nsrhs_mesh_element_colours.restype = ctypes.c_int
+    lib.nsrhs_assemble_rhs_vjp.argtypes = [P, ctypes.POINTER(Params), P, P, P, P, P]
+    lib.nsrhs_assemble_rhs_vjp.restype = ctypes.c_int
     _lib = lib
     return lib
 

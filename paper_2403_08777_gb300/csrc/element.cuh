@@ -123,6 +123,99 @@ __device__ __forceinline__ void element_geometry(const XT X[4][3], R c[3][3], R&
   element_geometry_from_edges<R, GR>(e, c, inv_det, rh, det_out);
 }
 
+// The element's 16 outputs from its gradients and Gauss-point accumulators:
+// K (viscous + pressure + SUPG momentum), Rs (continuity's PSPG part) and the
+// Galerkin convection, as described at the top of this file. Qv and Pv are
+// the symmetric 3x3 matrices Q = sum tau_g u_g u_g^T and P = sum u_g u_g^T
+// as (00, 11, 22, 01, 02, 12); P is read only in the skew-symmetric form.
+template <class R, int FLAGS>
+__device__ __forceinline__ void element_outputs(const R c[3][3], R inv_det, const R u[4][3],
+                                                const R G[3][3], const R gp[3], const R S[3],
+                                                R psum, R trG, R mu_eff, R stau, const R T[3],
+                                                const R Qv[6], const R Pv[6],
+                                                const ElemParams<R>& P, R F[4][4]) {
+  constexpr bool SKEW = (FLAGS & kSkew) != 0;
+  const R Q00 = Qv[0], Q11 = Qv[1], Q22 = Qv[2], Q01 = Qv[3], Q02 = Qv[4], Q12 = Qv[5];
+  const R P00 = Pv[0], P11 = Pv[1], P22 = Pv[2], P01 = Pv[3], P02 = Pv[4], P12 = Pv[5];
+  // K = pbar/6 I - inv_det/6 [Gh (mu_eff I + rho^2/4 Q) + rho/4 gph T^T], with the
+  // scalar factors folded into Qp and gq before the 3x3 product so that each
+  // entry is one chain of fused multiply-adds.
+  const R s6 = inv_det * (R)(1.0 / 6.0);
+  const R a2 = -s6 * (P.rho * P.rho * (R)0.25);
+  const R a1 = -s6 * mu_eff;
+  const R b4 = -s6 * (P.rho * (R)0.25);
+  const R Qp[3][3] = {{fmac(a2, Q00, a1), a2 * Q01, a2 * Q02},
+                      {a2 * Q01, fmac(a2, Q11, a1), a2 * Q12},
+                      {a2 * Q02, a2 * Q12, fmac(a2, Q22, a1)}};
+  const R pb6 = psum * (R)(1.0 / 24.0);
+  const R Pm[3][3] = {{P00, P01, P02}, {P01, P11, P12}, {P02, P12, P22}};
+  const R r48 = P.rho * (R)(1.0 / 48.0);
+  R K[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const R gq = b4 * gp[i];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      R acc = (i == j) ? fmac(gq, T[j], pb6) : gq * T[j];
+      if constexpr (SKEW) acc = fmac(r48, Pm[i][j], acc);
+      acc = fmac(G[i][0], Qp[0][j], acc);
+      acc = fmac(G[i][1], Qp[1][j], acc);
+      K[i][j] = fmac(G[i][2], Qp[2][j], acc);
+    }
+  }
+  // Rs = inv_det/24 (rho Gh T + stau gph)
+  const R s24 = inv_det * (R)(1.0 / 24.0);
+  const R sg = s24 * stau;
+  R sTT[3];
+  {
+    const R sT = s24 * P.rho;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) sTT[j] = sT * T[j];
+  }
+  R Rs[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    R acc = sg * gp[i];
+    acc = fmac(sTT[0], G[i][0], acc);
+    acc = fmac(sTT[1], G[i][1], acc);
+    Rs[i] = fmac(sTT[2], G[i][2], acc);
+  }
+  const R cont0 = trG * (R)(-1.0 / 24.0);
+  // Galerkin convection -(rho/120) Gh (S_u + u_a) = Gh v_a, v_a = m120 u_a + m120 S_u
+  // (halved in the skew-symmetric form)
+  const R m120 = P.rho * (R)(SKEW ? -1.0 / 240.0 : -1.0 / 120.0);
+  R mS[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) mS[i] = m120 * S[i];
+  R ysum[3] = {(R)0, (R)0, (R)0};
+  R csum = (R)0;
+#pragma unroll
+  for (int a = 1; a < 4; ++a) {
+    const R* ca = c[a - 1];
+    R v[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) v[i] = fmac(m120, u[a][i], mS[i]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const R y = fmac(K[i][2], ca[2], fmac(K[i][1], ca[1], K[i][0] * ca[0]));
+      ysum[i] += y;
+      F[a][i] = fmac(G[i][2], v[2], fmac(G[i][1], v[1], fmac(G[i][0], v[0], y)));
+    }
+    F[a][3] = fmac(-ca[2], Rs[2], fmac(-ca[1], Rs[1], fmac(-ca[0], Rs[0], cont0)));
+    csum += F[a][3];
+  }
+  {
+    R v[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) v[i] = fmac(m120, u[0][i], mS[i]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+      F[0][i] = fmac(G[i][2], v[2], fmac(G[i][1], v[1], fmac(G[i][0], v[0], -ysum[i])));
+    // sum_a c_a = 0: the continuity entries sum to 4 cont0
+    F[0][3] = fmac((R)4, cont0, -csum);
+  }
+}
+
 // Forward element RHS. u[a][i], p[a] nodal values; F[a][0..2] momentum,
 // F[a][3] continuity. FLAGS: kVreman | kSkew | kTauElem.
 // Skew-symmetric variant: the Galerkin convection becomes
@@ -232,83 +325,9 @@ __device__ __forceinline__ void element_rhs(const R c[3][3], R inv_det, R rh, co
     Q02 = tau_e * P02;
     Q12 = tau_e * P12;
   }
-  // K = pbar/6 I - inv_det/6 [Gh (mu_eff I + rho^2/4 Q) + rho/4 gph T^T], with the
-  // scalar factors folded into Qp and gq before the 3x3 product so that each
-  // entry is one chain of fused multiply-adds.
-  const R s6 = inv_det * (R)(1.0 / 6.0);
-  const R a2 = -s6 * (P.rho * P.rho * (R)0.25);
-  const R a1 = -s6 * mu_eff;
-  const R b4 = -s6 * (P.rho * (R)0.25);
-  const R Qp[3][3] = {{fmac(a2, Q00, a1), a2 * Q01, a2 * Q02},
-                      {a2 * Q01, fmac(a2, Q11, a1), a2 * Q12},
-                      {a2 * Q02, a2 * Q12, fmac(a2, Q22, a1)}};
-  const R pb6 = psum * (R)(1.0 / 24.0);
-  const R Pm[3][3] = {{P00, P01, P02}, {P01, P11, P12}, {P02, P12, P22}};
-  const R r48 = P.rho * (R)(1.0 / 48.0);
-  R K[3][3];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    const R gq = b4 * gp[i];
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      R acc = (i == j) ? fmac(gq, T[j], pb6) : gq * T[j];
-      if constexpr (SKEW) acc = fmac(r48, Pm[i][j], acc);
-      acc = fmac(G[i][0], Qp[0][j], acc);
-      acc = fmac(G[i][1], Qp[1][j], acc);
-      K[i][j] = fmac(G[i][2], Qp[2][j], acc);
-    }
-  }
-  // Rs = inv_det/24 (rho Gh T + stau gph)
-  const R s24 = inv_det * (R)(1.0 / 24.0);
-  const R sg = s24 * stau;
-  R sTT[3];
-  {
-    const R sT = s24 * P.rho;
-#pragma unroll
-    for (int j = 0; j < 3; ++j) sTT[j] = sT * T[j];
-  }
-  R Rs[3];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    R acc = sg * gp[i];
-    acc = fmac(sTT[0], G[i][0], acc);
-    acc = fmac(sTT[1], G[i][1], acc);
-    Rs[i] = fmac(sTT[2], G[i][2], acc);
-  }
-  const R cont0 = trG * (R)(-1.0 / 24.0);
-  // Galerkin convection -(rho/120) Gh (S_u + u_a) = Gh v_a, v_a = m120 u_a + m120 S_u
-  // (halved in the skew-symmetric form)
-  const R m120 = P.rho * (R)(SKEW ? -1.0 / 240.0 : -1.0 / 120.0);
-  R mS[3];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) mS[i] = m120 * S[i];
-  R ysum[3] = {(R)0, (R)0, (R)0};
-  R csum = (R)0;
-#pragma unroll
-  for (int a = 1; a < 4; ++a) {
-    const R* ca = c[a - 1];
-    R v[3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) v[i] = fmac(m120, u[a][i], mS[i]);
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      const R y = fmac(K[i][2], ca[2], fmac(K[i][1], ca[1], K[i][0] * ca[0]));
-      ysum[i] += y;
-      F[a][i] = fmac(G[i][2], v[2], fmac(G[i][1], v[1], fmac(G[i][0], v[0], y)));
-    }
-    F[a][3] = fmac(-ca[2], Rs[2], fmac(-ca[1], Rs[1], fmac(-ca[0], Rs[0], cont0)));
-    csum += F[a][3];
-  }
-  {
-    R v[3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) v[i] = fmac(m120, u[0][i], mS[i]);
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-      F[0][i] = fmac(G[i][2], v[2], fmac(G[i][1], v[1], fmac(G[i][0], v[0], -ysum[i])));
-    // sum_a c_a = 0: the continuity entries sum to 4 cont0
-    F[0][3] = fmac((R)4, cont0, -csum);
-  }
+  const R Qv[6] = {Q00, Q11, Q22, Q01, Q02, Q12};
+  const R Pv[6] = {P00, P11, P22, P01, P02, P12};
+  element_outputs<R, FLAGS>(c, inv_det, u, G, gp, S, psum, trG, mu_eff, stau, T, Qv, Pv, P, F);
 }
 
 // Reverse sweep: given w[a][0..3] (cotangent of F[a][0..3]), returns
@@ -316,10 +335,15 @@ __device__ __forceinline__ void element_rhs(const R c[3][3], R inv_det, R rh, co
 // It differentiates exactly the sequence of element_rhs (same intermediates),
 // recomputing the forward quantities; every product is written as a chain of
 // fused multiply-adds.
-template <class R, int FLAGS>
-__device__ __forceinline__ void element_vjp(const R c[3][3], R inv_det, R rh, const R u[4][3],
-                                            const R p[4], const R w[4][4], const ElemParams<R>& P,
-                                            R gu[4][3], R gpo[4]) {
+//
+// WITH_F: also write the element's forward outputs F (element_outputs) from
+// the recomputed intermediates, so that one pass yields the RHS entries and
+// the vector-Jacobian product at the same state.
+template <class R, int FLAGS, bool WITH_F>
+__device__ __forceinline__ void element_vjp_impl(const R c[3][3], R inv_det, R rh,
+                                                 const R u[4][3], const R p[4], const R w[4][4],
+                                                 const ElemParams<R>& P, R gu[4][3], R gpo[4],
+                                                 R (*F)[4]) {
   using M = MathOps<R>;
   constexpr bool VREMAN = (FLAGS & kVreman) != 0;
   constexpr bool SKEW = (FLAGS & kSkew) != 0;
@@ -403,7 +427,8 @@ __device__ __forceinline__ void element_vjp(const R c[3][3], R inv_det, R rh, co
       Q01 += tu[0] * ug[1];
       Q02 += tu[0] * ug[2];
       Q12 += tu[1] * ug[2];
-    } else {
+    }
+    if constexpr (TAUE || (WITH_F && SKEW)) {
       P00 += ug[0] * ug[0];
       P11 += ug[1] * ug[1];
       P22 += ug[2] * ug[2];
@@ -422,6 +447,14 @@ __device__ __forceinline__ void element_vjp(const R c[3][3], R inv_det, R rh, co
     Q01 = tau_e * P01;
     Q02 = tau_e * P02;
     Q12 = tau_e * P12;
+  }
+
+  if constexpr (WITH_F) {
+    const R Qv[6] = {Q00, Q11, Q22, Q01, Q02, Q12};
+    const R Pv[6] = {P00, P11, P22, P01, P02, P12};
+    const R psum = (p[0] + p[1]) + (p[2] + p[3]);
+    const R trG = G[0][0] + G[1][1] + G[2][2];
+    element_outputs<R, FLAGS>(c, inv_det, u, G, gp, S, psum, trG, mu_eff, stau, T, Qv, Pv, P, F);
   }
 
   // ---- reverse ----
@@ -672,6 +705,23 @@ __device__ __forceinline__ void element_vjp(const R c[3][3], R inv_det, R rh, co
     gsum += gpo[k + 1];
   }
   gpo[0] = (R)4 * pq - gsum;
+}
+
+template <class R, int FLAGS>
+__device__ __forceinline__ void element_vjp(const R c[3][3], R inv_det, R rh, const R u[4][3],
+                                            const R p[4], const R w[4][4], const ElemParams<R>& P,
+                                            R gu[4][3], R gpo[4]) {
+  element_vjp_impl<R, FLAGS, false>(c, inv_det, rh, u, p, w, P, gu, gpo, nullptr);
+}
+
+// The element RHS F and the vector-Jacobian product (gu, gpo) of w at the
+// same state in one pass: the forward intermediates are computed once.
+template <class R, int FLAGS>
+__device__ __forceinline__ void element_rhs_vjp(const R c[3][3], R inv_det, R rh,
+                                                const R u[4][3], const R p[4], const R w[4][4],
+                                                const ElemParams<R>& P, R F[4][4], R gu[4][3],
+                                                R gpo[4]) {
+  element_vjp_impl<R, FLAGS, true>(c, inv_det, rh, u, p, w, P, gu, gpo, F);
 }
 
 }  // namespace nsrhs

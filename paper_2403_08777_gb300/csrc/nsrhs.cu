@@ -438,6 +438,11 @@ __device__ __forceinline__ void scatter_add(double* p, double x) {
     atomicAdd(p, x);
 }
 
+// A result entry as double: itself, or a float widened with integer
+// operations (no FP64 instruction).
+__device__ __forceinline__ double to_double(double x) { return x; }
+__device__ __forceinline__ double to_double(float x) { return nsrhs::widen_f32(x); }
+
 // FP64 forward of element e: streamed connectivity and cached geometry,
 // gathered nodal (u, p), register-resident element arithmetic, immediate
 // scatter of the 16 entries.
@@ -688,6 +693,45 @@ __global__ void __launch_bounds__(kThreads)
   for (int64_t e = e0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < e1;
        e += (int64_t)gridDim.x * blockDim.x)
     vjp_mixed_element<FLAGS, true>(N, E, e, conn, geom_f, up, cot, P, grad);
+}
+
+// The RHS and the vector-Jacobian product at the same state in one pass
+// (element_rhs_vjp): one gather of (u, p) and the cotangent, one geometry
+// read, the forward intermediates computed once; R = double (FP64) or float
+// (mixed: float arithmetic, double accumulation by integer widening).
+template <class R, int FLAGS>
+__global__ void __launch_bounds__(kThreads, NSRHS_VJP_MIN_CTAS)
+    rhs_vjp_atomic_kernel(int64_t N, int64_t E, const int32_t* __restrict__ conn,
+                          const R* __restrict__ geom, const R* __restrict__ up,
+                          const R* __restrict__ cot, ElemParams<R> P, double* __restrict__ rhs,
+                          double* __restrict__ grad) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int32_t v[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) v[a] = ldg(conn + a * E + e);
+    R u[4][3], p[4], w[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) u[a][i] = ldg(up + i * N + v[a]);
+      p[a] = ldg(up + 3 * N + v[a]);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) w[a][k] = ldg(cot + k * N + v[a]);
+    }
+    R c[3][3], inv_det, rh;
+    load_geometry(geom, E, e, c, inv_det, rh);
+    R F[4][4], gu[4][3], gp[4];
+    nsrhs::element_rhs_vjp<R, FLAGS>(c, inv_det, rh, u, p, w, P, F, gu, gp);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) atomicAdd(rhs + k * N + v[a], to_double(F[a][k]));
+#pragma unroll
+      for (int i = 0; i < 3; ++i) atomicAdd(grad + i * N + v[a], to_double(gu[a][i]));
+      atomicAdd(grad + 3 * N + v[a], to_double(gp[a]));
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1404,6 +1448,36 @@ nsrhs_status nsrhs_assemble_vjp(const nsrhs_mesh* m, const nsrhs_params* p, cons
     with_flags(formulation_flags(p), [&](auto fl) {
       vjp_mixed_atomic_kernel<decltype(fl)::value><<<grid, kThreads, 0, s>>>(
           N, E, m->conn, m->geom_f, (const float*)up, (const float*)cot, P, grad);
+    });
+  }
+  return cuda_status(cudaGetLastError());
+}
+
+nsrhs_status nsrhs_assemble_rhs_vjp(const nsrhs_mesh* m, const nsrhs_params* p, const void* up,
+                                    const void* cot, double* rhs, double* grad, void* stream) {
+  if (!is_live(m) || !up || !cot || !rhs || !grad || rhs == grad) return NSRHS_EINVAL;
+  nsrhs_status st = check_params(p);
+  if (st != NSRHS_OK) return st;
+  if (p->scatter != NSRHS_SCATTER_AUTO && p->scatter != NSRHS_SCATTER_ATOMIC)
+    return NSRHS_EUNSUPPORTED;
+  cudaStream_t s = (cudaStream_t)stream;
+  DeviceGuard dg(m->device);
+  if (!dg.ok) return NSRHS_ECUDA;
+  const int64_t N = m->n_nodes, E = m->n_elems;
+  NSRHS_TRY(cudaMemsetAsync(rhs, 0, sizeof(double) * 4 * N, s));
+  NSRHS_TRY(cudaMemsetAsync(grad, 0, sizeof(double) * 4 * N, s));
+  const unsigned grid = grid_for(E, m->device, 16);
+  if (p->precision == NSRHS_FP64) {
+    auto P = elem_params<double>(p);
+    with_flags(formulation_flags(p), [&](auto fl) {
+      rhs_vjp_atomic_kernel<double, decltype(fl)::value><<<grid, kThreads, 0, s>>>(
+          N, E, m->conn, m->geom, (const double*)up, (const double*)cot, P, rhs, grad);
+    });
+  } else {
+    auto P = elem_params<float>(p);
+    with_flags(formulation_flags(p), [&](auto fl) {
+      rhs_vjp_atomic_kernel<float, decltype(fl)::value><<<grid, kThreads, 0, s>>>(
+          N, E, m->conn, m->geom_f, (const float*)up, (const float*)cot, P, rhs, grad);
     });
   }
   return cuda_status(cudaGetLastError());

@@ -84,6 +84,14 @@ int main() {
     std::printf("%s instructions (FMA-contracted estimate): fwd %ld vjp %ld\n",
                 vreman ? "vreman" : "plain", fwd_inst, vjp_inst);
     {
+      Cnt F3[4][4], gu3[4][3], gp3[4];
+      reset();
+      if (vreman) element_rhs_vjp<Cnt, kVreman>(c, inv_det, rh, u, p, w, P, F3, gu3, gp3);
+      else element_rhs_vjp<Cnt, 0>(c, inv_det, rh, u, p, w, P, F3, gu3, gp3);
+      std::printf("%s rhs+vjp %ld sfu %ld instructions %ld\n", vreman ? "vreman" : "plain",
+                  total(), g_sfu, total() - g_fused);
+    }
+    {
       Cnt F2[4][4];
       reset();
       if (vreman) element_rhs<Cnt, kVreman>(c, inv_det, rh, u, p, P, F2);

@@ -15,8 +15,9 @@ ROOT = os.path.dirname(HERE)
 
 def bench_constants():
     src = open(os.path.join(ROOT, "bench.py")).read()
-    plain = re.search(r'FLOPS_PER_TET = \{"fwd": (\d+), "vjp": (\d+)\}', src)
-    vrem = re.search(r'FLOPS_PER_TET_VREMAN = \{"fwd": (\d+), "vjp": (\d+)\}', src)
+    pat = r'\{"fwd": (\d+), "vjp": (\d+), "rhs_vjp": (\d+)\}'
+    plain = re.search(r'FLOPS_PER_TET = ' + pat, src)
+    vrem = re.search(r'FLOPS_PER_TET_VREMAN = ' + pat, src)
     return tuple(map(int, plain.groups())), tuple(map(int, vrem.groups()))
 
 
@@ -32,6 +33,9 @@ def test_flop_census_matches_bench(tmp_path):
         m = re.match(r"(\w+) fwd (\d+) sfu \d+ vjp (\d+) sfu \d+", line)
         if m:
             got[m.group(1)] = (int(m.group(2)), int(m.group(3)))
+        m = re.match(r"(\w+) rhs\+vjp (\d+) sfu", line)
+        if m:
+            got[m.group(1)] += (int(m.group(2)),)
     plain, vrem = bench_constants()
     assert got["plain"] == plain
     assert got["vreman"] == vrem

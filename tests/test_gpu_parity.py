@@ -392,3 +392,40 @@ def test_mixed_precision_adjoint(dev, cv, conv):
         g = m.assemble_vjp(up.float(), cot_d.float(), p).cpu().numpy()
         assert relerr(g, ref) <= TOL_VJP_FD, (scatter, relerr(g, ref))
     m.close()
+
+
+@pytest.mark.parametrize("cv,conv,tau", [(0.0, "convective", "gauss"), (0.07, "convective", "gauss"),
+                                         (0.0, "skew", "gauss"), (0.07, "skew", "element")])
+def test_one_pass_rhs_and_vjp(dev, cv, conv, tau):
+    """nsrhs_assemble_rhs_vjp: both outputs against the oracle (FP64 and
+    mixed), on a mesh with a ragged element count."""
+    w = mg.make_workload(11, jitter=0.2, order="random", mu=1e-3, mag_max=3.0, c_vreman=cv)
+    okw = dict(c_vreman=cv, skew=conv == "skew", tau_elem=tau == "element")
+    ref = oracle.assemble(w.coords, w.conn, w.up, w.rho, w.mu, **okw)
+    cot = mg.normal((4, w.n_nodes), seed=mg.SEED_COT)
+    gref = oracle.vjp(w.coords, w.conn, w.up, cot, w.rho, w.mu, **okw)
+    coords, conn, up, cot_d = on_dev(dev, w.coords, w.conn, w.up, cot)
+    m = ns.Mesh(coords, conn)
+    p = ns.Params(rho=w.rho, mu=w.mu, c_vreman=cv, convection=conv, tau=tau)
+    r, g = m.assemble_rhs_vjp(up, cot_d, p)
+    check_fp64(r.cpu().numpy(), ref)
+    assert relerr(g.cpu().numpy(), gref) <= TOL_VJP_ORACLE
+    pm = ns.Params(rho=w.rho, mu=w.mu, c_vreman=cv, convection=conv, tau=tau, precision="mixed")
+    r, g = m.assemble_rhs_vjp(up.float(), cot_d.float(), pm)
+    assert relerr(r.cpu().numpy(), ref) <= TOL_MIXED
+    assert relerr(g.cpu().numpy(), gref) <= TOL_VJP_FD
+    m.close()
+
+
+def test_one_pass_argument_errors(dev):
+    w = mg.make_workload(3)
+    coords, conn, up = on_dev(dev, w.coords, w.conn, w.up)
+    m = ns.Mesh(coords, conn)
+    out = torch.empty_like(up)
+    with pytest.raises(ns.NSRHSError) as ei:
+        m.assemble_rhs_vjp(up, up, ns.Params(), out=(out, out))
+    assert ei.value.status == _abi.EINVAL
+    with pytest.raises(ns.NSRHSError) as ei:
+        m.assemble_rhs_vjp(up, up, ns.Params(scatter="block"))
+    assert ei.value.status == _abi.EUNSUPPORTED
+    m.close()
