@@ -230,15 +230,16 @@ struct NodeSum<float> {
   __device__ __forceinline__ double value() const { return widen_f32(s) + widen_f32(c); }
 };
 
-// Forward assembly with block-staged gathers and scatters; R is the element
-// arithmetic type (float: mixed form, double: FP64 form). Dynamic shared
-// memory: block_kernel_smem<R, COLOUR>() bytes.
-// Resident CTAs per SM the compiler must allow (register cap): the float
-// kernel is latency-bound between its barrier-separated phases, so more CTAs
-// per SM help; the double kernel is bound by the FP64 pipe.
+// Shared memory of the forward block kernel (below), and the resident CTAs
+// per SM the compiler must allow (register cap): the float kernel is
+// latency-bound between its barrier-separated phases, so more CTAs per SM
+// help; the double kernel is bound by the FP64 pipe.
+// (COLOUR: one staging buffer, the copies of a block are waited for at once,
+// so that the RHS prefetch fits beside it at 4 CTAs per SM.)
 template <class R, bool COLOUR>
 constexpr size_t block_kernel_smem() {
-  return 8 * kBlockSlots * sizeof(R) + (COLOUR ? 4 * kBlockElems * sizeof(double) : 0);
+  return (COLOUR ? 8 : 12) * kBlockSlots * sizeof(R) +
+         (COLOUR ? 4 * kBlockElems * sizeof(double) : 0);
 }
 
 template <class R>
@@ -246,6 +247,42 @@ constexpr int block_kernel_min_ctas() {
   return sizeof(R) == 4 ? NSRHS_BLOCK_MIN_CTAS_F32 : 2;
 }
 
+// Asynchronous global-to-shared copies (cp.async): the gathers of the next
+// block are in flight while the current block computes.
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(BYTES)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int PENDING>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(PENDING) : "memory");
+}
+
+// Issues the copies of block b's nodal (u, v, w, p) into buf [4][kBlockSlots].
+template <class R>
+__device__ __forceinline__ void stage_block(int64_t N, int64_t b,
+                                            const int64_t* __restrict__ node_off,
+                                            const int32_t* __restrict__ nodes,
+                                            const R* __restrict__ up, R* buf) {
+  const int64_t off = __ldg(node_off + b);
+  const int nb = (int)(__ldg(node_off + b + 1) - off);
+  for (int j = threadIdx.x; j < nb; j += kBlockElems) {
+    const int64_t v = __ldg(nodes + off + j);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) cp_async<sizeof(R)>(buf + k * kBlockSlots + j, up + k * N + v);
+  }
+}
+
+// Forward assembly with block-staged gathers and scatters; R is the element
+// arithmetic type (float: mixed form, double: FP64 form). Dynamic shared
+// memory: block_kernel_smem<R, COLOUR>() bytes: two staging buffers for the
+// nodal values (the next block's copies land in one while the current block
+// computes from the other) and one for the element entries.
 //
 // COLOUR: the CTAs process the blocks order[i0 .. i1) of one block colour (no
 // two share a node), and each node's sums are added with a plain
@@ -259,21 +296,28 @@ __global__ void __launch_bounds__(kBlockElems, block_kernel_min_ctas<R>())
                      double* __restrict__ rhs, const int32_t* __restrict__ order = nullptr,
                      int64_t i0 = 0, int64_t i1 = 0) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  R* su = reinterpret_cast<R*>(smem_raw);  // [4][kBlockSlots] nodal u, v, w, p
-  R* sF = su + 4 * kBlockSlots;             // [4][kBlockSlots] element entries by slot
+  R* su0 = reinterpret_cast<R*>(smem_raw);  // [4][kBlockSlots] nodal u, v, w, p (even steps)
+  R* su1 = COLOUR ? su0 : su0 + 4 * kBlockSlots;  // the same (odd steps)
+  R* sF = su1 + 4 * kBlockSlots;             // [4][kBlockSlots] element entries by slot
   // COLOUR only: [4][kBlockElems] prefetched RHS of each thread's first node
   double* sold = reinterpret_cast<double*>(sF + 4 * kBlockSlots);
   const int tid = threadIdx.x;
   const int64_t first = COLOUR ? i0 : 0, last = COLOUR ? i1 : n_blocks;
-  for (int64_t i = first + blockIdx.x; i < last; i += gridDim.x) {
-    const int64_t b = COLOUR ? (int64_t)__ldg(order + i) : i;
+  auto block_at = [&](int64_t i) -> int64_t { return COLOUR ? (int64_t)__ldg(order + i) : i; };
+  int64_t i = first + blockIdx.x;
+  if (i < last) stage_block(N, block_at(i), node_off, nodes, up, su0);
+  cp_async_commit();
+  for (int step = 0; i < last; i += gridDim.x, ++step) {
+    R* su = (step & 1) ? su1 : su0;
+    const int64_t b = block_at(i);
+    // the next block's copies go into the other buffer, whose last readers
+    // finished before the previous step's middle barrier (COLOUR: one buffer,
+    // staged after this step's middle barrier below)
+    if (!COLOUR && i + gridDim.x < last)
+      stage_block(N, block_at(i + gridDim.x), node_off, nodes, up, (step & 1) ? su0 : su1);
+    cp_async_commit();
     const int64_t off = node_off[b];
     const int nb = (int)(node_off[b + 1] - off);
-    for (int j = tid; j < nb; j += kBlockElems) {
-      const int64_t v = __ldg(nodes + off + j);
-#pragma unroll
-      for (int k = 0; k < 4; ++k) su[k * kBlockSlots + j] = __ldg(up + k * N + v);
-    }
     // COLOUR: the current RHS of this thread's first node, loaded into shared
     // memory now so that the loads overlap the element arithmetic (no other
     // CTA of this launch writes it, and earlier colours' launches have
@@ -285,7 +329,8 @@ __global__ void __launch_bounds__(kBlockElems, block_kernel_min_ctas<R>())
         for (int k = 0; k < 4; ++k) sold[k * kBlockElems + tid] = rhs[k * N + v];
       }
     }
-    __syncthreads();
+    cp_async_wait<1>();  // this block's copies (all but the newest group) have landed
+    __syncthreads();     // ... for every thread; the previous block's sums are done
     const int64_t e = b * kBlockElems + tid;
     if (e < E) {
       int lc[4];
@@ -295,7 +340,7 @@ __global__ void __launch_bounds__(kBlockElems, block_kernel_min_ctas<R>())
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
 #pragma unroll
-        for (int i = 0; i < 3; ++i) u[a][i] = su[i * kBlockSlots + lc[a]];
+        for (int k = 0; k < 3; ++k) u[a][k] = su[k * kBlockSlots + lc[a]];
         p[a] = su[3 * kBlockSlots + lc[a]];
       }
       R c[3][3], inv_det, rh;
@@ -313,6 +358,12 @@ __global__ void __launch_bounds__(kBlockElems, block_kernel_min_ctas<R>())
         for (int k = 0; k < 4; ++k) sF[k * kBlockSlots + 4 * tid + a] = F[a][k];
     }
     __syncthreads();
+    if constexpr (COLOUR) {
+      // single buffer, no longer read: the next block's copies overlap the sums
+      if (i + gridDim.x < last)
+        stage_block(N, block_at(i + gridDim.x), node_off, nodes, up, su0);
+      cp_async_commit();
+    }
     const uint16_t* bslots = slots + b * kBlockSlots;
     for (int j = tid; j < nb; j += kBlockElems) {
       const int r0 = __ldg(runs + off + b + j), r1 = __ldg(runs + off + b + j + 1);
@@ -332,8 +383,8 @@ __global__ void __launch_bounds__(kBlockElems, block_kernel_min_ctas<R>())
           atomicAdd(rhs + k * N + v, acc[k].value());
       }
     }
-    __syncthreads();
   }
+  cp_async_wait<0>();
 }
 
 // Adjoint with block-staged gathers and scatters: the reverse of the forward

@@ -1326,10 +1326,13 @@ nsrhs_status nsrhs_assemble(const nsrhs_mesh* m, const nsrhs_params* p, const vo
       auto P = elem_params<float>(p);
       const size_t smem = nsrhs::block_kernel_smem<float, false>();
       with_flags(flags, [&](auto fl) {
-        nsrhs::fwd_block_kernel<float, decltype(fl)::value>
-            <<<grid, nsrhs::kBlockElems, smem, s>>>(N, E, nb, m->blk_node_off, m->blk_nodes,
-                                                    m->blk_runs, m->blk_slots, m->blk_lconn,
-                                                    m->geom_f, (const float*)up, P, rhs);
+        auto kern = nsrhs::fwd_block_kernel<float, decltype(fl)::value>;
+        err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err == cudaSuccess)
+          kern<<<grid, nsrhs::kBlockElems, smem, s>>>(N, E, nb, m->blk_node_off, m->blk_nodes,
+                                                      m->blk_runs, m->blk_slots, m->blk_lconn,
+                                                      m->geom_f, (const float*)up, P, rhs,
+                                                      nullptr, 0, 0);
       });
     }
     if (err != cudaSuccess) return cuda_status(err);
