@@ -3,15 +3,16 @@
 // Setup (once per mesh): elements are put in Morton order of their centroids,
 // so that consecutive elements are close in space, and cut into blocks of
 // kBlockElems elements. For every block the sorted list of the distinct nodes
-// it touches, its local connectivity (an index into that list per element
-// and local node) and, per distinct node, the run of contribution slots
-// (slot = 4 * element-in-block + local node) that land on it are stored.
+// it touches and, per distinct node, its run [runs[j], runs[j + 1]) in the
+// block's contributions sorted by node are stored; per element and local
+// node, its distinct-node index and the position of its contribution in that
+// sorted order (lmap = index << 16 | position).
 //
 // Assembly (per call): one CTA per block loads the nodal values of its
 // distinct nodes once into shared memory, each thread computes one element
-// from shared memory, writes its 16 entries to shared memory, and each
-// distinct node's entries are summed in double precision in a fixed order
-// (its run) and added to the global RHS with one atomic per component. The
+// from shared memory, writes its 16 entries to shared memory at their sorted
+// positions, and each distinct node's entries (a contiguous run) are summed
+// in a fixed order and added to the global RHS with one atomic per component. The
 // global atomics drop from 16 per element to 4 per (block, distinct node), and
 // the sums inside a block do not depend on scheduling.
 #pragma once
@@ -113,18 +114,19 @@ __global__ void permute_conn_kernel(int64_t E, const int32_t* __restrict__ in,
   }
 }
 
-// Per block: sort its (node << 16 | slot) keys, find the distinct nodes.
+// Per block: sort its (node << 16 | slot) keys (slot = 4 * element-in-block
+// + local node), find the distinct nodes.
 // pass 0 writes counts[b] = number of distinct nodes;
 // pass 1 (node_off = exclusive sum of counts) writes
 //   nodes[node_off[b] + j]        j-th distinct node (ascending)
 //   runs[node_off[b] + b + j]     first sorted position of node j (runs[.. + n] = #valid)
-//   slots[b * kBlockSlots + i]    slot of sorted position i
-//   lconn[a * E + e]              distinct-node index of (element e, local node a)
+//   lmap[a * E + e]               (distinct-node index << 16) | sorted position of
+//                                 (element e, local node a)
 __global__ void __launch_bounds__(kBlockElems)
     block_plan_kernel(int pass, int64_t E, const int32_t* __restrict__ conn,
                       int64_t* __restrict__ counts, const int64_t* __restrict__ node_off,
                       int32_t* __restrict__ nodes, uint16_t* __restrict__ runs,
-                      uint16_t* __restrict__ slots, uint16_t* __restrict__ lconn) {
+                      uint32_t* __restrict__ lmap) {
   __shared__ unsigned long long key[kBlockSlots];
   __shared__ int part[kBlockElems];
   const int tid = threadIdx.x;
@@ -188,12 +190,11 @@ __global__ void __launch_bounds__(kBlockElems)
     ++n_valid_here;
     u += flag[r];
     const int slot = (int)(kk & 0xffffull);
-    slots[b * kBlockSlots + i] = (uint16_t)slot;
     if (flag[r]) {
       nodes[off + u] = (int32_t)(kk >> 16);
       runs[off + b + u] = (uint16_t)i;
     }
-    lconn[(int64_t)(slot & 3) * E + e0 + (slot >> 2)] = (uint16_t)u;
+    lmap[(int64_t)(slot & 3) * E + e0 + (slot >> 2)] = ((uint32_t)u << 16) | (uint32_t)i;
   }
   // number of valid positions = elements in the block * 4
   if (tid == 0) {
@@ -291,7 +292,7 @@ template <class R, int FLAGS, bool COLOUR = false>
 __global__ void __launch_bounds__(kBlockElems, block_kernel_min_ctas<R>())
     fwd_block_kernel(int64_t N, int64_t E, int64_t n_blocks, const int64_t* __restrict__ node_off,
                      const int32_t* __restrict__ nodes, const uint16_t* __restrict__ runs,
-                     const uint16_t* __restrict__ slots, const uint16_t* __restrict__ lconn,
+                     const uint32_t* __restrict__ lmap,
                      const R* __restrict__ geom, const R* __restrict__ up, ElemParams<R> P,
                      double* __restrict__ rhs, const int32_t* __restrict__ order = nullptr,
                      int64_t i0 = 0, int64_t i1 = 0) {
@@ -333,15 +334,13 @@ __global__ void __launch_bounds__(kBlockElems, block_kernel_min_ctas<R>())
     __syncthreads();     // ... for every thread; the previous block's sums are done
     const int64_t e = b * kBlockElems + tid;
     if (e < E) {
-      int lc[4];
-#pragma unroll
-      for (int a = 0; a < 4; ++a) lc[a] = __ldg(lconn + a * E + e);
       R u[4][3], p[4];
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
+        const int lc = (int)(__ldg(lmap + a * E + e) >> 16);
 #pragma unroll
-        for (int k = 0; k < 3; ++k) u[a][k] = su[k * kBlockSlots + lc[a]];
-        p[a] = su[3 * kBlockSlots + lc[a]];
+        for (int k = 0; k < 3; ++k) u[a][k] = su[k * kBlockSlots + lc];
+        p[a] = su[3 * kBlockSlots + lc];
       }
       R c[3][3], inv_det, rh;
 #pragma unroll
@@ -353,9 +352,12 @@ __global__ void __launch_bounds__(kBlockElems, block_kernel_min_ctas<R>())
       R F[4][4];
       element_rhs<R, FLAGS>(c, inv_det, rh, u, p, P, F);
 #pragma unroll
-      for (int a = 0; a < 4; ++a)
+      for (int a = 0; a < 4; ++a) {
+        // reloaded (a cache hit) rather than held in registers through the arithmetic
+        const int pos = (int)(__ldg(lmap + a * E + e) & 0xffffu);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) sF[k * kBlockSlots + 4 * tid + a] = F[a][k];
+        for (int k = 0; k < 4; ++k) sF[k * kBlockSlots + pos] = F[a][k];
+      }
     }
     __syncthreads();
     if constexpr (COLOUR) {
@@ -364,15 +366,13 @@ __global__ void __launch_bounds__(kBlockElems, block_kernel_min_ctas<R>())
         stage_block(N, block_at(i + gridDim.x), node_off, nodes, up, su0);
       cp_async_commit();
     }
-    const uint16_t* bslots = slots + b * kBlockSlots;
     for (int j = tid; j < nb; j += kBlockElems) {
       const int r0 = __ldg(runs + off + b + j), r1 = __ldg(runs + off + b + j + 1);
       const int64_t v = __ldg(nodes + off + j);
       NodeSum<R> acc[4];
       for (int q = r0; q < r1; ++q) {
-        const int sl = __ldg(bslots + q);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) acc[k].add(sF[k * kBlockSlots + sl]);
+        for (int k = 0; k < 4; ++k) acc[k].add(sF[k * kBlockSlots + q]);
       }
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
@@ -389,15 +389,20 @@ __global__ void __launch_bounds__(kBlockElems, block_kernel_min_ctas<R>())
 
 // Adjoint with block-staged gathers and scatters: the reverse of the forward
 // block kernel. Per block the nodal (u, p) and the cotangent of its distinct
-// nodes are staged in shared memory, each thread runs one element's reverse
-// sweep, the 16 gradient entries go back to shared memory (over the staged
-// nodal values, after a barrier), and each node's entries are summed in a
-// fixed order and added with one atomic per component (COLOUR: with a plain
-// read-modify-write, blocks of one colour per launch). Dynamic shared memory:
+// nodes are staged in shared memory (double-buffered: the next block's
+// copies are in flight while the current one computes), each thread runs one
+// element's reverse sweep, the 16 gradient entries go back to shared memory
+// at their sorted positions (over the current block's staged values, after a
+// barrier), and each node's entries are summed in a fixed order and added
+// with one atomic per component (COLOUR: with a plain read-modify-write,
+// blocks of one colour per launch). Dynamic shared memory:
 // block_vjp_smem<R, COLOUR>() bytes.
+// (COLOUR: one staging buffer, staged after a block's sums, measured faster
+// for the coloured launches than two.)
 template <class R, bool COLOUR>
 constexpr size_t block_vjp_smem() {
-  return 8 * kBlockSlots * sizeof(R) + (COLOUR ? 4 * kBlockElems * sizeof(double) : 0);
+  return (COLOUR ? 8 : 16) * kBlockSlots * sizeof(R) +
+         (COLOUR ? 4 * kBlockElems * sizeof(double) : 0);
 }
 
 template <class R>
@@ -405,32 +410,58 @@ constexpr int block_vjp_min_ctas() {
   return sizeof(R) == 4 ? 2 : 1;
 }
 
+// Issues the copies of block b's nodal (u, v, w, p) and cotangent into
+// buf [8][kBlockSlots] (the cotangent at rows 4..7).
+template <class R>
+__device__ __forceinline__ void stage_block_vjp(int64_t N, int64_t b,
+                                                const int64_t* __restrict__ node_off,
+                                                const int32_t* __restrict__ nodes,
+                                                const R* __restrict__ up,
+                                                const R* __restrict__ cot, R* buf) {
+  const int64_t off = __ldg(node_off + b);
+  const int nb = (int)(__ldg(node_off + b + 1) - off);
+  for (int j = threadIdx.x; j < nb; j += kBlockElems) {
+    const int64_t v = __ldg(nodes + off + j);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      cp_async<sizeof(R)>(buf + k * kBlockSlots + j, up + k * N + v);
+      cp_async<sizeof(R)>(buf + (4 + k) * kBlockSlots + j, cot + k * N + v);
+    }
+  }
+}
+
 template <class R, int FLAGS, bool COLOUR = false>
 __global__ void __launch_bounds__(kBlockElems, block_vjp_min_ctas<R>())
     vjp_block_kernel(int64_t N, int64_t E, int64_t n_blocks, const int64_t* __restrict__ node_off,
                      const int32_t* __restrict__ nodes, const uint16_t* __restrict__ runs,
-                     const uint16_t* __restrict__ slots, const uint16_t* __restrict__ lconn,
+                     const uint32_t* __restrict__ lmap,
                      const R* __restrict__ geom, const R* __restrict__ up,
                      const R* __restrict__ cot, ElemParams<R> P, double* __restrict__ grad,
                      const int32_t* __restrict__ order, int64_t i0, int64_t i1) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  R* su = reinterpret_cast<R*>(smem_raw);  // [4][kBlockSlots] nodal u, v, w, p; then entries
-  R* sw = su + 4 * kBlockSlots;             // [4][kBlockSlots] cotangent
-  double* sold = reinterpret_cast<double*>(sw + 4 * kBlockSlots);  // COLOUR: [4][kBlockElems]
+  // two staging buffers [8][kBlockSlots]: u, v, w, p, then the cotangent
+  R* sb0 = reinterpret_cast<R*>(smem_raw);
+  R* sb1 = COLOUR ? sb0 : sb0 + 8 * kBlockSlots;
+  double* sold = reinterpret_cast<double*>(sb1 + 8 * kBlockSlots);  // COLOUR: [4][kBlockElems]
   const int tid = threadIdx.x;
   const int64_t first = COLOUR ? i0 : 0, last = COLOUR ? i1 : n_blocks;
-  for (int64_t i = first + blockIdx.x; i < last; i += gridDim.x) {
-    const int64_t b = COLOUR ? (int64_t)__ldg(order + i) : i;
+  auto block_at = [&](int64_t i) -> int64_t { return COLOUR ? (int64_t)__ldg(order + i) : i; };
+  int64_t i = first + blockIdx.x;
+  if (i < last) stage_block_vjp(N, block_at(i), node_off, nodes, up, cot, sb0);
+  cp_async_commit();
+  for (int step = 0; i < last; i += gridDim.x, ++step) {
+    R* su = (step & 1) ? sb1 : sb0;
+    R* sw = su + 4 * kBlockSlots;
+    const int64_t b = block_at(i);
+    // the other buffer was last read (as entries) in the previous step's sums,
+    // which every thread finished before the previous step's last barrier
+    // (COLOUR: one buffer, staged at the end of the previous step)
+    if (!COLOUR && i + gridDim.x < last)
+      stage_block_vjp(N, block_at(i + gridDim.x), node_off, nodes, up, cot,
+                      (step & 1) ? sb0 : sb1);
+    cp_async_commit();
     const int64_t off = node_off[b];
     const int nb = (int)(node_off[b + 1] - off);
-    for (int j = tid; j < nb; j += kBlockElems) {
-      const int64_t v = __ldg(nodes + off + j);
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        su[k * kBlockSlots + j] = __ldg(up + k * N + v);
-        sw[k * kBlockSlots + j] = __ldg(cot + k * N + v);
-      }
-    }
     if constexpr (COLOUR) {
       if (tid < nb) {
         const int64_t v = __ldg(nodes + off + tid);
@@ -438,21 +469,20 @@ __global__ void __launch_bounds__(kBlockElems, block_vjp_min_ctas<R>())
         for (int k = 0; k < 4; ++k) sold[k * kBlockElems + tid] = grad[k * N + v];
       }
     }
+    cp_async_wait<1>();
     __syncthreads();
     const int64_t e = b * kBlockElems + tid;
     R gu[4][3], gp[4];
     if (e < E) {
-      int lc[4];
-#pragma unroll
-      for (int a = 0; a < 4; ++a) lc[a] = __ldg(lconn + a * E + e);
       R u[4][3], p[4], w[4][4];
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
+        const int lc = (int)(__ldg(lmap + a * E + e) >> 16);
 #pragma unroll
-        for (int k = 0; k < 3; ++k) u[a][k] = su[k * kBlockSlots + lc[a]];
-        p[a] = su[3 * kBlockSlots + lc[a]];
+        for (int k = 0; k < 3; ++k) u[a][k] = su[k * kBlockSlots + lc];
+        p[a] = su[3 * kBlockSlots + lc];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) w[a][k] = sw[k * kBlockSlots + lc[a]];
+        for (int k = 0; k < 4; ++k) w[a][k] = sw[k * kBlockSlots + lc];
       }
       R c[3][3], inv_det, rh;
 #pragma unroll
@@ -467,21 +497,20 @@ __global__ void __launch_bounds__(kBlockElems, block_vjp_min_ctas<R>())
     if (e < E) {
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
+        const int pos = (int)(__ldg(lmap + a * E + e) & 0xffffu);
 #pragma unroll
-        for (int k = 0; k < 3; ++k) su[k * kBlockSlots + 4 * tid + a] = gu[a][k];
-        su[3 * kBlockSlots + 4 * tid + a] = gp[a];
+        for (int k = 0; k < 3; ++k) su[k * kBlockSlots + pos] = gu[a][k];
+        su[3 * kBlockSlots + pos] = gp[a];
       }
     }
     __syncthreads();
-    const uint16_t* bslots = slots + b * kBlockSlots;
     for (int j = tid; j < nb; j += kBlockElems) {
       const int r0 = __ldg(runs + off + b + j), r1 = __ldg(runs + off + b + j + 1);
       const int64_t v = __ldg(nodes + off + j);
       NodeSum<R> acc[4];
       for (int q = r0; q < r1; ++q) {
-        const int sl = __ldg(bslots + q);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) acc[k].add(su[k * kBlockSlots + sl]);
+        for (int k = 0; k < 4; ++k) acc[k].add(su[k * kBlockSlots + q]);
       }
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
@@ -492,8 +521,14 @@ __global__ void __launch_bounds__(kBlockElems, block_vjp_min_ctas<R>())
           atomicAdd(grad + k * N + v, acc[k].value());
       }
     }
-    __syncthreads();
+    __syncthreads();  // the sums have read su before it is staged into again
+    if constexpr (COLOUR) {
+      if (i + gridDim.x < last)
+        stage_block_vjp(N, block_at(i + gridDim.x), node_off, nodes, up, cot, sb0);
+      cp_async_commit();
+    }
   }
+  cp_async_wait<0>();
 }
 
 }  // namespace nsrhs

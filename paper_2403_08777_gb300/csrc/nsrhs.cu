@@ -49,8 +49,7 @@ struct nsrhs_mesh {
   int64_t* blk_node_off = nullptr;  // [n_blocks + 1]
   int32_t* blk_nodes = nullptr;     // [blk_node_off[n_blocks]]
   uint16_t* blk_runs = nullptr;     // [blk_node_off[n_blocks] + n_blocks]
-  uint16_t* blk_slots = nullptr;    // [n_blocks * kBlockSlots]
-  uint16_t* blk_lconn = nullptr;    // [4][E]
+  uint32_t* blk_lmap = nullptr;     // [4][E] (distinct-node index << 16) | sorted position
   double* inv_mass = nullptr;       // [N] 1 / lumped mass
   double* mass = nullptr;           // [N] lumped mass sum_e V_e / 4
   // Colour-major copy for the COLOUR scatter (colour.cuh), built when the
@@ -902,11 +901,10 @@ nsrhs_status build_blocks(nsrhs_mesh* m, cudaStream_t s) {
   DevBuf counts, tmp;
   NSRHS_TRY(counts.alloc((nb + 1) * sizeof(int64_t)));
   if ((st = mesh_alloc(m, &m->blk_node_off, (size_t)nb + 1)) != NSRHS_OK) return st;
-  if ((st = mesh_alloc(m, &m->blk_lconn, 4 * (size_t)E)) != NSRHS_OK) return st;
-  if ((st = mesh_alloc(m, &m->blk_slots, (size_t)nb * nsrhs::kBlockSlots)) != NSRHS_OK) return st;
+  if ((st = mesh_alloc(m, &m->blk_lmap, 4 * (size_t)E)) != NSRHS_OK) return st;
   // pass 0: distinct nodes per block
   nsrhs::block_plan_kernel<<<(unsigned)nb, nsrhs::kBlockElems, 0, s>>>(
-      0, E, m->conn, counts.as<int64_t>(), nullptr, nullptr, nullptr, nullptr, nullptr);
+      0, E, m->conn, counts.as<int64_t>(), nullptr, nullptr, nullptr, nullptr);
   NSRHS_TRY(cudaGetLastError());
   // node_off = exclusive prefix sum of the counts (counts[nb] = 0)
   {
@@ -924,8 +922,7 @@ nsrhs_status build_blocks(nsrhs_mesh* m, cudaStream_t s) {
   if ((st = mesh_alloc(m, &m->blk_nodes, (size_t)total)) != NSRHS_OK) return st;
   if ((st = mesh_alloc(m, &m->blk_runs, (size_t)(total + nb))) != NSRHS_OK) return st;
   nsrhs::block_plan_kernel<<<(unsigned)nb, nsrhs::kBlockElems, 0, s>>>(
-      1, E, m->conn, nullptr, m->blk_node_off, m->blk_nodes, m->blk_runs, m->blk_slots,
-      m->blk_lconn);
+      1, E, m->conn, nullptr, m->blk_node_off, m->blk_nodes, m->blk_runs, m->blk_lmap);
   NSRHS_TRY(cudaGetLastError());
   return NSRHS_OK;
 }
@@ -1259,7 +1256,7 @@ nsrhs_status nsrhs_assemble(const nsrhs_mesh* m, const nsrhs_params* p, const vo
           err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
           if (err == cudaSuccess)
             kern<<<grid, nsrhs::kBlockElems, smem, s>>>(
-                N, E, nb, m->blk_node_off, m->blk_nodes, m->blk_runs, m->blk_slots, m->blk_lconn,
+                N, E, nb, m->blk_node_off, m->blk_nodes, m->blk_runs, m->blk_lmap,
                 m->geom, (const double*)up, P, rhs, m->bcol_order, i0, i1);
         });
       } else {
@@ -1270,7 +1267,7 @@ nsrhs_status nsrhs_assemble(const nsrhs_mesh* m, const nsrhs_params* p, const vo
           err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
           if (err == cudaSuccess)
             kern<<<grid, nsrhs::kBlockElems, smem, s>>>(
-                N, E, nb, m->blk_node_off, m->blk_nodes, m->blk_runs, m->blk_slots, m->blk_lconn,
+                N, E, nb, m->blk_node_off, m->blk_nodes, m->blk_runs, m->blk_lmap,
                 m->geom_f, (const float*)up, P, rhs, m->bcol_order, i0, i1);
         });
       }
@@ -1318,7 +1315,7 @@ nsrhs_status nsrhs_assemble(const nsrhs_mesh* m, const nsrhs_params* p, const vo
         err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err == cudaSuccess)
           kern<<<grid, nsrhs::kBlockElems, smem, s>>>(N, E, nb, m->blk_node_off, m->blk_nodes,
-                                                      m->blk_runs, m->blk_slots, m->blk_lconn,
+                                                      m->blk_runs, m->blk_lmap,
                                                       m->geom, (const double*)up, P, rhs,
                                                       nullptr, 0, 0);
       });
@@ -1330,7 +1327,7 @@ nsrhs_status nsrhs_assemble(const nsrhs_mesh* m, const nsrhs_params* p, const vo
         err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err == cudaSuccess)
           kern<<<grid, nsrhs::kBlockElems, smem, s>>>(N, E, nb, m->blk_node_off, m->blk_nodes,
-                                                      m->blk_runs, m->blk_slots, m->blk_lconn,
+                                                      m->blk_runs, m->blk_lmap,
                                                       m->geom_f, (const float*)up, P, rhs,
                                                       nullptr, 0, 0);
       });
@@ -1369,7 +1366,11 @@ nsrhs_status nsrhs_assemble_vjp(const nsrhs_mesh* m, const nsrhs_params* p, cons
     return NSRHS_EUNSUPPORTED;
   NSRHS_TRY(cudaMemsetAsync(grad, 0, sizeof(double) * 4 * N, s));
   const int flags = formulation_flags(p);
-  if (p->scatter == NSRHS_SCATTER_BLOCK || p->scatter == NSRHS_SCATTER_BLOCK_COLOUR) {
+  // AUTO: atomics for the FP64 form (FP64-pipe-bound), blocks for the mixed
+  // form (measured faster)
+  const bool block = p->scatter == NSRHS_SCATTER_BLOCK ||
+                     (p->scatter == NSRHS_SCATTER_AUTO && p->precision == NSRHS_MIXED);
+  if (block || p->scatter == NSRHS_SCATTER_BLOCK_COLOUR) {
     // BLOCK: one grid over all blocks, atomics; BLOCK_COLOUR: one launch per
     // block colour, plain read-modify-write
     const bool coloured = p->scatter == NSRHS_SCATTER_BLOCK_COLOUR;
@@ -1385,7 +1386,7 @@ nsrhs_status nsrhs_assemble_vjp(const nsrhs_mesh* m, const nsrhs_params* p, cons
         err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err == cudaSuccess)
           kern<<<grid, nsrhs::kBlockElems, smem, s>>>(
-              N, E, nb, m->blk_node_off, m->blk_nodes, m->blk_runs, m->blk_slots, m->blk_lconn,
+              N, E, nb, m->blk_node_off, m->blk_nodes, m->blk_runs, m->blk_lmap,
               geom, u, c, P, grad, coloured ? m->bcol_order : nullptr, i0, i1);
       };
       if (p->precision == NSRHS_FP64) {
