@@ -330,8 +330,9 @@ class StepPipeline:
                 "cot": torch.empty(shape, dtype=torch.float64, device=dev),
                 "rhs": torch.empty(shape, dtype=torch.float64, device=dev),
                 "grad": torch.empty(shape, dtype=torch.float64, device=dev),
-                "loaded": torch.cuda.Event(), "fwd": torch.cuda.Event(),
-                "done": torch.cuda.Event(), "free": torch.cuda.Event(), "used": False})
+                "up_in": torch.cuda.Event(), "cot_in": torch.cuda.Event(),
+                "fwd": torch.cuda.Event(), "done": torch.cuda.Event(),
+                "free": torch.cuda.Event(), "used": False})
 
     def submit(self, k: int, up_host: torch.Tensor, cot_host: torch.Tensor | None,
                rhs_host: torch.Tensor, grad_host: torch.Tensor | None) -> None:
@@ -340,14 +341,17 @@ class StepPipeline:
             if b["used"]:
                 self.s_in.wait_event(b["free"])
             b["up"].copy_(up_host, non_blocking=True)
+            b["up_in"].record(self.s_in)
             if cot_host is not None:
+                # the cotangent's copy overlaps this step's forward
                 b["cot"].copy_(cot_host, non_blocking=True)
-            b["loaded"].record(self.s_in)
+            b["cot_in"].record(self.s_in)
         with torch.cuda.stream(self.s_cmp):
-            self.s_cmp.wait_event(b["loaded"])
+            self.s_cmp.wait_event(b["up_in"])
             self.mesh.assemble(b["up"], self.params, out=b["rhs"])
             b["fwd"].record(self.s_cmp)
             if cot_host is not None:
+                self.s_cmp.wait_event(b["cot_in"])
                 self.mesh.assemble_vjp(b["up"], b["cot"], self.params, out=b["grad"])
             b["done"].record(self.s_cmp)
         with torch.cuda.stream(self.s_out):

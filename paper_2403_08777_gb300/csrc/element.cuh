@@ -77,12 +77,34 @@ struct MathOps<double> {
   static __device__ __forceinline__ double rsqrt_(double x) { return rsqrt_nonneg(x); }
 };
 
+// Single precision (the mixed form): the special-function unit's
+// approximations (relative error about 2^-22 to 2^-23), far inside the mixed
+// form's accuracy, one instruction each instead of a correctly rounded
+// sequence. Arguments as for double.
 template <>
 struct MathOps<float> {
-  static __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
-  static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+#if defined(__CUDA_ARCH__)
+  static __device__ __forceinline__ float rcp(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+  }
+  static __device__ __forceinline__ float sqrt_(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+  }
+  static __device__ __forceinline__ float rsqrt_(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return x > 0.0f ? y : 0.0f;
+  }
+#else
+  static float rcp(float x) { return 1.0f / x; }
+  static float sqrt_(float x) { return sqrtf(x); }
+  static float rsqrt_(float x) { return x > 0.0f ? 1.0f / sqrtf(x) : 0.0f; }
+#endif
   static __device__ __forceinline__ float rcbrt_(float x) { return rcbrtf(x); }
-  static __device__ __forceinline__ float rsqrt_(float x) { return x > 0.0f ? rsqrtf(x) : 0.0f; }
 };
 
 // Element geometry from the edge vectors e[k] = X_{k+1} - X_0: unscaled
@@ -352,14 +374,14 @@ __device__ __forceinline__ void element_vjp_impl(const R c[3][3], R inv_det, R r
   R G[3][3], gp[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    R d1 = u[1][i] - u[0][i], d2 = u[2][i] - u[0][i], d3 = u[3][i] - u[0][i];
+    const R d1 = u[1][i] - u[0][i], d2 = u[2][i] - u[0][i], d3 = u[3][i] - u[0][i];
 #pragma unroll
-    for (int j = 0; j < 3; ++j) G[i][j] = d1 * c[0][j] + d2 * c[1][j] + d3 * c[2][j];
+    for (int j = 0; j < 3; ++j) G[i][j] = fmac(d3, c[2][j], fmac(d2, c[1][j], d1 * c[0][j]));
   }
   {
-    R d1 = p[1] - p[0], d2 = p[2] - p[0], d3 = p[3] - p[0];
+    const R d1 = p[1] - p[0], d2 = p[2] - p[0], d3 = p[3] - p[0];
 #pragma unroll
-    for (int j = 0; j < 3; ++j) gp[j] = d1 * c[0][j] + d2 * c[1][j] + d3 * c[2][j];
+    for (int j = 0; j < 3; ++j) gp[j] = fmac(d3, c[2][j], fmac(d2, c[1][j], d1 * c[0][j]));
   }
   R S[3];
 #pragma unroll
@@ -401,19 +423,19 @@ __device__ __forceinline__ void element_vjp_impl(const R c[3][3], R inv_det, R r
   R P00 = (R)0, P11 = (R)0, P22 = (R)0, P01 = (R)0, P02 = (R)0, P12 = (R)0;
   R tau_e = (R)0, yr_e = (R)0;  // per-element tau and 1/|S_u/4|
   if constexpr (TAUE) {
-    const R sm = (S[0] * S[0] + S[1] * S[1] + S[2] * S[2]) * (R)0.0625;
+    const R sm = fmac(S[2], S[2], fmac(S[1], S[1], S[0] * S[0])) * (R)0.0625;
     yr_e = M::rsqrt_(sm);
-    tau_e = M::rcp(k2 * (sm * yr_e) + k1);
+    tau_e = M::rcp(fmac(k2, sm * yr_e, k1));
   }
 #pragma unroll
   for (int g = 0; g < 4; ++g) {
     R ug[3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) ug[i] = bS[i] + (R)(kQA - kQB) * u[g][i];
+    for (int i = 0; i < 3; ++i) ug[i] = fmac((R)(kQA - kQB), u[g][i], bS[i]);
     if constexpr (!TAUE) {
-      R s = ug[0] * ug[0] + ug[1] * ug[1] + ug[2] * ug[2];
+      const R s = fmac(ug[2], ug[2], fmac(ug[1], ug[1], ug[0] * ug[0]));
       yr[g] = M::rsqrt_(s);
-      tau[g] = M::rcp(k2 * (s * yr[g]) + k1);
+      tau[g] = M::rcp(fmac(k2, s * yr[g], k1));
       stau += tau[g];
       R tu[3];
 #pragma unroll
@@ -421,20 +443,20 @@ __device__ __forceinline__ void element_vjp_impl(const R c[3][3], R inv_det, R r
         tu[i] = tau[g] * ug[i];
         T[i] += tu[i];
       }
-      Q00 += tu[0] * ug[0];
-      Q11 += tu[1] * ug[1];
-      Q22 += tu[2] * ug[2];
-      Q01 += tu[0] * ug[1];
-      Q02 += tu[0] * ug[2];
-      Q12 += tu[1] * ug[2];
+      Q00 = fmac(tu[0], ug[0], Q00);
+      Q11 = fmac(tu[1], ug[1], Q11);
+      Q22 = fmac(tu[2], ug[2], Q22);
+      Q01 = fmac(tu[0], ug[1], Q01);
+      Q02 = fmac(tu[0], ug[2], Q02);
+      Q12 = fmac(tu[1], ug[2], Q12);
     }
     if constexpr (TAUE || (WITH_F && SKEW)) {
-      P00 += ug[0] * ug[0];
-      P11 += ug[1] * ug[1];
-      P22 += ug[2] * ug[2];
-      P01 += ug[0] * ug[1];
-      P02 += ug[0] * ug[2];
-      P12 += ug[1] * ug[2];
+      P00 = fmac(ug[0], ug[0], P00);
+      P11 = fmac(ug[1], ug[1], P11);
+      P22 = fmac(ug[2], ug[2], P22);
+      P01 = fmac(ug[0], ug[1], P01);
+      P02 = fmac(ug[0], ug[2], P02);
+      P12 = fmac(ug[1], ug[2], P12);
     }
   }
   if constexpr (TAUE) {
@@ -470,9 +492,10 @@ __device__ __forceinline__ void element_vjp_impl(const R c[3][3], R inv_det, R r
     for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int j = 0; j < 3; ++j)
-        Om[i][j] = dw[0][i] * c[0][j] + dw[1][i] * c[1][j] + dw[2][i] * c[2][j];
+        Om[i][j] = fmac(dw[2][i], c[2][j], fmac(dw[1][i], c[1][j], dw[0][i] * c[0][j]));
 #pragma unroll
-    for (int j = 0; j < 3; ++j) cw[j] = dw[0][3] * c[0][j] + dw[1][3] * c[1][j] + dw[2][3] * c[2][j];
+    for (int j = 0; j < 3; ++j)
+      cw[j] = fmac(dw[2][3], c[2][j], fmac(dw[1][3], c[1][j], dw[0][3] * c[0][j]));
   }
   const R wcs = (w[0][3] + w[1][3]) + (w[2][3] + w[3][3]);
   const R s6 = inv_det * (R)(1.0 / 6.0);
@@ -494,24 +517,29 @@ __device__ __forceinline__ void element_vjp_impl(const R c[3][3], R inv_det, R r
   {
     R acc = Om[0][0] * G[0][0];
 #pragma unroll
-    for (int q = 1; q < 9; ++q) acc = Om[q / 3][q % 3] * G[q / 3][q % 3] + acc;
+    for (int q = 1; q < 9; ++q) acc = fmac(Om[q / 3][q % 3], G[q / 3][q % 3], acc);
     mub = -s6 * acc;
   }
-  // Qbar = a2 G^T Omega; symmetrised Qs = Qbar + Qbar^T
-  R Qs[3][3];
+  // Qbar = a2 G^T Omega; Qh = (Qbar + Qbar^T)/2, its symmetric part, built
+  // entry by entry (Q is symmetric, so only Qh matters)
+  R Qh[3][3];
   {
-    R Mt[3][3];
+    const R a2h = (R)0.5 * a2;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+      Qh[i][i] = a2 * fmac(G[2][i], Om[2][i], fmac(G[1][i], Om[1][i], G[0][i] * Om[0][i]));
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-      for (int j = 0; j < 3; ++j)
-        Mt[i][j] = G[0][i] * Om[0][j] + G[1][i] * Om[1][j] + G[2][i] * Om[2][j];
-    const R a22 = a2 + a2;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) Qs[i][i] = a22 * Mt[i][i];
-    Qs[0][1] = Qs[1][0] = a2 * (Mt[0][1] + Mt[1][0]);
-    Qs[0][2] = Qs[2][0] = a2 * (Mt[0][2] + Mt[2][0]);
-    Qs[1][2] = Qs[2][1] = a2 * (Mt[1][2] + Mt[2][1]);
+      for (int j = i + 1; j < 3; ++j) {
+        R acc = G[0][i] * Om[0][j];
+        acc = fmac(G[0][j], Om[0][i], acc);
+        acc = fmac(G[1][i], Om[1][j], acc);
+        acc = fmac(G[1][j], Om[1][i], acc);
+        acc = fmac(G[2][i], Om[2][j], acc);
+        acc = fmac(G[2][j], Om[2][i], acc);
+        Qh[i][j] = Qh[j][i] = a2h * acc;
+      }
   }
   // Tbar = b4 Omega^T gph + G^T Rq ; staubar = Rbar . gph ; gpbar = b4 Omega T + stau Rbar
   R Tb[3], gpb[3];
@@ -525,49 +553,49 @@ __device__ __forceinline__ void element_vjp_impl(const R c[3][3], R inv_det, R r
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
       R acc = Om[0][j] * gq[0];
-      acc = Om[1][j] * gq[1] + acc;
-      acc = Om[2][j] * gq[2] + acc;
-      acc = G[0][j] * Rq[0] + acc;
-      acc = G[1][j] * Rq[1] + acc;
-      Tb[j] = G[2][j] * Rq[2] + acc;
+      acc = fmac(Om[1][j], gq[1], acc);
+      acc = fmac(Om[2][j], gq[2], acc);
+      acc = fmac(G[0][j], Rq[0], acc);
+      acc = fmac(G[1][j], Rq[1], acc);
+      Tb[j] = fmac(G[2][j], Rq[2], acc);
     }
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       R acc = stau * Rb[i];
-      acc = Om[i][0] * bT[0] + acc;
-      acc = Om[i][1] * bT[1] + acc;
-      gpb[i] = Om[i][2] * bT[2] + acc;
+      acc = fmac(Om[i][0], bT[0], acc);
+      acc = fmac(Om[i][1], bT[1], acc);
+      gpb[i] = fmac(Om[i][2], bT[2], acc);
     }
   }
-  const R staub = Rb[0] * gp[0] + Rb[1] * gp[1] + Rb[2] * gp[2];
+  const R staub = fmac(Rb[2], gp[2], fmac(Rb[1], gp[1], Rb[0] * gp[0]));
   // Gbar = Omega Qp' + Rq T^T + sum_a wm_a v_a^T - (sum_a wc_a)/24 I,
   // Qp' = a2 Q + a1 I, v_a = -(rho/120)(u_a + S_u)
   R Gb[3][3];
   {
-    const R Qp[3][3] = {{a2 * Q00 + a1, a2 * Q01, a2 * Q02},
-                        {a2 * Q01, a2 * Q11 + a1, a2 * Q12},
-                        {a2 * Q02, a2 * Q12, a2 * Q22 + a1}};
+    const R Qp[3][3] = {{fmac(a2, Q00, a1), a2 * Q01, a2 * Q02},
+                        {a2 * Q01, fmac(a2, Q11, a1), a2 * Q12},
+                        {a2 * Q02, a2 * Q12, fmac(a2, Q22, a1)}};
     const R m120 = P.rho * (R)(SKEW ? -1.0 / 240.0 : -1.0 / 120.0);
     R v[4][3];
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
       const R mS = m120 * S[j];
 #pragma unroll
-      for (int a = 0; a < 4; ++a) v[a][j] = m120 * u[a][j] + mS;
+      for (int a = 0; a < 4; ++a) v[a][j] = fmac(m120, u[a][j], mS);
     }
     const R wc24 = wcs * (R)(1.0 / 24.0);
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
-        R acc = (i == j) ? Rq[i] * T[j] - wc24 : Rq[i] * T[j];
-        acc = Om[i][0] * Qp[0][j] + acc;
-        acc = Om[i][1] * Qp[1][j] + acc;
-        acc = Om[i][2] * Qp[2][j] + acc;
-        acc = w[0][i] * v[0][j] + acc;
-        acc = w[1][i] * v[1][j] + acc;
-        acc = w[2][i] * v[2][j] + acc;
-        Gb[i][j] = w[3][i] * v[3][j] + acc;
+        R acc = (i == j) ? fmac(Rq[i], T[j], -wc24) : Rq[i] * T[j];
+        acc = fmac(Om[i][0], Qp[0][j], acc);
+        acc = fmac(Om[i][1], Qp[1][j], acc);
+        acc = fmac(Om[i][2], Qp[2][j], acc);
+        acc = fmac(w[0][i], v[0][j], acc);
+        acc = fmac(w[1][i], v[1][j], acc);
+        acc = fmac(w[2][i], v[2][j], acc);
+        Gb[i][j] = fmac(w[3][i], v[3][j], acc);
       }
   }
   // Gauss points in reverse: ugb_g = dL/du_g
@@ -591,12 +619,10 @@ __device__ __forceinline__ void element_vjp_impl(const R c[3][3], R inv_det, R r
     R taub = (R)4 * staub;
 #pragma unroll
     for (int i = 0; i < 3; ++i) taub = Tb[i] * S[i] + taub;
-    R qp = (R)0;
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-      for (int j = 0; j < 3; ++j) qp = Qs[i][j] * Pm[i][j] + qp;
-    taub = (R)0.5 * qp + taub;
+      for (int j = 0; j < 3; ++j) taub = fmac(Qh[i][j], Pm[i][j], taub);
     const R db = -(tau_e * tau_e) * taub;
     mub = crh2 * db + mub;
     // |S_u/4| = sqrt(S.S/16): d/dS = S / (16 |S_u/4|)
@@ -604,33 +630,32 @@ __device__ __forceinline__ void element_vjp_impl(const R c[3][3], R inv_det, R r
 #pragma unroll
     for (int i = 0; i < 3; ++i) Sb_tau[i] = tau_e * Tb[i] + sc * S[i];
   }
+  const R te2 = (R)2 * tau_e;
 #pragma unroll
   for (int g = 0; g < 4; ++g) {
     R ug[3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) ug[i] = bS[i] + (R)(kQA - kQB) * u[g][i];
-    R Qu[3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) Qu[i] = Qs[i][0] * ug[0] + Qs[i][1] * ug[1] + Qs[i][2] * ug[2];
+    for (int i = 0; i < 3; ++i) ug[i] = fmac((R)(kQA - kQB), u[g][i], bS[i]);
     if constexpr (!TAUE) {
-      // tau-bar: Q enters as ug^T Qbar ug = ug . (Qs ug) / 2
-      R taub = Tb[0] * ug[0] + staub;
-      taub = Tb[1] * ug[1] + taub;
-      taub = Tb[2] * ug[2] + taub;
-      taub = (R)0.5 * (ug[0] * Qu[0] + ug[1] * Qu[1] + ug[2] * Qu[2]) + taub;
+      // T and Q enter as tau (Tb . u_g + u_g^T Qh u_g): with QT = Tb + Qh u_g,
+      // tau-bar = staub + u_g . QT and the tau-weighted part of u_g-bar is
+      // tau (Tb + 2 Qh u_g) = tau (2 QT - Tb)
+      R QT[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+        QT[i] = fmac(Qh[i][2], ug[2], fmac(Qh[i][1], ug[1], fmac(Qh[i][0], ug[0], Tb[i])));
+      const R taub = fmac(ug[2], QT[2], fmac(ug[1], QT[1], fmac(ug[0], QT[0], staub)));
       const R db = -(tau[g] * tau[g]) * taub;  // d(1/d)
-      mub = crh2 * db + mub;
+      mub = fmac(crh2, db, mub);
       const R sc = (k2 * yr[g]) * db;           // d|u_g| / du_g = u_g / |u_g|
 #pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        R acc = sc * ug[i];
-        acc = tau[g] * Tb[i] + acc;
-        ugb[g][i] = tau[g] * Qu[i] + acc;
-      }
+      for (int i = 0; i < 3; ++i)
+        ugb[g][i] = fmac(tau[g], fmac((R)2, QT[i], -Tb[i]), sc * ug[i]);
     } else {
-      // Q = tau P: d/du_g <Qbar, tau P> = tau Qs u_g
+      // Q = tau P: d/du_g <Qbar, tau P> = 2 tau Qh u_g
 #pragma unroll
-      for (int i = 0; i < 3; ++i) ugb[g][i] = tau_e * Qu[i];
+      for (int i = 0; i < 3; ++i)
+        ugb[g][i] = te2 * fmac(Qh[i][2], ug[2], fmac(Qh[i][1], ug[1], Qh[i][0] * ug[0]));
     }
     if constexpr (SKEW) {
 #pragma unroll
@@ -671,7 +696,7 @@ __device__ __forceinline__ void element_vjp_impl(const R c[3][3], R inv_det, R r
       R acc = (R)kQB * Usum[j];
       if constexpr (TAUE) acc = acc + Sb_tau[j];
 #pragma unroll
-      for (int i = 0; i < 3; ++i) acc = Hm[i][j] * ((w[0][i] + w[1][i]) + (w[2][i] + w[3][i])) + acc;
+      for (int i = 0; i < 3; ++i) acc = fmac(Hm[i][j], (w[0][i] + w[1][i]) + (w[2][i] + w[3][i]), acc);
       Sb[j] = acc;
     }
     R zsum[3] = {(R)0, (R)0, (R)0};
@@ -679,32 +704,32 @@ __device__ __forceinline__ void element_vjp_impl(const R c[3][3], R inv_det, R r
     for (int k = 0; k < 3; ++k) {
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
-        R z = Gb[i][0] * c[k][0] + Gb[i][1] * c[k][1] + Gb[i][2] * c[k][2];
+        const R z = fmac(Gb[i][2], c[k][2], fmac(Gb[i][1], c[k][1], Gb[i][0] * c[k][0]));
         zsum[i] += z;
-        R acc = (R)(kQA - kQB) * ugb[k + 1][i] + (z + Sb[i]);
-        acc = Hm[0][i] * w[k + 1][0] + acc;
-        acc = Hm[1][i] * w[k + 1][1] + acc;
-        gu[k + 1][i] = Hm[2][i] * w[k + 1][2] + acc;
+        R acc = fmac((R)(kQA - kQB), ugb[k + 1][i], z + Sb[i]);
+        acc = fmac(Hm[0][i], w[k + 1][0], acc);
+        acc = fmac(Hm[1][i], w[k + 1][1], acc);
+        gu[k + 1][i] = fmac(Hm[2][i], w[k + 1][2], acc);
       }
     }
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      R acc = (R)(kQA - kQB) * ugb[0][i] + (Sb[i] - zsum[i]);
-      acc = Hm[0][i] * w[0][0] + acc;
-      acc = Hm[1][i] * w[0][1] + acc;
-      gu[0][i] = Hm[2][i] * w[0][2] + acc;
+      R acc = fmac((R)(kQA - kQB), ugb[0][i], Sb[i] - zsum[i]);
+      acc = fmac(Hm[0][i], w[0][0], acc);
+      acc = fmac(Hm[1][i], w[0][1], acc);
+      gu[0][i] = fmac(Hm[2][i], w[0][2], acc);
     }
   }
   // gph = sum_a p_a c_a, p_bar = sum_a p_a / 4
   R gsum = (R)0;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    R acc = gpb[0] * c[k][0] + pq;
-    acc = gpb[1] * c[k][1] + acc;
-    gpo[k + 1] = gpb[2] * c[k][2] + acc;
+    R acc = fmac(gpb[0], c[k][0], pq);
+    acc = fmac(gpb[1], c[k][1], acc);
+    gpo[k + 1] = fmac(gpb[2], c[k][2], acc);
     gsum += gpo[k + 1];
   }
-  gpo[0] = (R)4 * pq - gsum;
+  gpo[0] = fmac((R)4, pq, -gsum);
 }
 
 template <class R, int FLAGS>
