@@ -141,6 +141,17 @@ def cpu_oracle_rates(w, procs: int, n_fwd: int, n_vjp: int, repeats: int = 1):
     return fwd_rate, vjp_rate, step_rate, sample, walls
 
 
+def cpu_oracle_serial(w, n_fwd: int, n_vjp: int):
+    """The same oracle on one core (this process): forward and adjoint tets/s
+    over the first n_fwd / n_vjp elements of the mesh."""
+    global _W
+    _W = w
+    tf = _oracle_slice((0, min(n_fwd, w.n_elems), "fwd", 0))
+    tv = _oracle_slice((0, min(n_vjp, w.n_elems), "vjp", mg.SEED_COT))
+    return {"cores": 1, "fwd_tets_per_s": min(n_fwd, w.n_elems) / tf,
+            "vjp_tets_per_s": min(n_vjp, w.n_elems) / tv}
+
+
 def host_cores() -> int:
     try:
         return len(os.sched_getaffinity(0))
@@ -254,7 +265,8 @@ def run_ours(args):
         procs = host_cores()
         fwd, vjp, step, sample, _ = cpu_oracle_rates(w, procs, args.sample_fwd, args.sample_vjp)
         cpu = {"value": step, "unit": UNIT, "cores": procs, "kind": "oracle", "sample": sample,
-               "fwd_tets_per_s": fwd, "vjp_tets_per_s": vjp}
+               "fwd_tets_per_s": fwd, "vjp_tets_per_s": vjp,
+               "serial": cpu_oracle_serial(w, args.sample_fwd, args.sample_vjp)}
 
     import torch
     import paper_2403_08777_gb300 as ns
