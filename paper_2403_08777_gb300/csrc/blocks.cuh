@@ -231,6 +231,93 @@ struct NodeSum<float> {
   __device__ __forceinline__ double value() const { return widen_f32(s) + widen_f32(c); }
 };
 
+// Two floats in one 64-bit register (low word first), added or subtracted
+// lane by lane in one instruction (the two-wide FP32 operations of sm_100
+// and later).
+__device__ __forceinline__ unsigned long long f32x2_add(unsigned long long a,
+                                                        unsigned long long b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ unsigned long long f32x2_sub(unsigned long long a,
+                                                        unsigned long long b) {
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ unsigned long long f32x2_pack(float lo, float hi) {
+  return ((unsigned long long)__float_as_uint(hi) << 32) | (unsigned long long)__float_as_uint(lo);
+}
+__device__ __forceinline__ float f32x2_lo(unsigned long long x) { return __uint_as_float((unsigned)x); }
+__device__ __forceinline__ float f32x2_hi(unsigned long long x) {
+  return __uint_as_float((unsigned)(x >> 32));
+}
+
+// NodeSum<float> on two components at once: lane by lane the same operations
+// in the same order, so the same result.
+struct NodeSumF32x2 {
+  unsigned long long s = 0ull, c = 0ull;
+  __device__ __forceinline__ void add(unsigned long long x) {
+    const unsigned long long t = f32x2_add(s, x);
+    const unsigned long long bp = f32x2_sub(t, s);
+    c = f32x2_add(c, f32x2_add(f32x2_sub(s, f32x2_sub(t, bp)), f32x2_sub(x, bp)));
+    s = t;
+  }
+  __device__ __forceinline__ double lo() const {
+    return widen_f32(f32x2_lo(s)) + widen_f32(f32x2_lo(c));
+  }
+  __device__ __forceinline__ double hi() const {
+    return widen_f32(f32x2_hi(s)) + widen_f32(f32x2_hi(c));
+  }
+};
+
+// The element entries by sorted position in shared memory: double, four
+// component rows [4][kBlockSlots]; float, two rows of component pairs
+// [2][kBlockSlots] (components 0-1, 2-3) so that one 64-bit access and one
+// two-wide addition serve two components.
+template <class R>
+struct Entries;
+template <>
+struct Entries<double> {
+  static __device__ __forceinline__ void put(void* base, int pos, const double f[4]) {
+    double* e = static_cast<double*>(base);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) e[k * kBlockSlots + pos] = f[k];
+  }
+  // sums of positions [r0, r1), in order
+  static __device__ __forceinline__ void sum(const void* base, int r0, int r1, double out[4]) {
+    const double* e = static_cast<const double*>(base);
+    NodeSum<double> acc[4];
+    for (int q = r0; q < r1; ++q) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) acc[k].add(e[k * kBlockSlots + q]);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) out[k] = acc[k].value();
+  }
+};
+template <>
+struct Entries<float> {
+  static __device__ __forceinline__ void put(void* base, int pos, const float f[4]) {
+    unsigned long long* e = static_cast<unsigned long long*>(base);
+    e[pos] = f32x2_pack(f[0], f[1]);
+    e[kBlockSlots + pos] = f32x2_pack(f[2], f[3]);
+  }
+  static __device__ __forceinline__ void sum(const void* base, int r0, int r1, double out[4]) {
+    const unsigned long long* e = static_cast<const unsigned long long*>(base);
+    NodeSumF32x2 a01, a23;
+    for (int q = r0; q < r1; ++q) {
+      a01.add(e[q]);
+      a23.add(e[kBlockSlots + q]);
+    }
+    out[0] = a01.lo();
+    out[1] = a01.hi();
+    out[2] = a23.lo();
+    out[3] = a23.hi();
+  }
+};
+
 // Shared memory of the forward block kernel (below), and the resident CTAs
 // per SM the compiler must allow (register cap): the float kernel is
 // latency-bound between its barrier-separated phases, so more CTAs per SM
@@ -352,12 +439,8 @@ __global__ void __launch_bounds__(kBlockElems, block_kernel_min_ctas<R>())
       R F[4][4];
       element_rhs<R, FLAGS>(c, inv_det, rh, u, p, P, F);
 #pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        // reloaded (a cache hit) rather than held in registers through the arithmetic
-        const int pos = (int)(__ldg(lmap + a * E + e) & 0xffffu);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) sF[k * kBlockSlots + pos] = F[a][k];
-      }
+      for (int a = 0; a < 4; ++a)
+        Entries<R>::put(sF, (int)(__ldg(lmap + a * E + e) & 0xffffu), F[a]);
     }
     __syncthreads();
     if constexpr (COLOUR) {
@@ -369,18 +452,14 @@ __global__ void __launch_bounds__(kBlockElems, block_kernel_min_ctas<R>())
     for (int j = tid; j < nb; j += kBlockElems) {
       const int r0 = __ldg(runs + off + b + j), r1 = __ldg(runs + off + b + j + 1);
       const int64_t v = __ldg(nodes + off + j);
-      NodeSum<R> acc[4];
-      for (int q = r0; q < r1; ++q) {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) acc[k].add(sF[k * kBlockSlots + q]);
-      }
+      double acc[4];
+      Entries<R>::sum(sF, r0, r1, acc);
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         if constexpr (COLOUR)
-          rhs[k * N + v] = (j == tid ? sold[k * kBlockElems + tid] : rhs[k * N + v]) +
-                           acc[k].value();
+          rhs[k * N + v] = (j == tid ? sold[k * kBlockElems + tid] : rhs[k * N + v]) + acc[k];
         else
-          atomicAdd(rhs + k * N + v, acc[k].value());
+          atomicAdd(rhs + k * N + v, acc[k]);
       }
     }
   }
@@ -497,28 +576,22 @@ __global__ void __launch_bounds__(kBlockElems, block_vjp_min_ctas<R>())
     if (e < E) {
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
-        const int pos = (int)(__ldg(lmap + a * E + e) & 0xffffu);
-#pragma unroll
-        for (int k = 0; k < 3; ++k) su[k * kBlockSlots + pos] = gu[a][k];
-        su[3 * kBlockSlots + pos] = gp[a];
+        const R g4[4] = {gu[a][0], gu[a][1], gu[a][2], gp[a]};
+        Entries<R>::put(su, (int)(__ldg(lmap + a * E + e) & 0xffffu), g4);
       }
     }
     __syncthreads();
     for (int j = tid; j < nb; j += kBlockElems) {
       const int r0 = __ldg(runs + off + b + j), r1 = __ldg(runs + off + b + j + 1);
       const int64_t v = __ldg(nodes + off + j);
-      NodeSum<R> acc[4];
-      for (int q = r0; q < r1; ++q) {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) acc[k].add(su[k * kBlockSlots + q]);
-      }
+      double acc[4];
+      Entries<R>::sum(su, r0, r1, acc);
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         if constexpr (COLOUR)
-          grad[k * N + v] = (j == tid ? sold[k * kBlockElems + tid] : grad[k * N + v]) +
-                            acc[k].value();
+          grad[k * N + v] = (j == tid ? sold[k * kBlockElems + tid] : grad[k * N + v]) + acc[k];
         else
-          atomicAdd(grad + k * N + v, acc[k].value());
+          atomicAdd(grad + k * N + v, acc[k]);
       }
     }
     __syncthreads();  // the sums have read su before it is staged into again
