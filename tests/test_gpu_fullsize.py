@@ -64,3 +64,31 @@ def test_fullsize_mixed_precision(dev):
     err = np.linalg.norm(x - ref) / np.linalg.norm(ref)
     assert err <= 1e-5, err
     m.close()
+
+
+def test_fullsize_one_pass_mixed_adjoint_and_colourings(dev):
+    """The one-pass call, the mixed adjoint (block scatter) and the coloured
+    scatters at full size, as the benchmark's forms run them."""
+    w = mg.paper_scale(n=256, order="rcm")
+    nodes, sub = sampled(w, 13)
+    idx = torch.from_numpy(nodes).to(dev)
+    m = ns.Mesh(torch.from_numpy(w.coords).to(dev), torch.from_numpy(w.conn).to(dev), colour=True)
+    up = torch.from_numpy(w.up).to(dev)
+    cot_h = mg.normal((4, w.n_nodes), seed=mg.SEED_COT)
+    cot = torch.from_numpy(cot_h).to(dev)
+    ref = oracle.assemble(w.coords, sub, w.up, w.rho, w.mu)[:, nodes]
+    gref = oracle.vjp(w.coords, sub, w.up, cot_h, w.rho, w.mu)[:, nodes]
+
+    def err(x, r):
+        return np.linalg.norm(x[:, idx].cpu().numpy() - r) / np.linalg.norm(r)
+
+    r, g = m.assemble_rhs_vjp(up, cot, ns.Params(rho=w.rho, mu=w.mu))
+    assert err(r, ref) <= 1e-12 and err(g, gref) <= 1e-12
+    pm = ns.Params(rho=w.rho, mu=w.mu, precision="mixed")
+    assert err(m.assemble_vjp(up.float(), cot.float(), pm), gref) <= 1e-6
+    assert err(m.assemble(up, ns.Params(rho=w.rho, mu=w.mu, scatter="colour")), ref) <= 1e-12
+    assert err(m.assemble_vjp(up, cot, ns.Params(rho=w.rho, mu=w.mu, scatter="colour")),
+               gref) <= 1e-12
+    pbc = ns.Params(rho=w.rho, mu=w.mu, precision="mixed", scatter="block_colour")
+    assert err(m.assemble(up.float(), pbc), ref) <= 1e-5
+    m.close()
