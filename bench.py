@@ -460,6 +460,7 @@ def run_ours(args):
     rk_ms = sa.elapsed_time(sb) / n_rk
     forms["explicit_step_ssprk3"] = {"ms": rk_ms, "assemblies_per_step": 3,
                                      "overhead_vs_3_assemblies": rk_ms / (3 * fwd_med)}
+    forms["explicit_step_small_graph"] = time_step_graph(16, dev, stream)
     del u_step, work
     forms["scatter_sweep"] = time_scatter_sweep(mesh, w, up, cot, dev, stream, args, fwd_med,
                                                 vjp_med)
@@ -573,6 +574,42 @@ def _timed(fn, dev, stream, args):
     b.record(stream)
     torch.cuda.synchronize(dev)
     return a.elapsed_time(b) / args.steps
+
+
+def time_step_graph(n, dev, stream, steps=50):
+    """SSP-RK3 steps on a small n^3-hex mesh, launched one call at a time and
+    replayed from one CUDA graph holding the same steps: microseconds per
+    step."""
+    import torch
+    import paper_2403_08777_gb300 as ns
+    w = mg.make_workload(n, order="rcm", mu=1e-3, mag_max=2.0)
+    m = ns.Mesh(torch.from_numpy(w.coords).to(dev), torch.from_numpy(w.conn).to(dev))
+    up = torch.from_numpy(w.up).to(dev)
+    p = ns.Params(rho=w.rho, mu=w.mu)
+    dt = 0.1 / n / float(np.abs(w.up[:3]).max())
+    work = torch.empty((8, w.n_nodes), dtype=torch.float64, device=dev)
+    u1 = up.clone()
+    for _ in range(3):
+        m.explicit_step(u1, dt, "ssprk3", p, work=work)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        m.explicit_step(u1, dt, "ssprk3", p, work=work)
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    direct = a.elapsed_time(b) * 1e3 / steps
+    u2 = up.clone()
+    g = ns.StepGraph(m, u2, dt, "ssprk3", p, steps=steps)
+    g.replay()
+    torch.cuda.synchronize(dev)
+    a.record(stream)
+    g.replay()
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    graphed = a.elapsed_time(b) * 1e3 / steps
+    m.close()
+    return {"workload": w.name, "n_tets": w.n_elems, "us_per_step_direct": direct,
+            "us_per_step_graph": graphed, "speedup": direct / graphed}
 
 
 def time_scatter_sweep(mesh, w, up, cot, dev, stream, args, fwd_ms, vjp_ms):

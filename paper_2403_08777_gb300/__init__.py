@@ -20,7 +20,7 @@ import torch
 from . import _abi
 from ._abi import NSRHSError, NativeLibraryMissing  # noqa: F401
 
-__all__ = ["Mesh", "Params", "assemble", "assemble_host", "StepPipeline", "NSRHSFunction",
+__all__ = ["Mesh", "Params", "assemble", "assemble_host", "StepPipeline", "StepGraph", "NSRHSFunction",
            "NSRHSError", "NativeLibraryMissing", "load_library"]
 
 _PREC = {"fp64": _abi.FP64, "mixed": _abi.MIXED}
@@ -295,6 +295,46 @@ def assemble_host(mesh: Mesh, up_host: torch.Tensor, params: Params | None = Non
     out_host.copy_(rhs, non_blocking=True)
     torch.cuda.current_stream(mesh.device).synchronize()
     return out_host
+
+
+class StepGraph:
+    """`steps` explicit time steps of up (in place) captured once in a CUDA
+    graph and replayed with one launch: for small meshes, where the steps'
+    kernel launches (each Runge-Kutta stage is a memset, an assembly and an
+    update) cost more than their work. The library calls allocate nothing and
+    never synchronise, so they can be captured; the graph is bound to the
+    addresses of `up` and of its own work buffer.
+
+        g = StepGraph(mesh, up, dt, "ssprk3", params, steps=10)
+        g.replay()            # ten steps, on the current stream
+    """
+
+    def __init__(self, mesh: Mesh, up: torch.Tensor, dt: float, scheme: str = "ssprk3",
+                 params: Params | None = None, *, steps: int = 1, **kw):
+        if steps < 1:
+            raise ValueError("steps must be >= 1")
+        p = mesh._params(params, kw)
+        _require(up, "up", torch.float64, (4, mesh.n_nodes), mesh.device)
+        self.mesh, self.up, self.steps = mesh, up, steps
+        self.work = torch.empty((8, mesh.n_nodes), dtype=torch.float64, device=mesh.device)
+        side = torch.cuda.Stream(mesh.device)
+        side.wait_stream(torch.cuda.current_stream(mesh.device))
+        with torch.cuda.stream(side):
+            # one eager step first (first launches of a kernel may initialise
+            # lazily, which capture does not allow), then restore up
+            saved = up.clone()
+            mesh.explicit_step(up, dt, scheme, p, work=self.work)
+            up.copy_(saved)
+        torch.cuda.current_stream(mesh.device).wait_stream(side)
+        del saved
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.device(mesh.device), torch.cuda.graph(self.graph):
+            for _ in range(steps):
+                mesh.explicit_step(up, dt, scheme, p, work=self.work)
+
+    def replay(self) -> torch.Tensor:
+        self.graph.replay()
+        return self.up
 
 
 class StepPipeline:

@@ -429,3 +429,31 @@ def test_one_pass_argument_errors(dev):
         m.assemble_rhs_vjp(up, up, ns.Params(scatter="block"))
     assert ei.value.status == _abi.EUNSUPPORTED
     m.close()
+
+
+@pytest.mark.parametrize("scatter", ["auto", "colour"])
+def test_step_graph_replays_the_direct_steps(dev, scatter):
+    """Explicit steps captured in a CUDA graph give the direct calls' result
+    (bitwise with the deterministic colour scatter)."""
+    w = mg.make_workload(6, jitter=0.2, order="rcm", mu=1e-3, mag_max=2.0)
+    coords, conn, up = on_dev(dev, w.coords, w.conn, w.up)
+    m = ns.Mesh(coords, conn, colour=scatter == "colour")
+    p = ns.Params(rho=w.rho, mu=w.mu, scatter=scatter)
+    direct = up.clone()
+    for _ in range(3):
+        m.explicit_step(direct, 2e-3, "ssprk3", p)
+    graphed = up.clone()
+    g = ns.StepGraph(m, graphed, 2e-3, "ssprk3", p, steps=3)
+    assert torch.equal(graphed, up)          # capture does not advance the state
+    g.replay()
+    if scatter == "colour":
+        assert torch.equal(graphed, direct)
+    else:
+        d = (graphed - up).cpu().numpy()
+        ref = (direct - up).cpu().numpy()
+        assert relerr(d, ref) <= 1e-13
+    g.replay()                               # three more steps
+    for _ in range(3):
+        m.explicit_step(direct, 2e-3, "ssprk3", p)
+    assert relerr((graphed - up).cpu().numpy(), (direct - up).cpu().numpy()) <= 1e-13
+    m.close()
