@@ -264,11 +264,13 @@ struct NodeSumF32x2 {
     c = f32x2_add(c, f32x2_add(f32x2_sub(s, f32x2_sub(t, bp)), f32x2_sub(x, bp)));
     s = t;
   }
+  // one per node and component: the hardware conversion (exact) is cheaper
+  // here than the integer widening used per entry elsewhere
   __device__ __forceinline__ double lo() const {
-    return widen_f32(f32x2_lo(s)) + widen_f32(f32x2_lo(c));
+    return (double)f32x2_lo(s) + (double)f32x2_lo(c);
   }
   __device__ __forceinline__ double hi() const {
-    return widen_f32(f32x2_hi(s)) + widen_f32(f32x2_hi(c));
+    return (double)f32x2_hi(s) + (double)f32x2_hi(c);
   }
 };
 
