@@ -232,9 +232,12 @@ nsrhs_status nsrhs_lumped_mass(const nsrhs_mesh* m, double* mass_dev, void* stre
 /*
  * One explicit step of length dt > 0 with L(u) = F(u, p) / (rho m), on
  * up_dev [4][n_nodes] double in place (rows u, v, w advanced, row p kept).
- * work_dev: caller-owned device scratch of 8 * n_nodes doubles (no
- * allocation inside). Requires precision NSRHS_FP64 and rho > 0. Each
- * Runge-Kutta stage runs one nsrhs_assemble on the stream.
+ * work_dev: caller-owned device scratch (no allocation inside) of
+ * 8 * n_nodes doubles for NSRHS_FP64, 10 * n_nodes for NSRHS_MIXED (which
+ * assembles each stage's RHS from a float copy of the double state, with
+ * float element arithmetic and double accumulation; the state and its
+ * update stay double). Requires rho > 0. Each Runge-Kutta stage runs one
+ * nsrhs_assemble on the stream.
  */
 nsrhs_status nsrhs_explicit_step(const nsrhs_mesh* m, const nsrhs_params* p, double dt,
                                  int32_t scheme, double* up_dev, double* work_dev, void* stream);

@@ -227,12 +227,15 @@ class Mesh:
     def explicit_step(self, up: torch.Tensor, dt: float, scheme: str = "ssprk3",
                       params: Params | None = None, *, work: torch.Tensor | None = None, **kw):
         """Advance the velocity rows of up [4, N] (float64, in place) by one
-        explicit step of rho m du/dt = F (pressure row kept); returns up."""
+        explicit step of rho m du/dt = F (pressure row kept); returns up.
+        precision='mixed' assembles the stage RHS in the mixed form (the
+        state stays float64); work is [8, N] (fp64) or [10, N] (mixed)."""
         p = self._params(params, kw)
         _require(up, "up", torch.float64, (4, self.n_nodes), self.device)
+        rows = 10 if p.precision == "mixed" else 8
         if work is None:
-            work = torch.empty((8, self.n_nodes), dtype=torch.float64, device=self.device)
-        _require(work, "work", torch.float64, (8, self.n_nodes), self.device)
+            work = torch.empty((rows, self.n_nodes), dtype=torch.float64, device=self.device)
+        _require(work, "work", torch.float64, (rows, self.n_nodes), self.device)
         sch = {"euler": _abi.EULER, "ssprk3": _abi.SSPRK3}[scheme]
         cp = p.to_c()
         with torch.cuda.device(self.device):
@@ -257,12 +260,11 @@ class Mesh:
 
 class NSRHSFunction(torch.autograd.Function):
     """rhs = A(up) with the hand-written adjoint kernel as backward.
-    Differentiable with respect to up only (mesh and parameters are constants)."""
+    Differentiable with respect to up only (mesh and parameters are constants);
+    fp64 (up float64) or mixed (up float32; rhs float64, gradient float32)."""
 
     @staticmethod
     def forward(ctx, up: torch.Tensor, mesh: Mesh, params: Params):
-        if params.precision != "fp64":
-            raise ValueError("NSRHSFunction differentiates the fp64 form")
         ctx.mesh, ctx.params = mesh, params
         ctx.save_for_backward(up)
         return mesh.assemble(up.detach().contiguous(), params)
@@ -270,12 +272,17 @@ class NSRHSFunction(torch.autograd.Function):
     @staticmethod
     def backward(ctx, grad_rhs: torch.Tensor):
         (up,) = ctx.saved_tensors
-        g = ctx.mesh.assemble_vjp(up.detach().contiguous(), grad_rhs.contiguous(), ctx.params)
-        return g, None, None
+        cot = grad_rhs.contiguous()
+        if ctx.params.precision == "mixed":
+            # float cotangent into the float reverse sweep; the gradient is
+            # accumulated in double and returned in up's dtype (float32)
+            cot = cot.float()
+        g = ctx.mesh.assemble_vjp(up.detach().contiguous(), cot, ctx.params)
+        return g.to(up.dtype), None, None
 
 
 def assemble(mesh: Mesh, up: torch.Tensor, params: Params | None = None, **kw) -> torch.Tensor:
-    """Differentiable RHS assembly (fp64)."""
+    """Differentiable RHS assembly (fp64, or mixed with float32 up)."""
     p = mesh._params(params, kw)
     return NSRHSFunction.apply(up, mesh, p)
 
@@ -316,7 +323,8 @@ class StepGraph:
         p = mesh._params(params, kw)
         _require(up, "up", torch.float64, (4, mesh.n_nodes), mesh.device)
         self.mesh, self.up, self.steps = mesh, up, steps
-        self.work = torch.empty((8, mesh.n_nodes), dtype=torch.float64, device=mesh.device)
+        rows = 10 if p.precision == "mixed" else 8
+        self.work = torch.empty((rows, mesh.n_nodes), dtype=torch.float64, device=mesh.device)
         side = torch.cuda.Stream(mesh.device)
         side.wait_stream(torch.cuda.current_stream(mesh.device))
         with torch.cuda.stream(side):

@@ -407,6 +407,14 @@ __global__ void rk_combine_kernel(int64_t N, double a0, double a1, double dt_rho
   }
 }
 
+// out = (float) in, [4][N] (the mixed form's explicit step assembles from a
+// float copy of the double state).
+__global__ void narrow_kernel(int64_t n, const double* __restrict__ in, float* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = __double2float_rn(in[i]);
+}
+
 // ---------------------------------------------------------------------------
 // Assembly kernels.
 
@@ -1559,16 +1567,24 @@ nsrhs_status nsrhs_explicit_step(const nsrhs_mesh* m, const nsrhs_params* p, dou
   if (st != NSRHS_OK) return st;
   if (!(dt > 0.0) || !std::isfinite(dt) || !(p->rho > 0.0)) return NSRHS_EINVAL;
   if (scheme != NSRHS_EULER && scheme != NSRHS_SSPRK3) return NSRHS_EINVAL;
-  if (p->precision != NSRHS_FP64) return NSRHS_EUNSUPPORTED;
   cudaStream_t s = (cudaStream_t)stream;
   DeviceGuard dg(m->device);
   if (!dg.ok) return NSRHS_ECUDA;
   const int64_t N = m->n_nodes;
   double* F = work_dev;              // [4][N] stage RHS
   double* stage = work_dev + 4 * N;  // [4][N] stage state
+  float* narrow = reinterpret_cast<float*>(work_dev + 8 * N);  // MIXED: [4][N] float state
   const double dtr = dt / p->rho;
   const unsigned grid = grid_for(N, m->device, 8);
-  auto rhs_of = [&](const double* u) { return nsrhs_assemble(m, p, u, F, stream); };
+  // the stage RHS: FP64 from the double state; MIXED from its float copy
+  // (float element arithmetic, double accumulation), the update in double
+  auto rhs_of = [&](const double* u) {
+    if (p->precision == NSRHS_FP64) return nsrhs_assemble(m, p, u, F, stream);
+    narrow_kernel<<<grid_for(4 * N, m->device, 8), kThreads, 0, s>>>(4 * N, u, narrow);
+    nsrhs_status st2 = cuda_status(cudaGetLastError());
+    if (st2 != NSRHS_OK) return st2;
+    return nsrhs_assemble(m, p, narrow, F, stream);
+  };
   if (scheme == NSRHS_EULER) {
     if ((st = rhs_of(up_dev)) != NSRHS_OK) return st;
     rk_combine_kernel<<<grid, kThreads, 0, s>>>(N, 0.0, 1.0, dtr, up_dev, up_dev, F, m->inv_mass,

@@ -457,3 +457,35 @@ def test_step_graph_replays_the_direct_steps(dev, scatter):
         m.explicit_step(direct, 2e-3, "ssprk3", p)
     assert relerr((graphed - up).cpu().numpy(), (direct - up).cpu().numpy()) <= 1e-13
     m.close()
+
+
+def test_mixed_explicit_steps_and_autograd(dev):
+    """The mixed form inside the explicit step (float stage RHS, double state)
+    and behind autograd (float32 up): both against the FP64 oracle within the
+    mixed form's tolerances."""
+    w = mg.make_workload(10, jitter=0.2, order="rcm", mu=1e-3, mag_max=2.0)
+    coords, conn, up = on_dev(dev, w.coords, w.conn, w.up)
+    m = ns.Mesh(coords, conn)
+    pm = ns.Params(rho=w.rho, mu=w.mu, precision="mixed")
+    for scheme in ("euler", "ssprk3"):
+        u = up.clone()
+        ref = w.up.copy()
+        for _ in range(2):
+            m.explicit_step(u, 2e-3, scheme, pm)
+            ref = oracle.explicit_step(w.coords, w.conn, ref, w.rho, w.mu, 2e-3, scheme)
+        assert u.dtype == torch.float64
+        assert relerr(u.cpu().numpy() - w.up, ref - w.up) <= TOL_MIXED, scheme
+    with pytest.raises(ValueError):   # the mixed step needs 10 rows of work
+        m.explicit_step(up.clone(), 2e-3, "euler", pm,
+                        work=torch.empty((8, w.n_nodes), dtype=torch.float64, device=dev))
+    up32 = up.float().requires_grad_(True)
+    rhs = ns.assemble(m, up32, pm)
+    assert rhs.dtype == torch.float64
+    assert relerr(rhs.detach().cpu().numpy(), oracle.assemble(w.coords, w.conn, w.up, w.rho,
+                                                               w.mu)) <= TOL_MIXED
+    cot = mg.normal((4, w.n_nodes), seed=mg.SEED_COT)
+    (g,) = torch.autograd.grad(rhs, up32, torch.from_numpy(cot).to(dev))
+    assert g.dtype == torch.float32
+    gref = oracle.vjp(w.coords, w.conn, w.up, cot, w.rho, w.mu)
+    assert relerr(g.double().cpu().numpy(), gref) <= TOL_VJP_FD
+    m.close()
