@@ -84,6 +84,8 @@ bool is_live(const nsrhs_mesh* m) {
 
 constexpr int kThreads = 128;
 constexpr int kGeomRows = 11;
+// Block-kernel grids: at most a full SM's worth of threads (2048) per SM.
+constexpr int kBlockCtasPerSm = 2048 / nsrhs::kBlockElems > 0 ? 2048 / nsrhs::kBlockElems : 1;
 
 // Minimum resident CTAs per SM requested from the compiler (register cap) for
 // the FP64 element kernels; measured choices, overridable at build time.
@@ -1255,7 +1257,7 @@ nsrhs_status nsrhs_assemble(const nsrhs_mesh* m, const nsrhs_params* p, const vo
     for (size_t k = 0; k + 1 < m->bcol_off.size() && err == cudaSuccess; ++k) {
       const int64_t i0 = m->bcol_off[k], i1 = m->bcol_off[k + 1];
       const unsigned grid = (unsigned)std::max<int64_t>(
-          1, std::min<int64_t>(i1 - i0, (int64_t)sm_count(m->device) * 8));
+          1, std::min<int64_t>(i1 - i0, (int64_t)sm_count(m->device) * kBlockCtasPerSm));
       if (p->precision == NSRHS_FP64) {
         auto P = elem_params<double>(p);
         const size_t smem = nsrhs::block_kernel_smem<double, true>();
@@ -1313,7 +1315,7 @@ nsrhs_status nsrhs_assemble(const nsrhs_mesh* m, const nsrhs_params* p, const vo
   if (block) {
     const int64_t nb = m->n_blocks;
     const unsigned grid = (unsigned)std::max<int64_t>(
-        1, std::min<int64_t>(nb, (int64_t)sm_count(m->device) * 8));
+        1, std::min<int64_t>(nb, (int64_t)sm_count(m->device) * kBlockCtasPerSm));
     cudaError_t err = cudaSuccess;
     if (p->precision == NSRHS_FP64) {
       auto P = elem_params<double>(p);
@@ -1388,7 +1390,7 @@ nsrhs_status nsrhs_assemble_vjp(const nsrhs_mesh* m, const nsrhs_params* p, cons
     for (size_t k = 0; k + 1 < ranges.size() && err == cudaSuccess; ++k) {
       const int64_t i0 = ranges[k], i1 = ranges[k + 1];
       const unsigned grid = (unsigned)std::max<int64_t>(
-          1, std::min<int64_t>(i1 - i0, (int64_t)sm_count(m->device) * 8));
+          1, std::min<int64_t>(i1 - i0, (int64_t)sm_count(m->device) * kBlockCtasPerSm));
       auto launch = [&](auto kern, size_t smem, const auto* geom, const auto* u, const auto* c,
                         const auto& P) {
         err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
