@@ -2,12 +2,16 @@
 // on linear tetrahedra (arXiv 2403.08777, Sec. II and V), GB300 / sm_103a.
 //
 // Host side: mesh objects (device copies of coordinates and connectivity,
-// validation, aspect-ratio classification), argument checking and kernel
-// launches. Device side: the element kernels (element.cuh holds the
-// per-element arithmetic). One thread assembles one element, with every
+// validation, aspect-ratio classification, Morton element order, cached
+// geometry, element blocks, optional colourings), argument checking and
+// kernel launches. Device side: the element kernels (element.cuh holds the
+// per-element arithmetic, blocks.cuh the block-staged kernels, colour.cuh
+// the colourings). One thread assembles one element, with every
 // intermediate in registers (the paper's specialisation + privatisation,
 // Sec. V-B/V-C), and scatters its 16 entries as soon as they are computed
-// (immediate scatter, Sec. V-D) with double-precision atomic adds, which
+// (immediate scatter, Sec. V-D): by double-precision atomic adds (the FP64
+// default), by per-block sums staged in shared memory (the mixed default),
+// or by plain read-modify-write in coloured launches. Atomics and colouring
 // resolve the write conflicts that the paper's CPU path avoids with a
 // separate serial scatter loop (Sec. V-C).
 
