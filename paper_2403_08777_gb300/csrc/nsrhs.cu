@@ -99,6 +99,14 @@ constexpr int kBlockCtasPerSm = 2048 / nsrhs::kBlockElems > 0 ? 2048 / nsrhs::kB
 #ifndef NSRHS_VJP_MIN_CTAS
 #define NSRHS_VJP_MIN_CTAS 1
 #endif
+// The coloured FP64 kernels hold the read-modify-write scatter's loads in
+// flight; capped so that as many CTAs fit per SM as for the atomic kernels.
+#ifndef NSRHS_FWD_COLOUR_MIN_CTAS
+#define NSRHS_FWD_COLOUR_MIN_CTAS 3
+#endif
+#ifndef NSRHS_VJP_COLOUR_MIN_CTAS
+#define NSRHS_VJP_COLOUR_MIN_CTAS 2
+#endif
 
 int sm_count(int device) {
   int n = 0;
@@ -500,7 +508,7 @@ __global__ void __launch_bounds__(kThreads, NSRHS_FWD_MIN_CTAS)
 // FP64 forward over the elements [e0, e1) of one colour of the colour-major
 // copy (row stride E), plain read-modify-write scatter.
 template <int FLAGS>
-__global__ void __launch_bounds__(kThreads, NSRHS_FWD_MIN_CTAS)
+__global__ void __launch_bounds__(kThreads, NSRHS_FWD_COLOUR_MIN_CTAS)
     fwd_fp64_colour_kernel(int64_t N, int64_t E, int64_t e0, int64_t e1,
                            const int32_t* __restrict__ conn, const double* __restrict__ geom,
                            const double* __restrict__ up, ElemParams<double> P,
@@ -640,7 +648,7 @@ __global__ void __launch_bounds__(kThreads, NSRHS_VJP_MIN_CTAS)
 }
 
 template <int FLAGS>
-__global__ void __launch_bounds__(kThreads, NSRHS_VJP_MIN_CTAS)
+__global__ void __launch_bounds__(kThreads, NSRHS_VJP_COLOUR_MIN_CTAS)
     vjp_fp64_colour_kernel(int64_t N, int64_t E, int64_t e0, int64_t e1,
                            const int32_t* __restrict__ conn, const double* __restrict__ geom,
                            const double* __restrict__ up, const double* __restrict__ cot,
