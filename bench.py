@@ -50,7 +50,7 @@ FLOPS_PER_TET_VREMAN = {"fwd": 571, "vjp": 1236, "rhs_vjp": 1531}
 # ncu capture of each kernel on the 128^3-hex RCM mesh, scaled to a launch by
 # the element count (traffic grows in proportion). None once a kernel has
 # changed since its counters were taken.
-DRAM_BYTES_PER_TET = {"fwd_fp64": 157.5, "vjp_fp64": 187.1}
+DRAM_BYTES_PER_TET = {"fwd_fp64": 158.3, "vjp_fp64": 187.9}
 
 # FP64 FMA lanes per SM per clock on GB300 (1.25 TF/s nominal at 2.07 GHz).
 FP64_LANES_PER_SM = 2
