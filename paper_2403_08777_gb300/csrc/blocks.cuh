@@ -8,13 +8,15 @@
 // node, its distinct-node index and the position of its contribution in that
 // sorted order (lmap = index << 16 | position).
 //
-// Assembly (per call): one CTA per block loads the nodal values of its
-// distinct nodes once into shared memory, each thread computes one element
-// from shared memory, writes its 16 entries to shared memory at their sorted
-// positions, and each distinct node's entries (a contiguous run) are summed
-// in a fixed order and added to the global RHS with one atomic per component. The
-// global atomics drop from 16 per element to 4 per (block, distinct node), and
-// the sums inside a block do not depend on scheduling.
+// Assembly (per call): each CTA walks its blocks; for a block it loads the
+// nodal values of the distinct nodes once into shared memory (as cp.async
+// copies issued one block ahead, double-buffered), each thread computes one
+// element from shared memory and writes its 16 entries to shared memory at
+// their sorted positions, and each distinct node's entries (a contiguous run)
+// are summed in a fixed order and added to the global RHS with one atomic per
+// component (or, for coloured blocks, a plain read-modify-write). The global
+// atomics drop from 16 per element to 4 per (block, distinct node), and the
+// sums inside a block do not depend on scheduling.
 #pragma once
 
 #include <cstdint>
