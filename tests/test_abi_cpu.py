@@ -73,6 +73,16 @@ def test_argument_errors_without_gpu(lib):
     info = _abi.MeshInfo()
     assert lib.nsrhs_mesh_get_info(fake, ctypes.byref(info)) == _abi.EINVAL
     assert lib.nsrhs_mesh_element_colours(fake, 0, fake, None) == _abi.EINVAL
+    assert lib.nsrhs_assemble_rhs_vjp(fake, ctypes.byref(p), fake, fake, fake, fake,
+                                      None) == _abi.EINVAL
+    assert lib.nsrhs_assemble_elmat(fake, ctypes.byref(p), fake, fake, None) == _abi.EINVAL
+    assert lib.nsrhs_lumped_mass(fake, fake, None) == _abi.EINVAL
+    assert lib.nsrhs_explicit_step(fake, ctypes.byref(p), 1e-3, 0, fake, fake, None) == _abi.EINVAL
+    # the no-alloc check validates its arguments before touching the device
+    res = P(0x2000)
+    assert lib.nsrhs_mesh_check_noalloc(0, 10, fake, fake, 10.0, None, res) == _abi.EINVAL
+    assert lib.nsrhs_mesh_check_noalloc(10, 10, fake, fake, -1.0, None, res) == _abi.EINVAL
+    assert lib.nsrhs_mesh_check_noalloc(10, 10, None, fake, 10.0, None, res) == _abi.EINVAL
     lib.nsrhs_destroy(None)
     lib.nsrhs_destroy(fake)
 
