@@ -60,10 +60,12 @@ typedef enum {
 
 typedef enum {
   NSRHS_FP64 = 0, /* double precision throughout */
-  NSRHS_MIXED = 1 /* float nodal (u,p) and float element arithmetic; double
-                     coordinate differences, double det/inverse on elements
-                     whose aspect ratio exceeds the mesh's threshold, double
-                     global accumulation */
+  NSRHS_MIXED = 1 /* float nodal (u,p) and float element arithmetic (with
+                     the hardware's approximate reciprocal and square roots);
+                     the element geometry (det and inverse) computed in double
+                     once per mesh for every element, so also for those whose
+                     aspect ratio exceeds the mesh's threshold, then rounded;
+                     double global accumulation */
 } nsrhs_precision;
 
 typedef enum {
@@ -120,9 +122,9 @@ typedef struct {
                           copy of the connectivity and geometry (about 150
                           bytes per element more) for NSRHS_SCATTER_COLOUR,
                           and colour the element blocks for
-                          NSRHS_SCATTER_BLOCK_COLOUR; 0 (default): not. Greedy colouring, at most 128
-                          colours, else mesh creation returns
-                          NSRHS_EUNSUPPORTED. */
+                          NSRHS_SCATTER_BLOCK_COLOUR; 0 (default): not.
+                          Greedy colouring, at most 128 colours, else mesh
+                          creation returns NSRHS_EUNSUPPORTED. */
   int32_t reserved;    /* must be 0 */
 } nsrhs_mesh_opts;
 
@@ -149,10 +151,11 @@ void nsrhs_mesh_opts_default(nsrhs_mesh_opts* o);
  * Create a mesh from device arrays coords [3][n_nodes] and conn [4][n_elems].
  * The library copies both (the caller may free them afterwards), checks on
  * the device that every index is in range and every element has detJ > 0,
- * classifies elements by aspect ratio, and builds the element blocks of the
- * BLOCK scatter (and, with opts->colour, the colouring of the COLOUR
- * scatter). opts may be NULL (defaults). Synchronises `stream` (with
- * colouring, once per colouring round).
+ * classifies elements by aspect ratio, orders them along a Morton curve of
+ * their centroids, caches their geometry, and builds the element blocks of
+ * the BLOCK scatter (and, with opts->colour, the colourings of the COLOUR
+ * and BLOCK_COLOUR scatters). opts may be NULL (defaults). Synchronises
+ * `stream` (with colouring, once per colouring round).
  * 1 <= n_nodes < 2^31, 1 <= n_elems < 2^31.
  * On error *out is set to NULL and nothing is leaked.
  */
@@ -168,8 +171,8 @@ nsrhs_status nsrhs_mesh_get_info(const nsrhs_mesh* m, nsrhs_mesh_info* info);
  * NSRHS_MIXED; rhs [4][n_nodes] double is overwritten (zeroed, then summed
  * into). up and rhs must not overlap. The summation order of the atomic
  * adds is unspecified, so results agree with a serial sum to rounding only;
- * with NSRHS_SCATTER_COLOUR the order is fixed and repeated calls give
- * bitwise identical results.
+ * with NSRHS_SCATTER_COLOUR and NSRHS_SCATTER_BLOCK_COLOUR the order is
+ * fixed and repeated calls give bitwise identical results.
  */
 nsrhs_status nsrhs_assemble(const nsrhs_mesh* m, const nsrhs_params* p, const void* up,
                             double* rhs, void* stream);
@@ -180,7 +183,9 @@ nsrhs_status nsrhs_assemble(const nsrhs_mesh* m, const nsrhs_params* p, const vo
  * pressure (the mesh and parameters are constants). NSRHS_FP64: up and cot
  * [4][n_nodes] double. NSRHS_MIXED: up and cot [4][n_nodes] float, float
  * reverse sweep, double accumulation. grad [4][n_nodes] double is
- * overwritten. The element quantities are recomputed, not stored.
+ * overwritten. The element quantities are recomputed, not stored. Where a
+ * Gauss-point velocity is exactly zero, |u_g| contributes the symmetric
+ * derivative 0. Scatter modes as for nsrhs_assemble.
  */
 nsrhs_status nsrhs_assemble_vjp(const nsrhs_mesh* m, const nsrhs_params* p, const void* up,
                                 const void* cot, double* grad, void* stream);
