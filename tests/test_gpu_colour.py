@@ -221,3 +221,35 @@ def test_colour_scatter_needs_a_coloured_mesh(dev):
         m.element_colours()
     assert ei.value.status == _abi.EUNSUPPORTED
     m.close()
+
+
+def fan_mesh(k):
+    """k tetrahedra sharing only node 0 (the origin); tet j spans the scaled
+    unit axes: every element needs its own colour."""
+    coords = [(0.0, 0.0, 0.0)]
+    conn = []
+    for j in range(k):
+        s = 1.0 + j
+        base = len(coords)
+        coords += [(s, 0.0, 0.0), (0.0, s, 0.0), (0.0, 0.0, s)]
+        conn.append((0, base, base + 1, base + 2))
+    return (np.ascontiguousarray(np.array(coords).T),
+            np.ascontiguousarray(np.array(conn, dtype=np.int32).T))
+
+
+def test_colouring_limit(dev):
+    """128 elements around one node take the 128 colours there are; 129
+    cannot be coloured and mesh creation reports it."""
+    coords, conn = fan_mesh(128)
+    c_d, n_d = on_dev(dev, coords, conn)
+    m = ns.Mesh(c_d, n_d, colour=True)
+    assert m.info()["n_colours"] == 128
+    cols = m.element_colours().cpu().numpy()
+    assert np.array_equal(np.sort(cols), np.arange(128))
+    m.close()
+    coords, conn = fan_mesh(129)
+    c_d, n_d = on_dev(dev, coords, conn)
+    with pytest.raises(ns.NSRHSError) as ei:
+        ns.Mesh(c_d, n_d, colour=True)
+    assert ei.value.status == _abi.EUNSUPPORTED
+    ns.Mesh(c_d, n_d).close()   # without colouring the mesh is fine

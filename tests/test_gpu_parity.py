@@ -261,6 +261,15 @@ def test_step_pipeline_matches_direct_calls(dev):
         g = m.assemble_vjp(ad, cot_d, p).cpu().numpy()
         assert relerr(rhs_h[k].numpy(), r) <= 1e-14
         assert relerr(grad_h[k].numpy(), g) <= 1e-14
+    # forward only (no cotangent), and the single-call host helper
+    pipe = ns.StepPipeline(m, p)
+    rhs2 = [torch.empty((4, w.n_nodes), dtype=torch.float64).pin_memory() for _ in ups]
+    for k in range(len(ups)):
+        pipe.submit(k, up_h[k], None, rhs2[k], None)
+    pipe.synchronize()
+    for k in range(len(ups)):
+        assert relerr(rhs2[k].numpy(), rhs_h[k].numpy()) <= 1e-14
+        assert relerr(ns.assemble_host(m, up_h[k], p).numpy(), rhs_h[k].numpy()) <= 1e-14
     m.close()
 
 
