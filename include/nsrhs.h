@@ -75,17 +75,16 @@ typedef enum {
                                memory, one atomic per (block, node, component);
                                forward and adjoint */
   NSRHS_SCATTER_COLOUR = 3, /* element colouring: elements sharing a node have
-                               different colours; one launch per colour with
-                               plain read-modify-write adds, in a fixed order,
-                               so results are bitwise reproducible. Needs a mesh
-                               created with opts.colour = 1, else
-                               NSRHS_EUNSUPPORTED */
+                               different colours; one launch per colour, whose
+                               atomic adds never meet at one address, so the
+                               summation order is fixed and results are
+                               bitwise reproducible. Needs a mesh created with
+                               opts.colour = 1, else NSRHS_EUNSUPPORTED */
   NSRHS_SCATTER_BLOCK_COLOUR = 4 /* BLOCK with its blocks coloured (blocks
                                sharing a node differ): per-block node sums in a
-                               fixed order, then plain read-modify-write adds,
-                               one launch per block colour; bitwise
-                               reproducible; forward and adjoint. Needs
-                               opts.colour = 1 */
+                               fixed order, then one launch per block colour;
+                               bitwise reproducible; forward and adjoint.
+                               Needs opts.colour = 1 */
 } nsrhs_scatter;
 
 typedef enum {

@@ -14,7 +14,8 @@
 // element from shared memory and writes its 16 entries to shared memory at
 // their sorted positions, and each distinct node's entries (a contiguous run)
 // are summed in a fixed order and added to the global RHS with one atomic per
-// component (or, for coloured blocks, a plain read-modify-write). The global
+// component (for coloured blocks, launched colour by colour, these never meet
+// at one address, so their order is fixed). The global
 // atomics drop from 16 per element to 4 per (block, distinct node), and the
 // sums inside a block do not depend on scheduling.
 #pragma once
@@ -326,12 +327,9 @@ struct Entries<float> {
 // per SM the compiler must allow (register cap): the float kernel is
 // latency-bound between its barrier-separated phases, so more CTAs per SM
 // help; the double kernel is bound by the FP64 pipe.
-// (COLOUR: one staging buffer, the copies of a block are waited for at once,
-// so that the RHS prefetch fits beside it at 4 CTAs per SM.)
 template <class R, bool COLOUR>
 constexpr size_t block_kernel_smem() {
-  return (COLOUR ? 8 : 12) * kBlockSlots * sizeof(R) +
-         (COLOUR ? 4 * kBlockElems * sizeof(double) : 0);
+  return 12 * kBlockSlots * sizeof(R);
 }
 
 template <class R>
@@ -377,8 +375,9 @@ __device__ __forceinline__ void stage_block(int64_t N, int64_t b,
 // computes from the other) and one for the element entries.
 //
 // COLOUR: the CTAs process the blocks order[i0 .. i1) of one block colour (no
-// two share a node), and each node's sums are added with a plain
-// read-modify-write; otherwise blocks 0 .. n_blocks - 1 with atomics.
+// two share a node, so every address receives at most one atomic in the
+// launch and the colour order fixes the summation order: deterministic);
+// otherwise blocks 0 .. n_blocks - 1.
 template <class R, int FLAGS, bool COLOUR = false>
 __global__ void __launch_bounds__(kBlockElems, block_kernel_min_ctas<R>())
     fwd_block_kernel(int64_t N, int64_t E, int64_t n_blocks, const int64_t* __restrict__ node_off,
@@ -389,10 +388,8 @@ __global__ void __launch_bounds__(kBlockElems, block_kernel_min_ctas<R>())
                      int64_t i0 = 0, int64_t i1 = 0) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R* su0 = reinterpret_cast<R*>(smem_raw);  // [4][kBlockSlots] nodal u, v, w, p (even steps)
-  R* su1 = COLOUR ? su0 : su0 + 4 * kBlockSlots;  // the same (odd steps)
+  R* su1 = su0 + 4 * kBlockSlots;            // the same (odd steps)
   R* sF = su1 + 4 * kBlockSlots;             // [4][kBlockSlots] element entries by slot
-  // COLOUR only: [4][kBlockElems] prefetched RHS of each thread's first node
-  double* sold = reinterpret_cast<double*>(sF + 4 * kBlockSlots);
   const int tid = threadIdx.x;
   const int64_t first = COLOUR ? i0 : 0, last = COLOUR ? i1 : n_blocks;
   auto block_at = [&](int64_t i) -> int64_t { return COLOUR ? (int64_t)__ldg(order + i) : i; };
@@ -403,24 +400,12 @@ __global__ void __launch_bounds__(kBlockElems, block_kernel_min_ctas<R>())
     R* su = (step & 1) ? su1 : su0;
     const int64_t b = block_at(i);
     // the next block's copies go into the other buffer, whose last readers
-    // finished before the previous step's middle barrier (COLOUR: one buffer,
-    // staged after this step's middle barrier below)
-    if (!COLOUR && i + gridDim.x < last)
+    // finished before the previous step's middle barrier
+    if (i + gridDim.x < last)
       stage_block(N, block_at(i + gridDim.x), node_off, nodes, up, (step & 1) ? su0 : su1);
     cp_async_commit();
     const int64_t off = node_off[b];
     const int nb = (int)(node_off[b + 1] - off);
-    // COLOUR: the current RHS of this thread's first node, loaded into shared
-    // memory now so that the loads overlap the element arithmetic (no other
-    // CTA of this launch writes it, and earlier colours' launches have
-    // completed).
-    if constexpr (COLOUR) {
-      if (tid < nb) {
-        const int64_t v = __ldg(nodes + off + tid);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) sold[k * kBlockElems + tid] = rhs[k * N + v];
-      }
-    }
     cp_async_wait<1>();  // this block's copies (all but the newest group) have landed
     __syncthreads();     // ... for every thread; the previous block's sums are done
     const int64_t e = b * kBlockElems + tid;
@@ -447,24 +432,13 @@ __global__ void __launch_bounds__(kBlockElems, block_kernel_min_ctas<R>())
         Entries<R>::put(sF, (int)(__ldg(lmap + a * E + e) & 0xffffu), F[a]);
     }
     __syncthreads();
-    if constexpr (COLOUR) {
-      // single buffer, no longer read: the next block's copies overlap the sums
-      if (i + gridDim.x < last)
-        stage_block(N, block_at(i + gridDim.x), node_off, nodes, up, su0);
-      cp_async_commit();
-    }
     for (int j = tid; j < nb; j += kBlockElems) {
       const int r0 = __ldg(runs + off + b + j), r1 = __ldg(runs + off + b + j + 1);
       const int64_t v = __ldg(nodes + off + j);
       double acc[4];
       Entries<R>::sum(sF, r0, r1, acc);
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        if constexpr (COLOUR)
-          rhs[k * N + v] = (j == tid ? sold[k * kBlockElems + tid] : rhs[k * N + v]) + acc[k];
-        else
-          atomicAdd(rhs + k * N + v, acc[k]);
-      }
+      for (int k = 0; k < 4; ++k) atomicAdd(rhs + k * N + v, acc[k]);
     }
   }
   cp_async_wait<0>();
@@ -477,15 +451,12 @@ __global__ void __launch_bounds__(kBlockElems, block_kernel_min_ctas<R>())
 // element's reverse sweep, the 16 gradient entries go back to shared memory
 // at their sorted positions (over the current block's staged values, after a
 // barrier), and each node's entries are summed in a fixed order and added
-// with one atomic per component (COLOUR: with a plain read-modify-write,
-// blocks of one colour per launch). Dynamic shared memory:
+// with one atomic per component (COLOUR: blocks of one colour per launch, so
+// that the summation order is fixed). Dynamic shared memory:
 // block_vjp_smem<R, COLOUR>() bytes.
-// (COLOUR: one staging buffer, staged after a block's sums, measured faster
-// for the coloured launches than two.)
 template <class R, bool COLOUR>
 constexpr size_t block_vjp_smem() {
-  return (COLOUR ? 8 : 16) * kBlockSlots * sizeof(R) +
-         (COLOUR ? 4 * kBlockElems * sizeof(double) : 0);
+  return 16 * kBlockSlots * sizeof(R);
 }
 
 template <class R>
@@ -524,8 +495,7 @@ __global__ void __launch_bounds__(kBlockElems, block_vjp_min_ctas<R>())
   extern __shared__ __align__(16) unsigned char smem_raw[];
   // two staging buffers [8][kBlockSlots]: u, v, w, p, then the cotangent
   R* sb0 = reinterpret_cast<R*>(smem_raw);
-  R* sb1 = COLOUR ? sb0 : sb0 + 8 * kBlockSlots;
-  double* sold = reinterpret_cast<double*>(sb1 + 8 * kBlockSlots);  // COLOUR: [4][kBlockElems]
+  R* sb1 = sb0 + 8 * kBlockSlots;
   const int tid = threadIdx.x;
   const int64_t first = COLOUR ? i0 : 0, last = COLOUR ? i1 : n_blocks;
   auto block_at = [&](int64_t i) -> int64_t { return COLOUR ? (int64_t)__ldg(order + i) : i; };
@@ -538,20 +508,12 @@ __global__ void __launch_bounds__(kBlockElems, block_vjp_min_ctas<R>())
     const int64_t b = block_at(i);
     // the other buffer was last read (as entries) in the previous step's sums,
     // which every thread finished before the previous step's last barrier
-    // (COLOUR: one buffer, staged at the end of the previous step)
-    if (!COLOUR && i + gridDim.x < last)
+    if (i + gridDim.x < last)
       stage_block_vjp(N, block_at(i + gridDim.x), node_off, nodes, up, cot,
                       (step & 1) ? sb0 : sb1);
     cp_async_commit();
     const int64_t off = node_off[b];
     const int nb = (int)(node_off[b + 1] - off);
-    if constexpr (COLOUR) {
-      if (tid < nb) {
-        const int64_t v = __ldg(nodes + off + tid);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) sold[k * kBlockElems + tid] = grad[k * N + v];
-      }
-    }
     cp_async_wait<1>();
     __syncthreads();
     const int64_t e = b * kBlockElems + tid;
@@ -591,19 +553,9 @@ __global__ void __launch_bounds__(kBlockElems, block_vjp_min_ctas<R>())
       double acc[4];
       Entries<R>::sum(su, r0, r1, acc);
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        if constexpr (COLOUR)
-          grad[k * N + v] = (j == tid ? sold[k * kBlockElems + tid] : grad[k * N + v]) + acc[k];
-        else
-          atomicAdd(grad + k * N + v, acc[k]);
-      }
+      for (int k = 0; k < 4; ++k) atomicAdd(grad + k * N + v, acc[k]);
     }
     __syncthreads();  // the sums have read su before it is staged into again
-    if constexpr (COLOUR) {
-      if (i + gridDim.x < last)
-        stage_block_vjp(N, block_at(i + gridDim.x), node_off, nodes, up, cot, sb0);
-      cp_async_commit();
-    }
   }
   cp_async_wait<0>();
 }

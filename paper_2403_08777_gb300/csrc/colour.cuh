@@ -1,12 +1,14 @@
 // Element colouring for the deterministic scatter.
 //
 // Two elements that share a node get different colours. The elements of one
-// colour can then add their 16 entries into the global RHS with plain loads
-// and stores (no two of them touch the same node), one launch per colour in a
-// fixed colour order, so every RHS entry is summed in the same order on every
-// call: the result is bitwise reproducible, unlike the atomic scatter. The
-// paper's CPU code keeps a separate scalar scatter loop for the same reason
-// (no lost updates, Sec. V-C); colouring is the GPU form of that guarantee.
+// colour then add their 16 entries into the global RHS with atomics that
+// never meet at one address (no two of them touch the same node), one launch
+// per colour in a fixed colour order, so every RHS entry is summed in the
+// same order on every call: the result is bitwise reproducible, unlike the
+// unordered atomic scatter, at almost no cost (the atomics stay
+// fire-and-forget). The paper's CPU code keeps a separate scalar scatter
+// loop to avoid lost updates (Sec. V-C); colouring is the GPU form of that
+// guarantee, with a fixed order on top.
 //
 // Colours are chosen greedily in the Jones-Plassmann way. Every element has a
 // fixed pseudo-random priority. In each round, an uncoloured element whose
@@ -19,9 +21,9 @@
 //
 // Blocks are coloured the same way (colour.cuh's block_* kernels): two
 // element blocks (blocks.cuh) that share a node get different colours, so the
-// block scatter can add each block's per-node sums with plain read-modify-write
-// stores, one launch per colour, keeping the blocks' locality. One warp
-// handles one block's node list.
+// block scatter's per-node atomics never meet at one address within a launch
+// and one launch per colour fixes their order, keeping the blocks' locality.
+// One warp handles one block's node list.
 //
 // The colour-major copy: after colouring, the elements are stably sorted by
 // colour (inside a colour they keep the Morton order) and the connectivity

@@ -11,9 +11,10 @@
 // Sec. V-B/V-C), and scatters its 16 entries as soon as they are computed
 // (immediate scatter, Sec. V-D): by double-precision atomic adds (the FP64
 // default), by per-block sums staged in shared memory (the mixed default),
-// or by plain read-modify-write in coloured launches. Atomics and colouring
-// resolve the write conflicts that the paper's CPU path avoids with a
-// separate serial scatter loop (Sec. V-C).
+// or in coloured launches, whose atomics never meet at one address, so that
+// their order (colour after colour) is fixed. Atomics resolve the write
+// conflicts that the paper's CPU path avoids with a separate serial scatter
+// loop (Sec. V-C); colouring also fixes the order of the sums.
 
 #include <cuda_runtime.h>
 
@@ -99,8 +100,8 @@ constexpr int kBlockCtasPerSm = 2048 / nsrhs::kBlockElems > 0 ? 2048 / nsrhs::kB
 #ifndef NSRHS_VJP_MIN_CTAS
 #define NSRHS_VJP_MIN_CTAS 1
 #endif
-// The coloured FP64 kernels hold the read-modify-write scatter's loads in
-// flight; capped so that as many CTAs fit per SM as for the atomic kernels.
+// The coloured FP64 kernels: capped so that as many CTAs fit per SM as for
+// the atomic kernels.
 #ifndef NSRHS_FWD_COLOUR_MIN_CTAS
 #define NSRHS_FWD_COLOUR_MIN_CTAS 3
 #endif
@@ -448,17 +449,6 @@ __device__ __forceinline__ void load_geometry(const R* __restrict__ geom, int64_
   rh = ldg(geom + 10 * E + e);
 }
 
-// One element's entry into the global sum: an atomic add, or, in a coloured
-// launch (no other thread of the launch touches this node), a plain
-// read-modify-write.
-template <bool COLOUR>
-__device__ __forceinline__ void scatter_add(double* p, double x) {
-  if constexpr (COLOUR)
-    *p += x;
-  else
-    atomicAdd(p, x);
-}
-
 // A result entry as double: itself, or a float widened with integer
 // operations (no FP64 instruction).
 __device__ __forceinline__ double to_double(double x) { return x; }
@@ -491,7 +481,7 @@ __device__ __forceinline__ void fwd_fp64_element(int64_t N, int64_t E, int64_t e
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int k = 0; k < 4; ++k) scatter_add<COLOUR>(rhs + k * N + v[a], F[a][k]);
+    for (int k = 0; k < 4; ++k) atomicAdd(rhs + k * N + v[a], F[a][k]);
 }
 
 // FP64 forward, one element per thread over all elements, atomic scatter.
@@ -506,7 +496,9 @@ __global__ void __launch_bounds__(kThreads, NSRHS_FWD_MIN_CTAS)
 }
 
 // FP64 forward over the elements [e0, e1) of one colour of the colour-major
-// copy (row stride E), plain read-modify-write scatter.
+// copy (row stride E). No two elements of a colour share a node, so every
+// address receives at most one atomic in the launch, and the colour order
+// fixes the summation order: the result is bitwise reproducible.
 template <int FLAGS>
 __global__ void __launch_bounds__(kThreads, NSRHS_FWD_COLOUR_MIN_CTAS)
     fwd_fp64_colour_kernel(int64_t N, int64_t E, int64_t e0, int64_t e1,
@@ -577,7 +569,7 @@ __device__ __forceinline__ void fwd_mixed_element(int64_t N, int64_t E, int64_t 
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int k = 0; k < 4; ++k) scatter_add<COLOUR>(rhs + k * N + v[a], nsrhs::widen_f32(F[a][k]));
+    for (int k = 0; k < 4; ++k) atomicAdd(rhs + k * N + v[a], nsrhs::widen_f32(F[a][k]));
 }
 
 template <int FLAGS>
@@ -631,8 +623,8 @@ __device__ __forceinline__ void vjp_fp64_element(int64_t N, int64_t E, int64_t e
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
 #pragma unroll
-    for (int i = 0; i < 3; ++i) scatter_add<COLOUR>(grad + i * N + v[a], gu[a][i]);
-    scatter_add<COLOUR>(grad + 3 * N + v[a], gp[a]);
+    for (int i = 0; i < 3; ++i) atomicAdd(grad + i * N + v[a], gu[a][i]);
+    atomicAdd(grad + 3 * N + v[a], gp[a]);
   }
 }
 
@@ -689,8 +681,8 @@ __device__ __forceinline__ void vjp_mixed_element(int64_t N, int64_t E, int64_t 
   for (int a = 0; a < 4; ++a) {
 #pragma unroll
     for (int i = 0; i < 3; ++i)
-      scatter_add<COLOUR>(grad + i * N + v[a], nsrhs::widen_f32(gu[a][i]));
-    scatter_add<COLOUR>(grad + 3 * N + v[a], nsrhs::widen_f32(gp[a]));
+      atomicAdd(grad + i * N + v[a], nsrhs::widen_f32(gu[a][i]));
+    atomicAdd(grad + 3 * N + v[a], nsrhs::widen_f32(gp[a]));
   }
 }
 
@@ -1393,8 +1385,8 @@ nsrhs_status nsrhs_assemble_vjp(const nsrhs_mesh* m, const nsrhs_params* p, cons
   const bool block = p->scatter == NSRHS_SCATTER_BLOCK ||
                      (p->scatter == NSRHS_SCATTER_AUTO && p->precision == NSRHS_MIXED);
   if (block || p->scatter == NSRHS_SCATTER_BLOCK_COLOUR) {
-    // BLOCK: one grid over all blocks, atomics; BLOCK_COLOUR: one launch per
-    // block colour, plain read-modify-write
+    // BLOCK: one grid over all blocks; BLOCK_COLOUR: one launch per block
+    // colour (the atomics of a launch never meet at one address)
     const bool coloured = p->scatter == NSRHS_SCATTER_BLOCK_COLOUR;
     const int64_t nb = m->n_blocks;
     std::vector<int64_t> ranges = coloured ? m->bcol_off : std::vector<int64_t>{0, nb};
