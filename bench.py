@@ -12,8 +12,16 @@ each (100,663,296 tets, 16,974,593 nodes), interior nodes jittered by
 N(0, 1e-2) noise + m*d with m ~ U(0, 10) and d uniform on the sphere,
 pressure ~ U(-1, 1), seeded and synthetic.
 
-Prints one JSON line (rank 0). --impl reference times the CPU oracle
-instead (bounded sample, host cores).
+Prints one JSON line (rank 0): `value` from the device-resident step,
+`e2e` through StepPipeline from pinned host buffers, `roofline` for the
+dominant kernel (the adjoint) against the FP64 pipe rate, `cpu_baseline`
+(the oracle on the host cores), sampled clocks, and under `forms` the other
+configurations: formulation variants, the one-pass RHS + adjoint, the
+element-matrix comparison path, explicit SSP-RK3 steps (and small-mesh steps
+from a CUDA graph), the scatter sweep (atomic / block / element colouring /
+block colouring), the mixed-precision forward and adjoint with their errors,
+the unstructured mesh, random vs RCM node order and the 64^3 adjoint.
+--impl reference times the CPU oracle instead (bounded sample, host cores).
 """
 from __future__ import annotations
 
