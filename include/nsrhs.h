@@ -113,10 +113,13 @@ typedef struct {
 
 /* Mesh options. */
 typedef struct {
-  double ar_threshold; /* aspect ratio above which the mixed form keeps double
-                          geometry; 10 by default. AR = l_max S / (6 sqrt(6) V)
-                          (l_max longest edge, S surface, V volume; 1 for the
-                          regular tet). */
+  double ar_threshold; /* aspect ratio above which an element counts as high-AR
+                          in nsrhs_mesh_info.n_high_ar; 10 by default.
+                          AR = l_max S / (6 sqrt(6) V) (l_max longest edge,
+                          S surface, V volume; 1 for the regular tet). The
+                          threshold changes no arithmetic: the geometry of
+                          every element is computed in double once per mesh
+                          (and rounded to float for the mixed form). */
   int32_t colour;      /* 1: also colour the elements and keep a colour-major
                           copy of the connectivity and geometry (about 150
                           bytes per element more) for NSRHS_SCATTER_COLOUR,

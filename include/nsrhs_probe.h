@@ -3,8 +3,11 @@
  * assembly kernels. The paper measures its machines' FP peaks with
  * microbenchmarks (Sec. III-B, III-C: likwid-bench peakflops, 9.7 TF/s FP64
  * on the A100) and places its kernels on that roofline (Sec. V-D, Fig. 4).
- * The element kernels here are bound by the FP64 pipe (no tensor cores), so
- * the denominator is this probe's measured FMA rate.
+ * The FP64 element kernels here are bound by the FP64 pipe (no tensor
+ * cores). Their roofline denominator is that pipe's issue rate (2 FP64 FMA
+ * lanes per SM per clock x 2 flops x SMs x the SM clock sampled while they
+ * run); this probe's measured FMA rate is reported beside it, and its FP32
+ * rate is the denominator of the mixed-precision kernels.
  */
 #ifndef NSRHS_PROBE_H
 #define NSRHS_PROBE_H

@@ -15,6 +15,11 @@
 // their order (colour after colour) is fixed. Atomics resolve the write
 // conflicts that the paper's CPU path avoids with a separate serial scatter
 // loop (Sec. V-C); colouring also fixes the order of the sums.
+//
+// Aspect ratio: mesh creation classifies elements by aspect ratio against
+// opts.ar_threshold, but only to report the count (n_high_ar). The threshold
+// changes no arithmetic: every element's determinant and inverse are computed
+// in double once per mesh, and the mixed form reads their float rounding.
 
 #include <cuda_runtime.h>
 

@@ -125,6 +125,23 @@ def test_single_reference_tet_closed_form(dev):
     m.close()
 
 
+@pytest.mark.parametrize("tau", ["gauss", "element"])
+def test_single_tet_vreman_feeds_tau_closed_form(dev, tau):
+    """The 50-digit closed form with the Vreman model and every term on
+    (mu_eff in the viscous term and in tau), through the C ABI, FP64 and
+    mixed."""
+    import test_oracle_pins as pins
+    rho, mu, cv, s, q = 2.0, 1e-3, 0.1, 0.2, -1.3
+    X, U = pins.vreman_stabilised_inputs(s, q)
+    exp = pins.closed_form_vreman_stabilised(rho, mu, cv, s, q, tau == "element")
+    coords, conn = X.T.copy(), np.arange(4, dtype=np.int32).reshape(4, 1)
+    w = mg.Workload("ref", 1, coords, conn, U.T.copy(), rho, mu)
+    for prec, tol in (("fp64", 1e-13), ("mixed", 1e-5)):
+        x, m = gpu_rhs(dev, w, ns.Params(rho=rho, mu=mu, c_vreman=cv, tau=tau, precision=prec))
+        assert np.abs(x.T - exp).max() <= tol * np.abs(exp).max(), prec
+        m.close()
+
+
 @pytest.mark.parametrize("n,cv", [(32, 0.0), (64, 0.0), (32, 0.07)])
 def test_mixed_precision_error(dev, n, cv):
     w = mg.make_workload(n, jitter=0.3, order="rcm", mu=1e-4, mag_max=10.0, c_vreman=cv)

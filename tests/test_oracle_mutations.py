@@ -47,6 +47,18 @@ MUTATIONS = [
      "ub[i] = 0.25 * (U[0][i] + U[1][i] + U[2][i] + U[3][i]);",
      "ub[i] = (U[0][i] + U[1][i] + U[2][i] + U[3][i]);"),
     ("viscous gradient transposed", "gg += dN[a][j] * G[i][j];", "gg += dN[a][j] * G[j][i];"),
+    ("Gauss-point tau with mu instead of mu_eff", "T tau = 1.0 / (P.c1 * mu_eff / (h * h) +",
+     "T tau = 1.0 / (P.c1 * P.mu / (h * h) +"),
+    ("per-element tau with mu instead of mu_eff", "tau_e = 1.0 / (P.c1 * mu_eff / (h * h) +",
+     "tau_e = 1.0 / (P.c1 * P.mu / (h * h) +"),
+    ("viscous term with mu instead of mu_eff", "f += -mu_eff * gg;", "f += -P.mu * gg;"),
+    ("eddy viscosity without density", "mu_eff = P.mu + P.rho * (P.c_vreman",
+     "mu_eff = P.mu + (P.c_vreman"),
+    ("Vreman B without beta_13^2", "be[0][2] * be[0][2] + be[1][1]",
+     "0.0 * be[0][2] + be[1][1]"),
+    ("Vreman B without beta_23^2", "be[1][1] * be[2][2] - be[1][2] * be[1][2];",
+     "be[1][1] * be[2][2];"),
+    ("Vreman A from the diagonal only", "A += al[i][j] * al[i][j];", "A += al[i][i] * al[i][i] / 3.0;"),
 ]
 
 
@@ -99,6 +111,22 @@ def battery(o):
         exp[:, 0] = -(s ** 3 / 6) * mu_eff * dN[:, 1]
         exp[:, 1] = -(s ** 3 / 6) * mu_eff * dN[:, 0]
         check("vreman closed form", np.abs(F - exp).max() <= 1e-14 * np.abs(exp).max())
+        # Vreman with every term on: mu_eff in tau, both tau modes
+        for te in (False, True):
+            X, U = pins.vreman_stabilised_inputs(0.2, -1.3)
+            ref = pins.closed_form_vreman_stabilised(2.0, 1e-3, 0.1, 0.2, -1.3, te)
+            got = o.element(X, U, 2.0, 1e-3, c_vreman=0.1, tau_elem=te)
+            check("vreman stabilised closed form", np.abs(got - ref).max()
+                  <= 1e-14 * np.abs(ref).max())
+        # Vreman with every beta_ij nonzero
+        s3 = 0.3
+        X = pins.ref_tet(s3)
+        U = np.zeros((4, 4))
+        U[:, :3] = X @ pins.G3.T
+        F = o.element(X, U, 2.0, 1e-3, c_vreman=0.1, terms=o.T_VISC)
+        mu_eff = 1e-3 + 2.0 * 0.1 * s3 * s3 * np.sqrt(pins.G3_B_OVER_H4 / pins.G3_A)
+        exp = -(s3 ** 3 / 6) * mu_eff * (np.array(pins.REF_DN, float) / s3) @ pins.G3.T
+        check("vreman 3-d closed form", np.abs(F[:, :3] - exp).max() <= 1e-13 * np.abs(exp).max())
         # per-term textbook forms on random tets
         rng = np.random.default_rng(100)
         for _ in range(3):

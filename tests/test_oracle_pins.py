@@ -142,6 +142,118 @@ def test_closed_form_vreman(s, cv, rho):
     assert np.abs(F2[:, 0] + V * mu * dN[:, 1]).max() <= 1e-15 * V * mu / s
 
 
+def closed_form_vreman_stabilised(rho, mu, cv, s, q, tau_elem, c1=4, c2=2):
+    """Every term with the Vreman model on, tet X0 = 0, Xk = s e_k;
+    u = (y, x, 1), p = q x. grad u has du/dy = dv/dx = 1, so alpha = (grad u)^T
+    has alpha_12 = alpha_21 = 1, beta = h^2 diag(1, 1, 0), B = h^4, A = 2 and
+    nu_t = cv h^2 / sqrt(2): mu_eff = mu + rho cv h^2 / sqrt(2) enters the
+    viscous term and tau (Sec. V-B: the element's eddy viscosity feeds its
+    terms). h = s, V = s^3/6, grad N_a = e/s, div u = 0.
+    Gauss point g: x_g = s N_1(xi_g), y_g = s N_2(xi_g), u_g = (y_g, x_g, 1),
+    (u.grad)u = (x_g, y_g, 0), residual r_g = (rho x_g + q, rho y_g, 0).
+    Galerkin convection: -rho int N_a c with c = (x, y, 0) linear, i.e. the
+    consistent mass matrix V (1 + delta_ab)/20 applied to c at the nodes
+    (0, (s,0,0), (0,s,0), 0). Per-element tau: |mean nodal u| = |(s/4, s/4, 1)|."""
+    rho, mu, cv, s, q = D(rho), D(mu), D(cv), D(s), D(q)
+    V, h, pbar = s ** 3 / 6, s, q * s / 4
+    mu_eff = mu + rho * cv * h * h / D(2).sqrt()
+    N = [[(QA if a == g else QB) for a in range(4)] for g in range(4)]
+    xs = [s * N[g][1] for g in range(4)]
+    ys = [s * N[g][2] for g in range(4)]
+    if tau_elem:
+        te = 1 / (c1 * mu_eff / h ** 2 + c2 * rho * (2 * (s / 4) ** 2 + 1).sqrt() / h)
+        taus = [te] * 4
+    else:
+        taus = [1 / (c1 * mu_eff / h ** 2 + c2 * rho * (ys[g] ** 2 + xs[g] ** 2 + 1).sqrt() / h)
+                for g in range(4)]
+    cnode = [(D(0), D(0)), (s, D(0)), (D(0), s), (D(0), D(0))]
+    F = [[D(0)] * 4 for _ in range(4)]
+    for a in range(4):
+        dN = [D(c) / s for c in REF_DN[a]]
+        conv = [-rho * sum(V * (1 + (a == b)) / 20 * cnode[b][i] for b in range(4))
+                for i in range(2)]
+        adv = [ys[g] * dN[0] + xs[g] * dN[1] + dN[2] for g in range(4)]   # u_g . grad N_a
+        r = [(rho * xs[g] + q, rho * ys[g]) for g in range(4)]
+        supg = [-V / 4 * sum(taus[g] * rho * adv[g] * r[g][i] for g in range(4)) for i in range(2)]
+        F[a][0] = conv[0] - V * mu_eff * dN[1] + V * pbar * dN[0] + supg[0]
+        F[a][1] = conv[1] - V * mu_eff * dN[0] + V * pbar * dN[1] + supg[1]
+        F[a][2] = V * pbar * dN[2]
+        F[a][3] = -V / 4 * sum(taus[g] * (dN[0] * r[g][0] + dN[1] * r[g][1]) for g in range(4))
+    return np.array([[float(x) for x in row] for row in F])
+
+
+def vreman_stabilised_inputs(s, q):
+    X = ref_tet(s)
+    U = np.zeros((4, 4))
+    U[:, 0] = X[:, 1]          # u = y
+    U[:, 1] = X[:, 0]          # v = x
+    U[:, 2] = 1.0              # w = 1
+    U[:, 3] = q * X[:, 0]      # p = q x
+    return X, U
+
+
+@pytest.mark.parametrize("tau_elem", [False, True])
+@pytest.mark.parametrize("rho,mu,cv,s,q", [(1.0, 1e-2, 0.07, 1.0, 0.0),
+                                           (2.0, 1e-3, 0.1, 0.2, -1.3),
+                                           (0.7, 5e-4, 0.07, 2.5, 0.8)])
+def test_closed_form_vreman_feeds_tau(rho, mu, cv, s, q, tau_elem):
+    """mu_eff (not mu) in tau and in the viscous term, with every term on and
+    both tau modes; the eddy viscosity is a sizeable part of mu_eff here."""
+    X, U = vreman_stabilised_inputs(s, q)
+    F = oracle.element(X, U, rho, mu, c_vreman=cv, tau_elem=tau_elem)
+    ref = closed_form_vreman_stabilised(rho, mu, cv, s, q, tau_elem)
+    assert np.abs(F - ref).max() <= 1e-14 * np.abs(ref).max()
+    # the same with the model off differs (so the check above sees mu_eff)
+    ref0 = closed_form_vreman_stabilised(rho, mu, 0.0, s, q, tau_elem)
+    assert np.abs(ref0 - ref).max() > 1e-6 * np.abs(ref).max()
+
+
+# grad u with every beta_ij of the Vreman model nonzero:
+# beta = h^2 G G^T = h^2 [[5, 2, 2], [2, 10, 3], [2, 3, 5]], whose principal
+# 2x2 minors are 46, 21 and 41, so B = 108 h^4; A = sum G_ij^2 = 20.
+G3 = np.array([[1.0, 2.0, 0.0], [0.0, 1.0, 3.0], [2.0, 0.0, 1.0]])
+G3_B_OVER_H4, G3_A = 108, 20
+
+
+@pytest.mark.parametrize("s,cv,rho", [(1.0, 0.07, 1.0), (0.3, 0.1, 2.0)])
+def test_closed_form_vreman_full_3d(s, cv, rho):
+    """u = G3 x + (0.5, -1, 2) on the reference tet scaled by s, viscous term
+    only: F_a,i = -V mu_eff sum_j dN_a/dx_j G_ij with
+    mu_eff = mu + rho cv h^2 sqrt(108/20), h = s (50-digit evaluation)."""
+    mu = 1e-3
+    X = ref_tet(s)
+    U = np.zeros((4, 4))
+    U[:, :3] = X @ G3.T + np.array([0.5, -1.0, 2.0])
+    F = oracle.element(X, U, rho, mu, c_vreman=cv, terms=oracle.T_VISC)
+    sd = D(s)
+    mu_eff = D(mu) + D(rho) * D(cv) * sd * sd * (D(G3_B_OVER_H4) / D(G3_A)).sqrt()
+    V = sd ** 3 / 6
+    exp = np.zeros((4, 4))
+    for a in range(4):
+        dN = [D(c) / sd for c in REF_DN[a]]
+        for i in range(3):
+            exp[a, i] = float(-V * mu_eff * sum(dN[j] * D(G3[i, j]) for j in range(3)))
+    assert np.abs(F - exp).max() <= 1e-14 * np.abs(exp).max()
+
+
+def test_vreman_full_3d_on_a_general_tet():
+    """The same velocity gradient on a general tet: the viscous term is
+    -V mu_eff grad N G^T with grad N from an independent linear solve and
+    mu_eff = mu + rho cv h^2 sqrt(108/20), h = detJ^(1/3)."""
+    rng = np.random.default_rng(11)
+    X = random_tet(rng)
+    U = np.zeros((4, 4))
+    U[:, :3] = X @ G3.T
+    U[:, 3] = rng.normal(size=4)
+    rho, mu, cv = 1.4, 2e-3, 0.07
+    det = np.linalg.det((X[1:] - X[0]).T)
+    h = np.cbrt(det)
+    mu_eff = mu + rho * cv * h * h * np.sqrt(G3_B_OVER_H4 / G3_A)
+    exp = -(det / 6) * mu_eff * bary_grad(X) @ G3.T
+    F = oracle.element(X, U, rho, mu, c_vreman=cv, terms=oracle.T_VISC)
+    assert np.abs(F[:, :3] - exp).max() <= 1e-13 * np.abs(exp).max()
+
+
 def random_tet(rng):
     while True:
         X = rng.normal(size=(4, 3))
