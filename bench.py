@@ -54,11 +54,32 @@ UNIT = "tets/s"
 FLOPS_PER_TET = {"fwd": 518, "vjp": 1091, "rhs_vjp": 1386}
 FLOPS_PER_TET_VREMAN = {"fwd": 571, "vjp": 1236, "rhs_vjp": 1531}
 
+# The METHOD's own operation count per tet and call (the oracle's definition
+# recorded as an expression DAG with constants folded and common
+# subexpressions once; the adjoint adds one reverse-mode sweep over it), with
+# the geometry nodes (coordinates only) separate: the work the restructured
+# kernels replace. tests/test_flop_count.py recomputes these from the oracle.
+FLOPS_PER_TET_METHOD = {"fwd": 932, "vjp": 2188, "geometry": 62}
+FLOPS_PER_TET_METHOD_VREMAN = {"fwd": 1020, "vjp": 2445, "geometry": 61}
+
+# Forming the element geometry from the node coordinates (edges, cofactors,
+# determinant, reciprocal, reciprocal cube root): the same census. The
+# default calls read it from the per-mesh cache; geometry="recompute" forms
+# it in the call.
+FLOPS_GEOMETRY = 43
+
 # DRAM bytes per tet (dram__bytes_read.sum + dram__bytes_write.sum) from one
 # ncu capture of each kernel on the 128^3-hex RCM mesh, scaled to a launch by
 # the element count (traffic grows in proportion). None once a kernel has
 # changed since its counters were taken.
-DRAM_BYTES_PER_TET = {"fwd_fp64": 158.3, "vjp_fp64": 187.9}
+DRAM_BYTES_PER_TET = {"fwd_fp64": 158.3, "vjp_fp64": 187.9,
+                      "fwd_mixed": 87.9, "vjp_mixed": 106.6}
+
+# Algorithmic (compulsory) bytes per tet with ideal node reuse (N/E = 0.1686
+# on the Kuhn mesh): connectivity or block map 16, cached geometry 88 (f64) or
+# 44 (f32), nodal reads and RHS read-modify-writes per node; see the kernels'
+# roofline table in the design notes.
+ALG_BYTES_PER_TET = {"fwd_fp64": 120.0, "vjp_fp64": 126.0, "fwd_mixed": 75.0, "vjp_mixed": 78.0}
 
 # FP64 FMA lanes per SM per clock on GB300 (1.25 TF/s nominal at 2.07 GHz).
 FP64_LANES_PER_SM = 2
@@ -81,6 +102,8 @@ def parse():
                     help="oracle forward elements per host process")
     ap.add_argument("--sample-vjp", type=int, default=1 << 16,
                     help="oracle adjoint elements per host process")
+    ap.add_argument("--sample-ref", type=int, default=1 << 16,
+                    help="--impl reference: elements per host process and step")
     return ap.parse_args()
 
 
@@ -241,26 +264,63 @@ def dist_env():
     return world, rank, local
 
 
+def bench_config(w, world: int) -> dict:
+    """The workload description both arms print (identical keys and values)."""
+    return {"workload": w.name, "n_tets": w.n_elems, "n_nodes": w.n_nodes,
+            "rho": w.rho, "mu": w.mu, "jitter": w.jitter, "order": w.order,
+            "step": "fp64 forward assembly + fp64 adjoint (VJP)",
+            "l2": "inputs larger than L2 (conn 1.6 GB + nodal 1.5 GB per step)",
+            "parallelism": f"replicas x{world}"}
+
+
 def run_reference(args):
+    """The oracle as it stands on the host cores: every step is the FP64
+    forward and then the adjoint over the same bounded sample of the
+    workload's elements (consecutive slices, one per host process, nodes
+    compacted per slice). ms_per_step is the wall time of those steps, so
+    steps x ms_per_step is the time actually spent; value = sampled elements
+    per step / step time, in the same tets/s of a forward + adjoint step."""
     world, rank, _ = dist_env()
     if rank != 0:
         return 0
     w = workload(args.n)
+    import oracle
+    oracle.build()
+    global _W
+    _W = w
     procs = host_cores()
-    cpu_oracle_rates(w, procs, args.sample_fwd, args.sample_vjp, repeats=max(1, args.warmup))
-    fwd, vjp, step, sample, walls = cpu_oracle_rates(w, procs, args.sample_fwd, args.sample_vjp,
-                                                     repeats=args.steps)
-    ms = 1e3 * w.n_elems / step
-    line = {"metric": METRIC, "value": step, "unit": UNIT, "n_gpus": args.gpus,
+    per = max(1, min(args.sample_ref, w.n_elems // procs))
+    n_sample = procs * per
+    tasks_f = [(i * per, (i + 1) * per, "fwd", 0) for i in range(procs)]
+    tasks_v = [(i * per, (i + 1) * per, "vjp", mg.SEED_COT) for i in range(procs)]
+    steps_ms, fwd_s, vjp_s = [], [], []
+    with mp.get_context("fork").Pool(procs) as pool:
+        for k in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            pool.map(_oracle_slice, tasks_f)
+            t1 = time.perf_counter()
+            pool.map(_oracle_slice, tasks_v)
+            t2 = time.perf_counter()
+            if k >= args.warmup:
+                steps_ms.append(1e3 * (t2 - t0))
+                fwd_s.append(t1 - t0)
+                vjp_s.append(t2 - t1)
+    ms = sum(steps_ms) / len(steps_ms)
+    value = n_sample / (ms * 1e-3)
+    sample = (f"each step: the forward and then the adjoint over the same {n_sample} elements "
+              f"({procs} host processes x {per} consecutive elements of the {w.name} mesh, "
+              f"nodes compacted per slice); value = {n_sample} tets / mean step wall time")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": w.name, "n_tets": w.n_elems, "n_nodes": w.n_nodes,
-                       "rho": w.rho, "mu": w.mu, "step": "fp64 forward + adjoint",
-                       "sample": sample},
-            "cpu_baseline": {"value": step, "unit": UNIT, "cores": procs, "kind": "oracle",
-                             "sample": sample, "fwd_tets_per_s": fwd, "vjp_tets_per_s": vjp},
-            "e2e": {"value": step, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "config": bench_config(w, world),
+            "sample": {"tets_per_step": n_sample, "fraction_of_workload": n_sample / w.n_elems},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle",
+                             "sample": sample,
+                             "fwd_tets_per_s": n_sample / statistics.mean(fwd_s),
+                             "vjp_tets_per_s": n_sample / statistics.mean(vjp_s)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -404,6 +464,35 @@ def run_ours(args):
     forms["vjp_fp64"] = {"ms": vjp_med, "tets_per_s": w.n_elems / (vjp_med * 1e-3),
                          "tflops": flops["vjp"] * w.n_elems / (vjp_med * 1e-3) / 1e12,
                          "vs_fwd_fp64": fwd_med / vjp_med}
+    for k in ("fwd_fp64", "vjp_fp64"):
+        forms[k]["frac_fp64_pipe"] = forms[k]["tflops"] / fp64_peak
+    # the Vreman model switched on (c_v = 0.07; the configurations give only
+    # rho and mu, so the headline runs without it), and the element geometry
+    # formed from the coordinates in every call instead of read from the cache
+    def pipe_line(ms, flops_per_tet, extra=None):
+        tf = flops_per_tet * w.n_elems / (ms * 1e-3) / 1e12
+        d = {"ms": ms, "tets_per_s": w.n_elems / (ms * 1e-3), "flops_per_tet": flops_per_tet,
+             "tflops": tf, "frac_fp64_pipe": tf / fp64_peak}
+        d.update(extra or {})
+        return d
+
+    pvr = ns.Params(rho=w.rho, mu=w.mu, c_vreman=0.07)
+    t = _timed(lambda: mesh.assemble(up, pvr, out=rhs), dev, stream, args)
+    forms["fwd_fp64_vreman"] = pipe_line(t, FLOPS_PER_TET_VREMAN["fwd"], {"c_vreman": 0.07})
+    t = _timed(lambda: mesh.assemble_vjp(up, cot, pvr, out=grad), dev, stream, args)
+    forms["vjp_fp64_vreman"] = pipe_line(t, FLOPS_PER_TET_VREMAN["vjp"], {"c_vreman": 0.07})
+    prc = ns.Params(rho=w.rho, mu=w.mu, c_vreman=w.c_vreman, geometry="recompute")
+    t = _timed(lambda: mesh.assemble(up, prc, out=rhs), dev, stream, args)
+    forms["fwd_fp64_uncached"] = pipe_line(t, flops["fwd"] + FLOPS_GEOMETRY,
+                                           {"vs_cached": fwd_med / t})
+    t = _timed(lambda: mesh.assemble_vjp(up, cot, prc, out=grad), dev, stream, args)
+    forms["vjp_fp64_uncached"] = pipe_line(t, flops["vjp"] + FLOPS_GEOMETRY,
+                                           {"vs_cached": vjp_med / t})
+    info = mesh.info()
+    forms["geometry_cache"] = {
+        "bytes_f64": 88 * w.n_elems, "bytes_f32": 44 * w.n_elems,
+        "mesh_device_bytes": info["device_bytes"],
+        "note": "the mesh here also holds both colourings (colour-major copies)"}
     for name, kw in (("fwd_fp64_skew", {"convection": "skew"}),
                      ("fwd_fp64_tau_element", {"tau": "element"})):
         pv = ns.Params(rho=w.rho, mu=w.mu, c_vreman=w.c_vreman, **kw)
@@ -519,18 +608,33 @@ def run_ours(args):
                                 f"probe measured {fp64_probe:.3f} TF/s in this run"),
                 "flops_per_tet": flops["vjp" if dom == "vjp_fp64" else "fwd"],
                 "launch_ms": dom_ms}
+    # the same launch counted with the method's own operations (the oracle's
+    # definition): what the restructured algebra does in fewer operations
+    mflops = FLOPS_PER_TET_METHOD_VREMAN if w.c_vreman else FLOPS_PER_TET_METHOD
+    mper = mflops["vjp" if dom == "vjp_fp64" else "fwd"]
+    roofline["flops_per_tet_method"] = mper
+    roofline["achieved_method"] = mper * w.n_elems / (dom_ms * 1e-3) / 1e12
+    roofline["frac_method"] = roofline["achieved_method"] / fp64_peak
+    # the mixed-precision kernels against both of their roofs: FP32 FMA (the
+    # live probe) and HBM (algorithmic bytes against the measured copy peak)
+    roofline_mixed = {}
+    mixed_ms = {"fwd_mixed": forms.get("mixed_same_mesh", {}).get("ms"),
+                "vjp_mixed": forms["vjp_mixed"]["ms"]}
+    for key, ms in mixed_ms.items():
+        if ms is not None:
+            roofline_mixed[key] = mixed_roofline(key, ms, w.n_elems, fp32_probe, _measured_hbm())
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w.name, "n_tets": w.n_elems, "n_nodes": w.n_nodes,
-                       "rho": w.rho, "mu": w.mu, "jitter": w.jitter, "order": w.order,
-                       "step": "fp64 forward assembly + fp64 adjoint (VJP)",
-                       "l2": "inputs larger than L2 (conn 1.6 GB + nodal 1.5 GB per step)",
-                       "parallelism": f"replicas x{world}"},
+            "config": bench_config(w, world),
             "roofline": roofline,
             "roofline_fwd": {"bound": "alu", "achieved": forms["fwd_fp64"]["tflops"],
                              "peak": fp64_peak, "unit": "TFLOP/s",
-                             "frac": forms["fwd_fp64"]["tflops"] / fp64_peak},
+                             "frac": forms["fwd_fp64"]["tflops"] / fp64_peak,
+                             "flops_per_tet": flops["fwd"],
+                             "flops_per_tet_method": mflops["fwd"],
+                             "achieved_method": mflops["fwd"] * w.n_elems / (fwd_med * 1e-3) / 1e12},
+            "roofline_mixed": roofline_mixed,
             "peaks": {"fp64_tflops": fp64_peak, "fp64_probe_tflops": fp64_probe,
                       "fp32_probe_tflops": fp32_probe,
                       "hbm_gbs_measured_peaks_json": _measured_hbm()},
@@ -550,6 +654,35 @@ def run_ours(args):
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+MIXED_KERNELS = {"fwd_mixed": "fwd_block_kernel<float,0>", "vjp_mixed": "vjp_block_kernel<float,0>"}
+
+
+def mixed_roofline(key, ms, n_elems, fp32_peak, hbm_peak):
+    """One mixed-precision kernel on its two roofs. FP32: algorithmic flops
+    (the census) per launch / launch time against the FP32 FMA-chain probe.
+    HBM: algorithmic bytes per launch / launch time against the measured copy
+    bandwidth; the ncu-measured DRAM bytes are `traffic`. `bound` names the
+    roof the kernel is closer to."""
+    sec = ms * 1e-3
+    kind = key.split("_")[0]
+    tf = FLOPS_PER_TET[kind] * n_elems / sec / 1e12
+    alg = ALG_BYTES_PER_TET[key] * n_elems / sec / 1e9
+    meas = DRAM_BYTES_PER_TET.get(key)
+    d = {"kernel": MIXED_KERNELS[key], "launch_ms": ms,
+         "fp32": {"achieved": tf, "peak": fp32_peak, "unit": "TFLOP/s", "frac": tf / fp32_peak,
+                  "peak_source": "FP32 FMA-chain probe, measured in this run"},
+         "hbm": {"achieved": alg, "peak": hbm_peak, "unit": "GB/s",
+                 "frac": alg / hbm_peak if hbm_peak else None,
+                 "bytes_per_tet_algorithmic": ALG_BYTES_PER_TET[key],
+                 "measured_dram_gbs": meas * n_elems / sec / 1e9 if meas else None,
+                 "peak_source": "hbm_gbs of the driver's measured peaks (copy bandwidth)"},
+         "traffic": meas * n_elems if meas else None}
+    fh = d["hbm"]["frac"] or 0.0
+    d["bound"] = "hbm" if fh >= d["fp32"]["frac"] else "alu"
+    d["frac"] = max(fh, d["fp32"]["frac"])
+    return d
 
 
 def time_mixed(mesh, w, dev, stream, args, fp64_ms):

@@ -99,6 +99,20 @@ typedef enum {
   NSRHS_TAU_ELEMENT = 1 /* one tau per element from |mean nodal velocity| */
 } nsrhs_tau_mode;
 
+typedef enum {
+  NSRHS_GEOM_CACHED = 0,   /* read each element's cofactors, 1/detJ and
+                              detJ^(-1/3), computed in double once per mesh
+                              (88 bytes per element streamed per call) */
+  NSRHS_GEOM_RECOMPUTE = 1 /* form the Jacobian, its cofactors, 1/detJ and
+                              detJ^(-1/3) from the gathered node coordinates in
+                              every call (Sec. V-B: constant shape-function
+                              gradients per element): 43 more FP64 operations
+                              per element instead of the streamed record.
+                              NSRHS_FP64 with scatter AUTO or ATOMIC, in
+                              nsrhs_assemble and nsrhs_assemble_vjp only;
+                              otherwise NSRHS_EUNSUPPORTED */
+} nsrhs_geometry;
+
 /* Physical and numerical parameters (uniform over one call). */
 typedef struct {
   double rho;         /* density, >= 0 */
@@ -109,6 +123,8 @@ typedef struct {
   int32_t scatter;    /* nsrhs_scatter */
   int32_t convection; /* nsrhs_convection */
   int32_t tau_mode;   /* nsrhs_tau_mode */
+  int32_t geometry;   /* nsrhs_geometry */
+  int32_t reserved;   /* must be 0 */
 } nsrhs_params;
 
 /* Mesh options. */
@@ -143,7 +159,7 @@ typedef struct {
 } nsrhs_mesh_info;
 
 /* Fill *p with rho=1, mu=1e-2, c_vreman=0, c1=4, c2=2, FP64, AUTO,
-   convective form, tau at the Gauss points. */
+   convective form, tau at the Gauss points, cached geometry. */
 void nsrhs_params_default(nsrhs_params* p);
 
 /* Fill *o with ar_threshold = 10, colour = 0. */

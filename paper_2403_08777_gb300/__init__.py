@@ -28,6 +28,7 @@ _SCAT = {"auto": _abi.SCATTER_AUTO, "atomic": _abi.SCATTER_ATOMIC, "block": _abi
          "colour": _abi.SCATTER_COLOUR, "block_colour": _abi.SCATTER_BLOCK_COLOUR}
 _CONV = {"convective": _abi.CONVECTIVE, "skew": _abi.SKEW}
 _TAU = {"gauss": _abi.TAU_GAUSS, "element": _abi.TAU_ELEMENT}
+_GEOM = {"cached": _abi.GEOM_CACHED, "recompute": _abi.GEOM_RECOMPUTE}
 
 
 def load_library():
@@ -45,14 +46,16 @@ class Params:
     scatter: str = "auto"
     convection: str = "convective"   # or "skew" (energy-preserving)
     tau: str = "gauss"               # or "element"
+    geometry: str = "cached"         # or "recompute" (formed from coordinates in every call)
 
     def to_c(self) -> _abi.Params:
         if (self.precision not in _PREC or self.scatter not in _SCAT or
-                self.convection not in _CONV or self.tau not in _TAU):
+                self.convection not in _CONV or self.tau not in _TAU or
+                self.geometry not in _GEOM):
             raise ValueError(f"bad option in {self}")
         return _abi.Params(self.rho, self.mu, self.c_vreman, self.c1, self.c2,
                            _PREC[self.precision], _SCAT[self.scatter], _CONV[self.convection],
-                           _TAU[self.tau])
+                           _TAU[self.tau], _GEOM[self.geometry], 0)
 
 
 def _stream_handle(device: torch.device) -> ctypes.c_void_p:

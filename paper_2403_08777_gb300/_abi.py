@@ -11,6 +11,7 @@ FP64, MIXED = 0, 1
 SCATTER_AUTO, SCATTER_ATOMIC, SCATTER_BLOCK, SCATTER_COLOUR, SCATTER_BLOCK_COLOUR = 0, 1, 2, 3, 4
 CONVECTIVE, SKEW = 0, 1
 TAU_GAUSS, TAU_ELEMENT = 0, 1
+GEOM_CACHED, GEOM_RECOMPUTE = 0, 1
 EULER, SSPRK3 = 0, 1
 ELEMENT_COLOUR, ELEMENT_BLOCK_COLOUR, ELEMENT_BLOCK = 0, 1, 2
 
@@ -26,7 +27,8 @@ class Params(ctypes.Structure):
     _fields_ = [("rho", ctypes.c_double), ("mu", ctypes.c_double), ("c_vreman", ctypes.c_double),
                 ("c1", ctypes.c_double), ("c2", ctypes.c_double), ("precision", ctypes.c_int32),
                 ("scatter", ctypes.c_int32), ("convection", ctypes.c_int32),
-                ("tau_mode", ctypes.c_int32)]
+                ("tau_mode", ctypes.c_int32), ("geometry", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class MeshOpts(ctypes.Structure):

@@ -454,6 +454,31 @@ __device__ __forceinline__ void load_geometry(const R* __restrict__ geom, int64_
   rh = ldg(geom + 10 * E + e);
 }
 
+// Where an element's geometry (cofactors, 1/detJ, detJ^(-1/3)) comes from:
+// the per-mesh cache (an 88-byte streamed record), or the node coordinates
+// gathered through the connectivity and formed into the Jacobian in the
+// call itself (Sec. V-B's per-element constant gradients, 43 FP64 operations).
+struct GeomCached {
+  const double* __restrict__ geom;
+  __device__ __forceinline__ void get(int64_t E, int64_t e, const int32_t v[4], double c[3][3],
+                                      double& inv_det, double& rh) const {
+    load_geometry(geom, E, e, c, inv_det, rh);
+  }
+};
+struct GeomRecompute {
+  const double* __restrict__ coords;  // [3][N]
+  int64_t N;
+  __device__ __forceinline__ void get(int64_t E, int64_t e, const int32_t v[4], double c[3][3],
+                                      double& inv_det, double& rh) const {
+    double X[4][3];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int d = 0; d < 3; ++d) X[a][d] = __ldg(coords + d * N + v[a]);
+    nsrhs::element_geometry<double, double>(X, c, inv_det, rh);
+  }
+};
+
 // A result entry as double: itself, or a float widened with integer
 // operations (no FP64 instruction).
 __device__ __forceinline__ double to_double(double x) { return x; }
@@ -462,10 +487,9 @@ __device__ __forceinline__ double to_double(float x) { return nsrhs::widen_f32(x
 // FP64 forward of element e: streamed connectivity and cached geometry,
 // gathered nodal (u, p), register-resident element arithmetic, immediate
 // scatter of the 16 entries.
-template <int FLAGS, bool COLOUR>
+template <int FLAGS, bool COLOUR, class GS = GeomCached>
 __device__ __forceinline__ void fwd_fp64_element(int64_t N, int64_t E, int64_t e,
-                                                 const int32_t* __restrict__ conn,
-                                                 const double* __restrict__ geom,
+                                                 const int32_t* __restrict__ conn, const GS& gs,
                                                  const double* __restrict__ up,
                                                  const ElemParams<double>& P,
                                                  double* __restrict__ rhs) {
@@ -480,7 +504,7 @@ __device__ __forceinline__ void fwd_fp64_element(int64_t N, int64_t E, int64_t e
     p[a] = ldg(up + 3 * N + v[a]);
   }
   double c[3][3], inv_det, rh;
-  load_geometry(geom, E, e, c, inv_det, rh);
+  gs.get(E, e, v, c, inv_det, rh);
   double F[4][4];
   nsrhs::element_rhs<double, FLAGS>(c, inv_det, rh, u, p, P, F);
 #pragma unroll
@@ -497,7 +521,20 @@ __global__ void __launch_bounds__(kThreads, NSRHS_FWD_MIN_CTAS)
                            ElemParams<double> P, double* __restrict__ rhs) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E;
        e += (int64_t)gridDim.x * blockDim.x)
-    fwd_fp64_element<FLAGS, false>(N, E, e, conn, geom, up, P, rhs);
+    fwd_fp64_element<FLAGS, false>(N, E, e, conn, GeomCached{geom}, up, P, rhs);
+}
+
+// FP64 forward with the element geometry formed from the gathered node
+// coordinates in the call (no cached geometry read), atomic scatter.
+template <int FLAGS>
+__global__ void __launch_bounds__(kThreads, NSRHS_FWD_MIN_CTAS)
+    fwd_fp64_recompute_kernel(int64_t N, int64_t E, const int32_t* __restrict__ conn,
+                              const double* __restrict__ coords, const double* __restrict__ up,
+                              ElemParams<double> P, double* __restrict__ rhs) {
+  const GeomRecompute gs{coords, N};
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E;
+       e += (int64_t)gridDim.x * blockDim.x)
+    fwd_fp64_element<FLAGS, false>(N, E, e, conn, gs, up, P, rhs);
 }
 
 // FP64 forward over the elements [e0, e1) of one colour of the colour-major
@@ -512,7 +549,7 @@ __global__ void __launch_bounds__(kThreads, NSRHS_FWD_COLOUR_MIN_CTAS)
                            double* __restrict__ rhs) {
   for (int64_t e = e0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < e1;
        e += (int64_t)gridDim.x * blockDim.x)
-    fwd_fp64_element<FLAGS, true>(N, E, e, conn, geom, up, P, rhs);
+    fwd_fp64_element<FLAGS, true>(N, E, e, conn, GeomCached{geom}, up, P, rhs);
 }
 
 // Element-matrix comparison kernel: the same RHS through a full 16x16
@@ -601,10 +638,9 @@ __global__ void __launch_bounds__(kThreads)
 // FP64 vector-Jacobian product of element e: gather the cotangent at the
 // element's nodes (the reverse of the scatter), recompute the element, run
 // the reverse sweep, scatter-add the gradient (the reverse of the gather).
-template <int FLAGS, bool COLOUR>
+template <int FLAGS, bool COLOUR, class GS = GeomCached>
 __device__ __forceinline__ void vjp_fp64_element(int64_t N, int64_t E, int64_t e,
-                                                 const int32_t* __restrict__ conn,
-                                                 const double* __restrict__ geom,
+                                                 const int32_t* __restrict__ conn, const GS& gs,
                                                  const double* __restrict__ up,
                                                  const double* __restrict__ cot,
                                                  const ElemParams<double>& P,
@@ -622,7 +658,7 @@ __device__ __forceinline__ void vjp_fp64_element(int64_t N, int64_t E, int64_t e
     for (int k = 0; k < 4; ++k) w[a][k] = ldg(cot + k * N + v[a]);
   }
   double c[3][3], inv_det, rh;
-  load_geometry(geom, E, e, c, inv_det, rh);
+  gs.get(E, e, v, c, inv_det, rh);
   double gu[4][3], gp[4];
   nsrhs::element_vjp<double, FLAGS>(c, inv_det, rh, u, p, w, P, gu, gp);
 #pragma unroll
@@ -641,7 +677,21 @@ __global__ void __launch_bounds__(kThreads, NSRHS_VJP_MIN_CTAS)
                            double* __restrict__ grad) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E;
        e += (int64_t)gridDim.x * blockDim.x)
-    vjp_fp64_element<FLAGS, false>(N, E, e, conn, geom, up, cot, P, grad);
+    vjp_fp64_element<FLAGS, false>(N, E, e, conn, GeomCached{geom}, up, cot, P, grad);
+}
+
+// FP64 adjoint with the element geometry formed from the gathered node
+// coordinates in the call, atomic scatter.
+template <int FLAGS>
+__global__ void __launch_bounds__(kThreads, NSRHS_VJP_MIN_CTAS)
+    vjp_fp64_recompute_kernel(int64_t N, int64_t E, const int32_t* __restrict__ conn,
+                              const double* __restrict__ coords, const double* __restrict__ up,
+                              const double* __restrict__ cot, ElemParams<double> P,
+                              double* __restrict__ grad) {
+  const GeomRecompute gs{coords, N};
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E;
+       e += (int64_t)gridDim.x * blockDim.x)
+    vjp_fp64_element<FLAGS, false>(N, E, e, conn, gs, up, cot, P, grad);
 }
 
 template <int FLAGS>
@@ -652,7 +702,7 @@ __global__ void __launch_bounds__(kThreads, NSRHS_VJP_COLOUR_MIN_CTAS)
                            ElemParams<double> P, double* __restrict__ grad) {
   for (int64_t e = e0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < e1;
        e += (int64_t)gridDim.x * blockDim.x)
-    vjp_fp64_element<FLAGS, true>(N, E, e, conn, geom, up, cot, P, grad);
+    vjp_fp64_element<FLAGS, true>(N, E, e, conn, GeomCached{geom}, up, cot, P, grad);
 }
 
 // Mixed-precision vector-Jacobian product of element e: float (u, p), float
@@ -817,7 +867,15 @@ nsrhs_status check_params(const nsrhs_params* p) {
     return NSRHS_EINVAL;
   if (p->convection != NSRHS_CONVECTIVE && p->convection != NSRHS_SKEW) return NSRHS_EINVAL;
   if (p->tau_mode != NSRHS_TAU_GAUSS && p->tau_mode != NSRHS_TAU_ELEMENT) return NSRHS_EINVAL;
+  if (p->geometry != NSRHS_GEOM_CACHED && p->geometry != NSRHS_GEOM_RECOMPUTE) return NSRHS_EINVAL;
+  if (p->reserved != 0) return NSRHS_EINVAL;
   return NSRHS_OK;
+}
+
+// The geometry-recompute path exists for the FP64 atomic forward and adjoint.
+bool recompute_supported(const nsrhs_params* p) {
+  return p->precision == NSRHS_FP64 &&
+         (p->scatter == NSRHS_SCATTER_AUTO || p->scatter == NSRHS_SCATTER_ATOMIC);
 }
 
 template <class R>
@@ -1185,6 +1243,8 @@ void nsrhs_params_default(nsrhs_params* p) {
   p->scatter = NSRHS_SCATTER_AUTO;
   p->convection = NSRHS_CONVECTIVE;
   p->tau_mode = NSRHS_TAU_GAUSS;
+  p->geometry = NSRHS_GEOM_CACHED;
+  p->reserved = 0;
 }
 
 void nsrhs_mesh_opts_default(nsrhs_mesh_opts* o) {
@@ -1258,7 +1318,17 @@ nsrhs_status nsrhs_assemble(const nsrhs_mesh* m, const nsrhs_params* p, const vo
   if ((p->scatter == NSRHS_SCATTER_COLOUR && m->col_conn == nullptr) ||
       (p->scatter == NSRHS_SCATTER_BLOCK_COLOUR && m->bcol_order == nullptr))
     return NSRHS_EUNSUPPORTED;
+  if (p->geometry == NSRHS_GEOM_RECOMPUTE && !recompute_supported(p)) return NSRHS_EUNSUPPORTED;
   NSRHS_TRY(cudaMemsetAsync(rhs, 0, sizeof(double) * 4 * N, s));
+  if (p->geometry == NSRHS_GEOM_RECOMPUTE) {
+    auto P = elem_params<double>(p);
+    with_flags(flags, [&](auto fl) {
+      fwd_fp64_recompute_kernel<decltype(fl)::value><<<grid_for(E, m->device, 16), kThreads, 0,
+                                                       s>>>(N, E, m->conn, m->coords,
+                                                            (const double*)up, P, rhs);
+    });
+    return cuda_status(cudaGetLastError());
+  }
   if (p->scatter == NSRHS_SCATTER_BLOCK_COLOUR) {
     // one launch per block colour, in colour order
     const int64_t nb = m->n_blocks;
@@ -1383,8 +1453,19 @@ nsrhs_status nsrhs_assemble_vjp(const nsrhs_mesh* m, const nsrhs_params* p, cons
   if ((p->scatter == NSRHS_SCATTER_COLOUR && m->col_conn == nullptr) ||
       (p->scatter == NSRHS_SCATTER_BLOCK_COLOUR && m->bcol_order == nullptr))
     return NSRHS_EUNSUPPORTED;
+  if (p->geometry == NSRHS_GEOM_RECOMPUTE && !recompute_supported(p)) return NSRHS_EUNSUPPORTED;
   NSRHS_TRY(cudaMemsetAsync(grad, 0, sizeof(double) * 4 * N, s));
   const int flags = formulation_flags(p);
+  if (p->geometry == NSRHS_GEOM_RECOMPUTE) {
+    auto P = elem_params<double>(p);
+    with_flags(flags, [&](auto fl) {
+      vjp_fp64_recompute_kernel<decltype(fl)::value><<<grid_for(E, m->device, 16), kThreads, 0,
+                                                       s>>>(N, E, m->conn, m->coords,
+                                                            (const double*)up,
+                                                            (const double*)cot, P, grad);
+    });
+    return cuda_status(cudaGetLastError());
+  }
   // AUTO: atomics for the FP64 form (FP64-pipe-bound), blocks for the mixed
   // form (measured faster)
   const bool block = p->scatter == NSRHS_SCATTER_BLOCK ||
@@ -1483,6 +1564,7 @@ nsrhs_status nsrhs_assemble_rhs_vjp(const nsrhs_mesh* m, const nsrhs_params* p, 
   if (st != NSRHS_OK) return st;
   if (p->scatter != NSRHS_SCATTER_AUTO && p->scatter != NSRHS_SCATTER_ATOMIC)
     return NSRHS_EUNSUPPORTED;
+  if (p->geometry != NSRHS_GEOM_CACHED) return NSRHS_EUNSUPPORTED;
   cudaStream_t s = (cudaStream_t)stream;
   DeviceGuard dg(m->device);
   if (!dg.ok) return NSRHS_ECUDA;
@@ -1534,7 +1616,7 @@ nsrhs_status nsrhs_assemble_elmat(const nsrhs_mesh* m, const nsrhs_params* p, co
   nsrhs_status st = check_params(p);
   if (st != NSRHS_OK) return st;
   if (p->precision != NSRHS_FP64 || p->convection != NSRHS_CONVECTIVE ||
-      p->tau_mode != NSRHS_TAU_GAUSS)
+      p->tau_mode != NSRHS_TAU_GAUSS || p->geometry != NSRHS_GEOM_CACHED)
     return NSRHS_EUNSUPPORTED;
   cudaStream_t s = (cudaStream_t)stream;
   DeviceGuard dg(m->device);

@@ -41,11 +41,11 @@ def test_status_strings_and_defaults(lib):
     p = _abi.Params()
     lib.nsrhs_params_default(ctypes.byref(p))
     assert (p.rho, p.mu, p.c_vreman, p.c1, p.c2, p.precision, p.scatter, p.convection,
-            p.tau_mode) == (1.0, 1e-2, 0.0, 4.0, 2.0, 0, 0, 0, 0)
+            p.tau_mode, p.geometry, p.reserved) == (1.0, 1e-2, 0.0, 4.0, 2.0, 0, 0, 0, 0, 0, 0)
     o = _abi.MeshOpts()
     lib.nsrhs_mesh_opts_default(ctypes.byref(o))
     assert (o.ar_threshold, o.colour, o.reserved) == (10.0, 0, 0)
-    assert ctypes.sizeof(_abi.Params) == 56 and ctypes.sizeof(_abi.MeshInfo) == 80
+    assert ctypes.sizeof(_abi.Params) == 64 and ctypes.sizeof(_abi.MeshInfo) == 80
     assert ctypes.sizeof(_abi.MeshOpts) == 16
 
 

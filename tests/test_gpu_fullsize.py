@@ -49,6 +49,21 @@ def test_fullsize_fp64_forward_and_adjoint(dev):
     gref = oracle.vjp(w.coords, sub, w.up, cot, w.rho, w.mu)[:, nodes]
     gerr = np.linalg.norm(g - gref) / np.linalg.norm(gref)
     assert gerr <= 1e-12, gerr
+    # the same with the geometry formed in the call, and with the Vreman model
+    idx = torch.from_numpy(nodes).to(dev)
+    cot_d = torch.from_numpy(cot).to(dev)
+    prc = ns.Params(rho=w.rho, mu=w.mu, geometry="recompute")
+    x = m.assemble(up, prc)[:, idx].cpu().numpy()
+    assert np.linalg.norm(x - ref) / np.linalg.norm(ref) <= 1e-12
+    x = m.assemble_vjp(up, cot_d, prc)[:, idx].cpu().numpy()
+    assert np.linalg.norm(x - gref) / np.linalg.norm(gref) <= 1e-12
+    pv = ns.Params(rho=w.rho, mu=w.mu, c_vreman=0.07)
+    refv = oracle.assemble(w.coords, sub, w.up, w.rho, w.mu, c_vreman=0.07)[:, nodes]
+    x = m.assemble(up, pv)[:, idx].cpu().numpy()
+    assert np.linalg.norm(x - refv) / np.linalg.norm(refv) <= 1e-12
+    grefv = oracle.vjp(w.coords, sub, w.up, cot, w.rho, w.mu, c_vreman=0.07)[:, nodes]
+    x = m.assemble_vjp(up, cot_d, pv)[:, idx].cpu().numpy()
+    assert np.linalg.norm(x - grefv) / np.linalg.norm(grefv) <= 1e-12
     m.close()
 
 

@@ -317,6 +317,62 @@ def test_formulation_variants_match_oracle(dev, cv, conv, tau):
     m.close()
 
 
+@pytest.mark.parametrize("cv,conv,tau", VARIANTS)
+def test_recomputed_geometry_matches_oracle(dev, cv, conv, tau):
+    """geometry='recompute' (Jacobian, cofactors, 1/detJ, detJ^(-1/3) formed
+    from the gathered coordinates in the call): forward and adjoint against
+    the oracle, every formulation variant, a ragged element count."""
+    w = mg.make_workload(13, jitter=0.3, order="random", mu=1e-3, mag_max=3.0, c_vreman=cv)
+    okw = dict(c_vreman=cv, skew=conv == "skew", tau_elem=tau == "element")
+    ref = oracle.assemble(w.coords, w.conn, w.up, w.rho, w.mu, **okw)
+    cot = mg.normal((4, w.n_nodes), seed=mg.SEED_COT)
+    gref = oracle.vjp(w.coords, w.conn, w.up, cot, w.rho, w.mu, **okw)
+    coords, conn, up, cot_d = on_dev(dev, w.coords, w.conn, w.up, cot)
+    m = ns.Mesh(coords, conn)
+    for scatter in ("auto", "atomic"):
+        p = ns.Params(rho=w.rho, mu=w.mu, c_vreman=cv, convection=conv, tau=tau, scatter=scatter,
+                      geometry="recompute")
+        check_fp64(m.assemble(up, p).cpu().numpy(), ref)
+        g = m.assemble_vjp(up, cot_d, p).cpu().numpy()
+        assert relerr(g, gref) <= TOL_VJP_ORACLE, (scatter, relerr(g, gref))
+    m.close()
+
+
+def test_recomputed_geometry_unsupported_combinations(dev):
+    w = mg.make_workload(4)
+    coords, conn, up = on_dev(dev, w.coords, w.conn, w.up)
+    m = ns.Mesh(coords, conn, colour=True)
+    for kw in (dict(scatter="block"), dict(scatter="colour"), dict(scatter="block_colour"),
+               dict(precision="mixed")):
+        p = ns.Params(geometry="recompute", **kw)
+        u = up.float() if kw.get("precision") == "mixed" else up
+        with pytest.raises(_abi.NSRHSError):
+            m.assemble(u, p)
+        with pytest.raises(_abi.NSRHSError):
+            m.assemble_vjp(u, u, p)
+    with pytest.raises(_abi.NSRHSError):
+        m.assemble_rhs_vjp(up, up, ns.Params(geometry="recompute"))
+    with pytest.raises(_abi.NSRHSError):
+        m.assemble_elmat(up, ns.Params(geometry="recompute"))
+    # out-of-range geometry and a nonzero reserved field are argument errors
+    import ctypes
+    lib = ns.load_library()
+    out = torch.empty_like(up)
+    for geo, res in ((2, 0), (-1, 0), (0, 1)):
+        cp = ns.Params().to_c()
+        cp.geometry, cp.reserved = geo, res
+        st = lib.nsrhs_assemble(m.handle, ctypes.byref(cp), ctypes.c_void_p(up.data_ptr()),
+                                ctypes.c_void_p(out.data_ptr()), None)
+        assert st == _abi.EINVAL
+    # the FP64 explicit step assembles through the recompute path
+    w2 = up.clone()
+    m.explicit_step(w2, 1e-4, "euler", ns.Params(geometry="recompute"))
+    w3 = up.clone()
+    m.explicit_step(w3, 1e-4, "euler", ns.Params())
+    assert relerr(w2.cpu().numpy(), w3.cpu().numpy()) <= 1e-14
+    m.close()
+
+
 def test_skew_convection_does_no_work_on_gpu(dev):
     """The energy identity through the kernel: with the skew-symmetric form
     the convective RHS does no work, so with mu -> tiny, no pressure and no
