@@ -104,6 +104,9 @@ def parse():
                     help="oracle adjoint elements per host process")
     ap.add_argument("--sample-ref", type=int, default=1 << 16,
                     help="--impl reference: elements per host process and step")
+    ap.add_argument("--profile", choices=["fp64", "mixed"], default=None,
+                    help="for Nsight Compute: only `--steps` forward and adjoint launches of "
+                         "that form on the --n mesh (after --warmup), no JSON line")
     return ap.parse_args()
 
 
@@ -933,10 +936,35 @@ def _measured_hbm():
         return None
 
 
+def run_profile(args):
+    """A short launch sequence for a profiler: the forward and the adjoint of
+    one form, --warmup then --steps times each, on the --n mesh."""
+    import torch
+    import paper_2403_08777_gb300 as ns
+    w = workload(args.n)
+    dev = torch.device("cuda", 0)
+    mesh = ns.Mesh(torch.from_numpy(w.coords).to(dev), torch.from_numpy(w.conn).to(dev))
+    up = torch.from_numpy(w.up).to(dev)
+    cot = torch.from_numpy(mg.normal((4, w.n_nodes), seed=mg.SEED_COT)).to(dev)
+    if args.profile == "mixed":
+        up, cot = up.float(), cot.float()
+    p = ns.Params(rho=w.rho, mu=w.mu, precision=args.profile)
+    out = torch.empty((4, w.n_nodes), dtype=torch.float64, device=dev)
+    for _ in range(args.warmup + args.steps):
+        mesh.assemble(up, p, out=out)
+    for _ in range(args.warmup + args.steps):
+        mesh.assemble_vjp(up, cot, p, out=out)
+    torch.cuda.synchronize(dev)
+    mesh.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile:
+        return run_profile(args)
     return run_ours(args)
 
 

@@ -6,7 +6,7 @@
 // it touches and, per distinct node, its run [runs[j], runs[j + 1]) in the
 // block's contributions sorted by node are stored; per element and local
 // node, its distinct-node index and the position of its contribution in that
-// sorted order (lmap = index << 16 | position).
+// sorted order (lmap = index << 16 | position, in the element's record).
 //
 // Assembly (per call): each CTA walks its blocks; for a block it loads the
 // nodal values of the distinct nodes once into shared memory (as cp.async
@@ -36,6 +36,34 @@ namespace nsrhs {
 #endif
 constexpr int kBlockElems = NSRHS_BLOCK_ELEMS;  // elements per block = threads per CTA
 constexpr int kBlockSlots = 4 * kBlockElems;     // at most this many distinct nodes
+
+// Per-element record of the block kernels and the mixed form, 64 bytes (four
+// 16-byte loads): the element geometry rounded to float (cofactor vectors
+// c_k at g[3k + d], 1/detJ at g[9], detJ^(-1/3) at g[10]; computed in double
+// once per mesh) and, per local node a, lmap[a] = (index of the node among the
+// block's distinct nodes << 16) | position of the element's contribution to
+// it in the block's node-sorted order.
+struct __align__(16) ElemRecF {
+  float g[12];  // g[11] unused
+  uint32_t lmap[4];
+};
+static_assert(sizeof(ElemRecF) == 64, "ElemRecF layout");
+
+// Loads of one record: the float geometry (three 16-byte loads) and the
+// block map (one).
+__device__ __forceinline__ void load_rec_geometry(const ElemRecF* __restrict__ rec, int64_t e,
+                                                  float c[3][3], float& inv_det, float& rh) {
+  const float4* r = reinterpret_cast<const float4*>(rec + e);
+  const float4 a = __ldg(r), b = __ldg(r + 1), d = __ldg(r + 2);
+  c[0][0] = a.x; c[0][1] = a.y; c[0][2] = a.z;
+  c[1][0] = a.w; c[1][1] = b.x; c[1][2] = b.y;
+  c[2][0] = b.z; c[2][1] = b.w; c[2][2] = d.x;
+  inv_det = d.y;
+  rh = d.z;
+}
+__device__ __forceinline__ uint4 load_rec_lmap(const ElemRecF* __restrict__ rec, int64_t e) {
+  return __ldg(reinterpret_cast<const uint4*>(rec + e) + 3);
+}
 
 // ---- setup ----
 
@@ -123,13 +151,13 @@ __global__ void permute_conn_kernel(int64_t E, const int32_t* __restrict__ in,
 // pass 1 (node_off = exclusive sum of counts) writes
 //   nodes[node_off[b] + j]        j-th distinct node (ascending)
 //   runs[node_off[b] + b + j]     first sorted position of node j (runs[.. + n] = #valid)
-//   lmap[a * E + e]               (distinct-node index << 16) | sorted position of
+//   rec[e].lmap[a]                (distinct-node index << 16) | sorted position of
 //                                 (element e, local node a)
 __global__ void __launch_bounds__(kBlockElems)
     block_plan_kernel(int pass, int64_t E, const int32_t* __restrict__ conn,
                       int64_t* __restrict__ counts, const int64_t* __restrict__ node_off,
                       int32_t* __restrict__ nodes, uint16_t* __restrict__ runs,
-                      uint32_t* __restrict__ lmap) {
+                      ElemRecF* __restrict__ rec) {
   __shared__ unsigned long long key[kBlockSlots];
   __shared__ int part[kBlockElems];
   const int tid = threadIdx.x;
@@ -197,7 +225,7 @@ __global__ void __launch_bounds__(kBlockElems)
       nodes[off + u] = (int32_t)(kk >> 16);
       runs[off + b + u] = (uint16_t)i;
     }
-    lmap[(int64_t)(slot & 3) * E + e0 + (slot >> 2)] = ((uint32_t)u << 16) | (uint32_t)i;
+    rec[e0 + (slot >> 2)].lmap[slot & 3] = ((uint32_t)u << 16) | (uint32_t)i;
   }
   // number of valid positions = elements in the block * 4
   if (tid == 0) {
@@ -206,6 +234,7 @@ __global__ void __launch_bounds__(kBlockElems)
   }
   (void)n_valid_here;
 }
+
 
 // ---- assembly ----
 
@@ -221,17 +250,6 @@ struct NodeSum<double> {
   double s = 0.0;
   __device__ __forceinline__ void add(double x) { s += x; }
   __device__ __forceinline__ double value() const { return s; }
-};
-template <>
-struct NodeSum<float> {
-  float s = 0.0f, c = 0.0f;
-  __device__ __forceinline__ void add(float x) {
-    const float t = s + x;
-    const float bp = t - s;
-    c += (s - (t - bp)) + (x - bp);
-    s = t;
-  }
-  __device__ __forceinline__ double value() const { return widen_f32(s) + widen_f32(c); }
 };
 
 // Two floats in one 64-bit register (low word first), added or subtracted
@@ -249,16 +267,12 @@ __device__ __forceinline__ unsigned long long f32x2_sub(unsigned long long a,
   asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
   return d;
 }
-__device__ __forceinline__ unsigned long long f32x2_pack(float lo, float hi) {
-  return ((unsigned long long)__float_as_uint(hi) << 32) | (unsigned long long)__float_as_uint(lo);
-}
 __device__ __forceinline__ float f32x2_lo(unsigned long long x) { return __uint_as_float((unsigned)x); }
 __device__ __forceinline__ float f32x2_hi(unsigned long long x) {
   return __uint_as_float((unsigned)(x >> 32));
 }
 
-// NodeSum<float> on two components at once: lane by lane the same operations
-// in the same order, so the same result.
+// The compensated float sum (TwoSum per addition) on two components at once.
 struct NodeSumF32x2 {
   unsigned long long s = 0ull, c = 0ull;
   __device__ __forceinline__ void add(unsigned long long x) {
@@ -277,51 +291,102 @@ struct NodeSumF32x2 {
   }
 };
 
-// The element entries by sorted position in shared memory: double, four
-// component rows [4][kBlockSlots]; float, two rows of component pairs
-// [2][kBlockSlots] (components 0-1, 2-3) so that one 64-bit access and one
-// two-wide addition serve two components.
+// Shared-memory layouts. Staged nodal values: one 4-component record per
+// distinct node (u, v, w, p; the adjoint adds the cotangent's 4), so that an
+// element reads each of its nodes with 128-bit loads. Element entries: one
+// 4-component record per sorted position.
 template <class R>
-struct Entries;
+struct Smem;
 template <>
-struct Entries<double> {
-  static __device__ __forceinline__ void put(void* base, int pos, const double f[4]) {
-    double* e = static_cast<double*>(base);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) e[k * kBlockSlots + pos] = f[k];
+struct Smem<float> {
+  // the 4 values of node slot lc from a [slot][stride] float buffer
+  static __device__ __forceinline__ void get4(const float* buf, int stride, int lc, float v[4]) {
+    const float4 q = *reinterpret_cast<const float4*>(buf + stride * lc);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
   }
-  // sums of positions [r0, r1), in order
-  static __device__ __forceinline__ void sum(const void* base, int r0, int r1, double out[4]) {
-    const double* e = static_cast<const double*>(base);
-    NodeSum<double> acc[4];
+  static __device__ __forceinline__ void put4(float* buf, int pos, const float f[4]) {
+    *reinterpret_cast<float4*>(buf + 4 * pos) = make_float4(f[0], f[1], f[2], f[3]);
+  }
+  // sums of components 2h and 2h + 1 over the positions [r0, r1), in order
+  static __device__ __forceinline__ void sum_pair(const float* buf, int h, int r0, int r1,
+                                                  double& lo, double& hi) {
+    const unsigned long long* e = reinterpret_cast<const unsigned long long*>(buf) + h;
+    NodeSumF32x2 acc;
+    unsigned long long x = r0 < r1 ? e[2 * r0] : 0ull;
     for (int q = r0; q < r1; ++q) {
-#pragma unroll
-      for (int k = 0; k < 4; ++k) acc[k].add(e[k * kBlockSlots + q]);
+      const unsigned long long next = q + 1 < r1 ? e[2 * (q + 1)] : 0ull;
+      acc.add(x);
+      x = next;
     }
-#pragma unroll
-    for (int k = 0; k < 4; ++k) out[k] = acc[k].value();
+    lo = acc.lo();
+    hi = acc.hi();
   }
 };
 template <>
-struct Entries<float> {
-  static __device__ __forceinline__ void put(void* base, int pos, const float f[4]) {
-    unsigned long long* e = static_cast<unsigned long long*>(base);
-    e[pos] = f32x2_pack(f[0], f[1]);
-    e[kBlockSlots + pos] = f32x2_pack(f[2], f[3]);
+struct Smem<double> {
+  static __device__ __forceinline__ void get4(const double* buf, int stride, int lc, double v[4]) {
+    const double2* q = reinterpret_cast<const double2*>(buf + stride * lc);
+    const double2 a = q[0], b = q[1];
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
   }
-  static __device__ __forceinline__ void sum(const void* base, int r0, int r1, double out[4]) {
-    const unsigned long long* e = static_cast<const unsigned long long*>(base);
-    NodeSumF32x2 a01, a23;
+  static __device__ __forceinline__ void put4(double* buf, int pos, const double f[4]) {
+    double2* q = reinterpret_cast<double2*>(buf + 4 * pos);
+    q[0] = make_double2(f[0], f[1]);
+    q[1] = make_double2(f[2], f[3]);
+  }
+  static __device__ __forceinline__ void sum_pair(const double* buf, int h, int r0, int r1,
+                                                  double& lo, double& hi) {
+    const double2* e = reinterpret_cast<const double2*>(buf) + h;
+    NodeSum<double> a, b;
     for (int q = r0; q < r1; ++q) {
-      a01.add(e[q]);
-      a23.add(e[kBlockSlots + q]);
+      const double2 x = e[2 * q];
+      a.add(x.x);
+      b.add(x.y);
     }
-    out[0] = a01.lo();
-    out[1] = a01.hi();
-    out[2] = a23.lo();
-    out[3] = a23.hi();
+    lo = a.value();
+    hi = b.value();
   }
 };
+
+// Geometry of element e for the block kernels: float from the element record
+// (mixed form), double from the cached [11][E] rows (FP64 form).
+__device__ __forceinline__ void block_geometry(const ElemRecF* __restrict__ rec,
+                                               const double* __restrict__, int64_t, int64_t e,
+                                               float c[3][3], float& inv_det, float& rh) {
+  load_rec_geometry(rec, e, c, inv_det, rh);
+}
+__device__ __forceinline__ void block_geometry(const ElemRecF* __restrict__,
+                                               const double* __restrict__ geom, int64_t E,
+                                               int64_t e, double c[3][3], double& inv_det,
+                                               double& rh) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) c[k][d] = __ldg(geom + (3 * k + d) * E + e);
+  inv_det = __ldg(geom + 9 * E + e);
+  rh = __ldg(geom + 10 * E + e);
+}
+
+// The per-node phase of a block: each distinct node's entries (a contiguous
+// run of sorted positions) summed in a fixed order and added to out [4][N]
+// with one atomic per component. Work item i = (node i / 2, component pair
+// i % 2): two threads per node, so that twice as many threads share the runs
+// and each sums one 64-bit pair.
+template <class R>
+__device__ __forceinline__ void block_node_sums(int64_t N, int64_t b, int64_t off, int nb,
+                                                const int32_t* __restrict__ nodes,
+                                                const uint16_t* __restrict__ runs, const R* buf,
+                                                double* __restrict__ out) {
+  for (int i = threadIdx.x; i < 2 * nb; i += kBlockElems) {
+    const int j = i >> 1, h = i & 1;
+    const int r0 = __ldg(runs + off + b + j), r1 = __ldg(runs + off + b + j + 1);
+    const int64_t v = __ldg(nodes + off + j);
+    double lo, hi;
+    Smem<R>::sum_pair(buf, h, r0, r1, lo, hi);
+    atomicAdd(out + (2 * h) * N + v, lo);
+    atomicAdd(out + (2 * h + 1) * N + v, hi);
+  }
+}
 
 // Shared memory of the forward block kernel (below), and the resident CTAs
 // per SM the compiler must allow (register cap): the float kernel is
@@ -353,18 +418,26 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(PENDING) : "memory");
 }
 
-// Issues the copies of block b's nodal (u, v, w, p) into buf [4][kBlockSlots].
+// Issues the copies of block b's nodal (u, v, w, p) into buf [kBlockSlots][4]
+// (and, with cot, the cotangent into buf [kBlockSlots][8] columns 4..7).
 template <class R>
 __device__ __forceinline__ void stage_block(int64_t N, int64_t b,
                                             const int64_t* __restrict__ node_off,
                                             const int32_t* __restrict__ nodes,
-                                            const R* __restrict__ up, R* buf) {
+                                            const R* __restrict__ up, const R* __restrict__ cot,
+                                            R* buf) {
   const int64_t off = __ldg(node_off + b);
   const int nb = (int)(__ldg(node_off + b + 1) - off);
+  const int stride = cot ? 8 : 4;
   for (int j = threadIdx.x; j < nb; j += kBlockElems) {
     const int64_t v = __ldg(nodes + off + j);
+    R* slot = buf + stride * j;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) cp_async<sizeof(R)>(buf + k * kBlockSlots + j, up + k * N + v);
+    for (int k = 0; k < 4; ++k) cp_async<sizeof(R)>(slot + k, up + k * N + v);
+    if (cot) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) cp_async<sizeof(R)>(slot + 4 + k, cot + k * N + v);
+    }
   }
 }
 
@@ -382,19 +455,19 @@ template <class R, int FLAGS, bool COLOUR = false>
 __global__ void __launch_bounds__(kBlockElems, block_kernel_min_ctas<R>())
     fwd_block_kernel(int64_t N, int64_t E, int64_t n_blocks, const int64_t* __restrict__ node_off,
                      const int32_t* __restrict__ nodes, const uint16_t* __restrict__ runs,
-                     const uint32_t* __restrict__ lmap,
-                     const R* __restrict__ geom, const R* __restrict__ up, ElemParams<R> P,
-                     double* __restrict__ rhs, const int32_t* __restrict__ order = nullptr,
-                     int64_t i0 = 0, int64_t i1 = 0) {
+                     const ElemRecF* __restrict__ rec, const double* __restrict__ geom64,
+                     const R* __restrict__ up, ElemParams<R> P, double* __restrict__ rhs,
+                     const int32_t* __restrict__ order = nullptr, int64_t i0 = 0,
+                     int64_t i1 = 0) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  R* su0 = reinterpret_cast<R*>(smem_raw);  // [4][kBlockSlots] nodal u, v, w, p (even steps)
+  R* su0 = reinterpret_cast<R*>(smem_raw);  // [kBlockSlots][4] nodal u, v, w, p (even steps)
   R* su1 = su0 + 4 * kBlockSlots;            // the same (odd steps)
-  R* sF = su1 + 4 * kBlockSlots;             // [4][kBlockSlots] element entries by slot
+  R* sF = su1 + 4 * kBlockSlots;             // [kBlockSlots][4] element entries by position
   const int tid = threadIdx.x;
   const int64_t first = COLOUR ? i0 : 0, last = COLOUR ? i1 : n_blocks;
   auto block_at = [&](int64_t i) -> int64_t { return COLOUR ? (int64_t)__ldg(order + i) : i; };
   int64_t i = first + blockIdx.x;
-  if (i < last) stage_block(N, block_at(i), node_off, nodes, up, su0);
+  if (i < last) stage_block<R>(N, block_at(i), node_off, nodes, up, nullptr, su0);
   cp_async_commit();
   for (int step = 0; i < last; i += gridDim.x, ++step) {
     R* su = (step & 1) ? su1 : su0;
@@ -402,7 +475,8 @@ __global__ void __launch_bounds__(kBlockElems, block_kernel_min_ctas<R>())
     // the next block's copies go into the other buffer, whose last readers
     // finished before the previous step's middle barrier
     if (i + gridDim.x < last)
-      stage_block(N, block_at(i + gridDim.x), node_off, nodes, up, (step & 1) ? su0 : su1);
+      stage_block<R>(N, block_at(i + gridDim.x), node_off, nodes, up, nullptr,
+                     (step & 1) ? su0 : su1);
     cp_async_commit();
     const int64_t off = node_off[b];
     const int nb = (int)(node_off[b + 1] - off);
@@ -410,36 +484,27 @@ __global__ void __launch_bounds__(kBlockElems, block_kernel_min_ctas<R>())
     __syncthreads();     // ... for every thread; the previous block's sums are done
     const int64_t e = b * kBlockElems + tid;
     if (e < E) {
+      const uint4 lm = load_rec_lmap(rec, e);
+      const uint32_t lmv[4] = {lm.x, lm.y, lm.z, lm.w};
       R u[4][3], p[4];
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
-        const int lc = (int)(__ldg(lmap + a * E + e) >> 16);
-#pragma unroll
-        for (int k = 0; k < 3; ++k) u[a][k] = su[k * kBlockSlots + lc];
-        p[a] = su[3 * kBlockSlots + lc];
+        R q[4];
+        Smem<R>::get4(su, 4, (int)(lmv[a] >> 16), q);
+        u[a][0] = q[0];
+        u[a][1] = q[1];
+        u[a][2] = q[2];
+        p[a] = q[3];
       }
       R c[3][3], inv_det, rh;
-#pragma unroll
-      for (int k = 0; k < 3; ++k)
-#pragma unroll
-        for (int d = 0; d < 3; ++d) c[k][d] = __ldg(geom + (3 * k + d) * E + e);
-      inv_det = __ldg(geom + 9 * E + e);
-      rh = __ldg(geom + 10 * E + e);
+      block_geometry(rec, geom64, E, e, c, inv_det, rh);
       R F[4][4];
       element_rhs<R, FLAGS>(c, inv_det, rh, u, p, P, F);
 #pragma unroll
-      for (int a = 0; a < 4; ++a)
-        Entries<R>::put(sF, (int)(__ldg(lmap + a * E + e) & 0xffffu), F[a]);
+      for (int a = 0; a < 4; ++a) Smem<R>::put4(sF, (int)(lmv[a] & 0xffffu), F[a]);
     }
     __syncthreads();
-    for (int j = tid; j < nb; j += kBlockElems) {
-      const int r0 = __ldg(runs + off + b + j), r1 = __ldg(runs + off + b + j + 1);
-      const int64_t v = __ldg(nodes + off + j);
-      double acc[4];
-      Entries<R>::sum(sF, r0, r1, acc);
-#pragma unroll
-      for (int k = 0; k < 4; ++k) atomicAdd(rhs + k * N + v, acc[k]);
-    }
+    block_node_sums<R>(N, b, off, nb, nodes, runs, sF, rhs);
   }
   cp_async_wait<0>();
 }
@@ -464,53 +529,32 @@ constexpr int block_vjp_min_ctas() {
   return sizeof(R) == 4 ? 2 : 1;
 }
 
-// Issues the copies of block b's nodal (u, v, w, p) and cotangent into
-// buf [8][kBlockSlots] (the cotangent at rows 4..7).
-template <class R>
-__device__ __forceinline__ void stage_block_vjp(int64_t N, int64_t b,
-                                                const int64_t* __restrict__ node_off,
-                                                const int32_t* __restrict__ nodes,
-                                                const R* __restrict__ up,
-                                                const R* __restrict__ cot, R* buf) {
-  const int64_t off = __ldg(node_off + b);
-  const int nb = (int)(__ldg(node_off + b + 1) - off);
-  for (int j = threadIdx.x; j < nb; j += kBlockElems) {
-    const int64_t v = __ldg(nodes + off + j);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      cp_async<sizeof(R)>(buf + k * kBlockSlots + j, up + k * N + v);
-      cp_async<sizeof(R)>(buf + (4 + k) * kBlockSlots + j, cot + k * N + v);
-    }
-  }
-}
-
 template <class R, int FLAGS, bool COLOUR = false>
 __global__ void __launch_bounds__(kBlockElems, block_vjp_min_ctas<R>())
     vjp_block_kernel(int64_t N, int64_t E, int64_t n_blocks, const int64_t* __restrict__ node_off,
                      const int32_t* __restrict__ nodes, const uint16_t* __restrict__ runs,
-                     const uint32_t* __restrict__ lmap,
-                     const R* __restrict__ geom, const R* __restrict__ up,
-                     const R* __restrict__ cot, ElemParams<R> P, double* __restrict__ grad,
-                     const int32_t* __restrict__ order, int64_t i0, int64_t i1) {
+                     const ElemRecF* __restrict__ rec, const double* __restrict__ geom64,
+                     const R* __restrict__ up, const R* __restrict__ cot, ElemParams<R> P,
+                     double* __restrict__ grad, const int32_t* __restrict__ order, int64_t i0,
+                     int64_t i1) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  // two staging buffers [8][kBlockSlots]: u, v, w, p, then the cotangent
+  // two staging buffers [kBlockSlots][8]: u, v, w, p, then the cotangent
   R* sb0 = reinterpret_cast<R*>(smem_raw);
   R* sb1 = sb0 + 8 * kBlockSlots;
   const int tid = threadIdx.x;
   const int64_t first = COLOUR ? i0 : 0, last = COLOUR ? i1 : n_blocks;
   auto block_at = [&](int64_t i) -> int64_t { return COLOUR ? (int64_t)__ldg(order + i) : i; };
   int64_t i = first + blockIdx.x;
-  if (i < last) stage_block_vjp(N, block_at(i), node_off, nodes, up, cot, sb0);
+  if (i < last) stage_block<R>(N, block_at(i), node_off, nodes, up, cot, sb0);
   cp_async_commit();
   for (int step = 0; i < last; i += gridDim.x, ++step) {
     R* su = (step & 1) ? sb1 : sb0;
-    R* sw = su + 4 * kBlockSlots;
     const int64_t b = block_at(i);
     // the other buffer was last read (as entries) in the previous step's sums,
     // which every thread finished before the previous step's last barrier
     if (i + gridDim.x < last)
-      stage_block_vjp(N, block_at(i + gridDim.x), node_off, nodes, up, cot,
-                      (step & 1) ? sb0 : sb1);
+      stage_block<R>(N, block_at(i + gridDim.x), node_off, nodes, up, cot,
+                     (step & 1) ? sb0 : sb1);
     cp_async_commit();
     const int64_t off = node_off[b];
     const int nb = (int)(node_off[b + 1] - off);
@@ -518,43 +562,37 @@ __global__ void __launch_bounds__(kBlockElems, block_vjp_min_ctas<R>())
     __syncthreads();
     const int64_t e = b * kBlockElems + tid;
     R gu[4][3], gp[4];
+    uint4 lm = make_uint4(0u, 0u, 0u, 0u);
     if (e < E) {
+      lm = load_rec_lmap(rec, e);
+      const uint32_t lmv[4] = {lm.x, lm.y, lm.z, lm.w};
       R u[4][3], p[4], w[4][4];
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
-        const int lc = (int)(__ldg(lmap + a * E + e) >> 16);
-#pragma unroll
-        for (int k = 0; k < 3; ++k) u[a][k] = su[k * kBlockSlots + lc];
-        p[a] = su[3 * kBlockSlots + lc];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) w[a][k] = sw[k * kBlockSlots + lc];
+        const int lc = (int)(lmv[a] >> 16);
+        R q[4];
+        Smem<R>::get4(su, 8, lc, q);
+        u[a][0] = q[0];
+        u[a][1] = q[1];
+        u[a][2] = q[2];
+        p[a] = q[3];
+        Smem<R>::get4(su + 4, 8, lc, w[a]);
       }
       R c[3][3], inv_det, rh;
-#pragma unroll
-      for (int k = 0; k < 3; ++k)
-#pragma unroll
-        for (int d = 0; d < 3; ++d) c[k][d] = __ldg(geom + (3 * k + d) * E + e);
-      inv_det = __ldg(geom + 9 * E + e);
-      rh = __ldg(geom + 10 * E + e);
+      block_geometry(rec, geom64, E, e, c, inv_det, rh);
       element_vjp<R, FLAGS>(c, inv_det, rh, u, p, w, P, gu, gp);
     }
     __syncthreads();  // the staged values are no longer read: reuse su for the entries
     if (e < E) {
+      const uint32_t lmv[4] = {lm.x, lm.y, lm.z, lm.w};
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
         const R g4[4] = {gu[a][0], gu[a][1], gu[a][2], gp[a]};
-        Entries<R>::put(su, (int)(__ldg(lmap + a * E + e) & 0xffffu), g4);
+        Smem<R>::put4(su, (int)(lmv[a] & 0xffffu), g4);
       }
     }
     __syncthreads();
-    for (int j = tid; j < nb; j += kBlockElems) {
-      const int r0 = __ldg(runs + off + b + j), r1 = __ldg(runs + off + b + j + 1);
-      const int64_t v = __ldg(nodes + off + j);
-      double acc[4];
-      Entries<R>::sum(su, r0, r1, acc);
-#pragma unroll
-      for (int k = 0; k < 4; ++k) atomicAdd(grad + k * N + v, acc[k]);
-    }
+    block_node_sums<R>(N, b, off, nb, nodes, runs, su, grad);
     __syncthreads();  // the sums have read su before it is staged into again
   }
   cp_async_wait<0>();

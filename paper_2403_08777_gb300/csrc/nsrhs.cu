@@ -51,7 +51,9 @@ struct nsrhs_mesh {
   // it depends on the mesh only, and one streamed 88-byte record costs far
   // less on GB300 than the ~40 FP64 instructions that recompute it.
   double* geom = nullptr;
-  float* geom_f = nullptr;    // the same rounded to float, for the mixed form
+  // Per-element records [E] (blocks.cuh): the same geometry rounded to float
+  // (the mixed form) and the block map of the block kernels.
+  nsrhs::ElemRecF* rec = nullptr;
   // Element blocks (blocks.cuh): elements are stored in Morton order of
   // their centroids; per block of kBlockElems elements its distinct nodes,
   // their contribution runs and the local connectivity.
@@ -59,7 +61,6 @@ struct nsrhs_mesh {
   int64_t* blk_node_off = nullptr;  // [n_blocks + 1]
   int32_t* blk_nodes = nullptr;     // [blk_node_off[n_blocks]]
   uint16_t* blk_runs = nullptr;     // [blk_node_off[n_blocks] + n_blocks]
-  uint32_t* blk_lmap = nullptr;     // [4][E] (distinct-node index << 16) | sorted position
   double* inv_mass = nullptr;       // [N] 1 / lumped mass
   double* mass = nullptr;           // [N] lumped mass sum_e V_e / 4
   // Colour-major copy for the COLOUR scatter (colour.cuh), built when the
@@ -68,7 +69,7 @@ struct nsrhs_mesh {
   std::vector<int64_t> col_off;
   int32_t* col_conn = nullptr;      // [4][E]
   double* col_geom = nullptr;       // [kGeomRows][E]
-  float* col_geom_f = nullptr;      // [kGeomRows][E]
+  nsrhs::ElemRecF* col_rec = nullptr;  // [E] records in colour-major order
   uint8_t* colour = nullptr;        // [E] colour of each element (Morton order)
   int32_t* elem_order = nullptr;    // [E] caller's index of each element (Morton order)
   // Block colouring for the BLOCK_COLOUR scatter: block colour k is the
@@ -362,10 +363,11 @@ nsrhs_status check_scratch_address(CheckPartial** out) {
 }
 
 // Cached element geometry (setup): double cofactors, 1/detJ and detJ^(-1/3)
-// of every element, and their float roundings.
+// of every element, and their float roundings in the element records (whose
+// block map the block planning fills in afterwards).
 __global__ void geometry_kernel(int64_t N, int64_t E, const double* __restrict__ coords,
                                 const int32_t* __restrict__ conn, double* __restrict__ geom,
-                                float* __restrict__ geom_f) {
+                                nsrhs::ElemRecF* __restrict__ rec) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E;
        e += (int64_t)gridDim.x * blockDim.x) {
     double X[4][3];
@@ -384,11 +386,16 @@ __global__ void geometry_kernel(int64_t N, int64_t E, const double* __restrict__
       for (int d = 0; d < 3; ++d) g[3 * k + d] = c[k][d];
     g[9] = inv_det;
     g[10] = rh;
+    nsrhs::ElemRecF r;
 #pragma unroll
     for (int q = 0; q < kGeomRows; ++q) {
       geom[q * E + e] = g[q];
-      geom_f[q * E + e] = __double2float_rn(g[q]);
+      r.g[q] = __double2float_rn(g[q]);
     }
+    r.g[11] = 0.0f;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) r.lmap[a] = 0u;
+    rec[e] = r;
   }
 }
 
@@ -590,7 +597,7 @@ __global__ void __launch_bounds__(kThreads)
 template <int FLAGS, bool COLOUR>
 __device__ __forceinline__ void fwd_mixed_element(int64_t N, int64_t E, int64_t e,
                                                   const int32_t* __restrict__ conn,
-                                                  const float* __restrict__ geom_f,
+                                                  const nsrhs::ElemRecF* __restrict__ rec,
                                                   const float* __restrict__ up,
                                                   const ElemParams<float>& P,
                                                   double* __restrict__ rhs) {
@@ -605,7 +612,7 @@ __device__ __forceinline__ void fwd_mixed_element(int64_t N, int64_t E, int64_t 
     p[a] = ldg(up + 3 * N + v[a]);
   }
   float c[3][3], inv_det, rh;
-  load_geometry(geom_f, E, e, c, inv_det, rh);
+  nsrhs::load_rec_geometry(rec, e, c, inv_det, rh);
   float F[4][4];
   nsrhs::element_rhs<float, FLAGS>(c, inv_det, rh, u, p, P, F);
 #pragma unroll
@@ -617,22 +624,22 @@ __device__ __forceinline__ void fwd_mixed_element(int64_t N, int64_t E, int64_t 
 template <int FLAGS>
 __global__ void __launch_bounds__(kThreads)
     fwd_mixed_atomic_kernel(int64_t N, int64_t E, const int32_t* __restrict__ conn,
-                            const float* __restrict__ geom_f, const float* __restrict__ up,
+                            const nsrhs::ElemRecF* __restrict__ rec, const float* __restrict__ up,
                             ElemParams<float> P, double* __restrict__ rhs) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E;
        e += (int64_t)gridDim.x * blockDim.x)
-    fwd_mixed_element<FLAGS, false>(N, E, e, conn, geom_f, up, P, rhs);
+    fwd_mixed_element<FLAGS, false>(N, E, e, conn, rec, up, P, rhs);
 }
 
 template <int FLAGS>
 __global__ void __launch_bounds__(kThreads)
     fwd_mixed_colour_kernel(int64_t N, int64_t E, int64_t e0, int64_t e1,
-                            const int32_t* __restrict__ conn, const float* __restrict__ geom_f,
-                            const float* __restrict__ up, ElemParams<float> P,
-                            double* __restrict__ rhs) {
+                            const int32_t* __restrict__ conn,
+                            const nsrhs::ElemRecF* __restrict__ rec, const float* __restrict__ up,
+                            ElemParams<float> P, double* __restrict__ rhs) {
   for (int64_t e = e0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < e1;
        e += (int64_t)gridDim.x * blockDim.x)
-    fwd_mixed_element<FLAGS, true>(N, E, e, conn, geom_f, up, P, rhs);
+    fwd_mixed_element<FLAGS, true>(N, E, e, conn, rec, up, P, rhs);
 }
 
 // FP64 vector-Jacobian product of element e: gather the cotangent at the
@@ -711,7 +718,7 @@ __global__ void __launch_bounds__(kThreads, NSRHS_VJP_COLOUR_MIN_CTAS)
 template <int FLAGS, bool COLOUR>
 __device__ __forceinline__ void vjp_mixed_element(int64_t N, int64_t E, int64_t e,
                                                   const int32_t* __restrict__ conn,
-                                                  const float* __restrict__ geom_f,
+                                                  const nsrhs::ElemRecF* __restrict__ rec,
                                                   const float* __restrict__ up,
                                                   const float* __restrict__ cot,
                                                   const ElemParams<float>& P,
@@ -729,7 +736,7 @@ __device__ __forceinline__ void vjp_mixed_element(int64_t N, int64_t E, int64_t 
     for (int k = 0; k < 4; ++k) w[a][k] = ldg(cot + k * N + v[a]);
   }
   float c[3][3], inv_det, rh;
-  load_geometry(geom_f, E, e, c, inv_det, rh);
+  nsrhs::load_rec_geometry(rec, e, c, inv_det, rh);
   float gu[4][3], gp[4];
   nsrhs::element_vjp<float, FLAGS>(c, inv_det, rh, u, p, w, P, gu, gp);
 #pragma unroll
@@ -744,33 +751,34 @@ __device__ __forceinline__ void vjp_mixed_element(int64_t N, int64_t E, int64_t 
 template <int FLAGS>
 __global__ void __launch_bounds__(kThreads)
     vjp_mixed_atomic_kernel(int64_t N, int64_t E, const int32_t* __restrict__ conn,
-                            const float* __restrict__ geom_f, const float* __restrict__ up,
+                            const nsrhs::ElemRecF* __restrict__ rec, const float* __restrict__ up,
                             const float* __restrict__ cot, ElemParams<float> P,
                             double* __restrict__ grad) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E;
        e += (int64_t)gridDim.x * blockDim.x)
-    vjp_mixed_element<FLAGS, false>(N, E, e, conn, geom_f, up, cot, P, grad);
+    vjp_mixed_element<FLAGS, false>(N, E, e, conn, rec, up, cot, P, grad);
 }
 
 template <int FLAGS>
 __global__ void __launch_bounds__(kThreads)
     vjp_mixed_colour_kernel(int64_t N, int64_t E, int64_t e0, int64_t e1,
-                            const int32_t* __restrict__ conn, const float* __restrict__ geom_f,
-                            const float* __restrict__ up, const float* __restrict__ cot,
-                            ElemParams<float> P, double* __restrict__ grad) {
+                            const int32_t* __restrict__ conn,
+                            const nsrhs::ElemRecF* __restrict__ rec, const float* __restrict__ up,
+                            const float* __restrict__ cot, ElemParams<float> P,
+                            double* __restrict__ grad) {
   for (int64_t e = e0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < e1;
        e += (int64_t)gridDim.x * blockDim.x)
-    vjp_mixed_element<FLAGS, true>(N, E, e, conn, geom_f, up, cot, P, grad);
+    vjp_mixed_element<FLAGS, true>(N, E, e, conn, rec, up, cot, P, grad);
 }
 
 // The RHS and the vector-Jacobian product at the same state in one pass
 // (element_rhs_vjp): one gather of (u, p) and the cotangent, one geometry
 // read, the forward intermediates computed once; R = double (FP64) or float
 // (mixed: float arithmetic, double accumulation by integer widening).
-template <class R, int FLAGS>
+template <class R, int FLAGS, class G>
 __global__ void __launch_bounds__(kThreads, NSRHS_VJP_MIN_CTAS)
     rhs_vjp_atomic_kernel(int64_t N, int64_t E, const int32_t* __restrict__ conn,
-                          const R* __restrict__ geom, const R* __restrict__ up,
+                          const G* __restrict__ geom, const R* __restrict__ up,
                           const R* __restrict__ cot, ElemParams<R> P, double* __restrict__ rhs,
                           double* __restrict__ grad) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E;
@@ -788,7 +796,8 @@ __global__ void __launch_bounds__(kThreads, NSRHS_VJP_MIN_CTAS)
       for (int k = 0; k < 4; ++k) w[a][k] = ldg(cot + k * N + v[a]);
     }
     R c[3][3], inv_det, rh;
-    load_geometry(geom, E, e, c, inv_det, rh);
+    nsrhs::block_geometry(reinterpret_cast<const nsrhs::ElemRecF*>(geom),
+                          reinterpret_cast<const double*>(geom), E, e, c, inv_det, rh);
     R F[4][4], gu[4][3], gp[4];
     nsrhs::element_rhs_vjp<R, FLAGS>(c, inv_det, rh, u, p, w, P, F, gu, gp);
 #pragma unroll
@@ -978,7 +987,6 @@ nsrhs_status build_blocks(nsrhs_mesh* m, cudaStream_t s) {
   DevBuf counts, tmp;
   NSRHS_TRY(counts.alloc((nb + 1) * sizeof(int64_t)));
   if ((st = mesh_alloc(m, &m->blk_node_off, (size_t)nb + 1)) != NSRHS_OK) return st;
-  if ((st = mesh_alloc(m, &m->blk_lmap, 4 * (size_t)E)) != NSRHS_OK) return st;
   // pass 0: distinct nodes per block
   nsrhs::block_plan_kernel<<<(unsigned)nb, nsrhs::kBlockElems, 0, s>>>(
       0, E, m->conn, counts.as<int64_t>(), nullptr, nullptr, nullptr, nullptr);
@@ -999,7 +1007,7 @@ nsrhs_status build_blocks(nsrhs_mesh* m, cudaStream_t s) {
   if ((st = mesh_alloc(m, &m->blk_nodes, (size_t)total)) != NSRHS_OK) return st;
   if ((st = mesh_alloc(m, &m->blk_runs, (size_t)(total + nb))) != NSRHS_OK) return st;
   nsrhs::block_plan_kernel<<<(unsigned)nb, nsrhs::kBlockElems, 0, s>>>(
-      1, E, m->conn, nullptr, m->blk_node_off, m->blk_nodes, m->blk_runs, m->blk_lmap);
+      1, E, m->conn, nullptr, m->blk_node_off, m->blk_nodes, m->blk_runs, m->rec);
   NSRHS_TRY(cudaGetLastError());
   return NSRHS_OK;
 }
@@ -1071,15 +1079,15 @@ nsrhs_status build_colouring(nsrhs_mesh* m, cudaStream_t s) {
                                             8, s));
   if ((st = mesh_alloc(m, &m->col_conn, 4 * (size_t)E)) != NSRHS_OK) return st;
   if ((st = mesh_alloc(m, &m->col_geom, kGeomRows * (size_t)E)) != NSRHS_OK) return st;
-  if ((st = mesh_alloc(m, &m->col_geom_f, kGeomRows * (size_t)E)) != NSRHS_OK) return st;
+  if ((st = mesh_alloc(m, &m->col_rec, (size_t)E)) != NSRHS_OK) return st;
   const int32_t* perm = ids_sorted.as<int32_t>();
   nsrhs::permute_rows_kernel<int32_t><<<grid, kThreads, 0, s>>>(4, E, perm, m->conn, m->col_conn);
   NSRHS_TRY(cudaGetLastError());
   nsrhs::permute_rows_kernel<double><<<grid, kThreads, 0, s>>>(kGeomRows, E, perm, m->geom,
                                                                m->col_geom);
   NSRHS_TRY(cudaGetLastError());
-  nsrhs::permute_rows_kernel<float><<<grid, kThreads, 0, s>>>(kGeomRows, E, perm, m->geom_f,
-                                                              m->col_geom_f);
+  nsrhs::permute_rows_kernel<nsrhs::ElemRecF><<<grid, kThreads, 0, s>>>(1, E, perm, m->rec,
+                                                                        m->col_rec);
   NSRHS_TRY(cudaGetLastError());
   NSRHS_TRY(cudaStreamSynchronize(s));
   m->info.n_colours = n_col;
@@ -1205,9 +1213,9 @@ nsrhs_status mesh_build(nsrhs_mesh* m, const double* coords, const int32_t* conn
   if ((st = morton_reorder(m, m->elem_order, s)) != NSRHS_OK) return st;
   // Cached geometry (double and float) of every element.
   if ((st = mesh_alloc(m, &m->geom, kGeomRows * (size_t)E)) != NSRHS_OK) return st;
-  if ((st = mesh_alloc(m, &m->geom_f, kGeomRows * (size_t)E)) != NSRHS_OK) return st;
+  if ((st = mesh_alloc(m, &m->rec, (size_t)E)) != NSRHS_OK) return st;
   geometry_kernel<<<grid_for(E, m->device, 8), kThreads, 0, s>>>(N, E, m->coords, m->conn,
-                                                                 m->geom, m->geom_f);
+                                                                 m->geom, m->rec);
   NSRHS_TRY(cudaGetLastError());
   if ((st = build_blocks(m, s)) != NSRHS_OK) return st;
   if (opts.colour && (st = build_colouring(m, s)) != NSRHS_OK) return st;
@@ -1345,7 +1353,7 @@ nsrhs_status nsrhs_assemble(const nsrhs_mesh* m, const nsrhs_params* p, const vo
           err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
           if (err == cudaSuccess)
             kern<<<grid, nsrhs::kBlockElems, smem, s>>>(
-                N, E, nb, m->blk_node_off, m->blk_nodes, m->blk_runs, m->blk_lmap,
+                N, E, nb, m->blk_node_off, m->blk_nodes, m->blk_runs, m->rec,
                 m->geom, (const double*)up, P, rhs, m->bcol_order, i0, i1);
         });
       } else {
@@ -1356,8 +1364,8 @@ nsrhs_status nsrhs_assemble(const nsrhs_mesh* m, const nsrhs_params* p, const vo
           err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
           if (err == cudaSuccess)
             kern<<<grid, nsrhs::kBlockElems, smem, s>>>(
-                N, E, nb, m->blk_node_off, m->blk_nodes, m->blk_runs, m->blk_lmap,
-                m->geom_f, (const float*)up, P, rhs, m->bcol_order, i0, i1);
+                N, E, nb, m->blk_node_off, m->blk_nodes, m->blk_runs, m->rec,
+                nullptr, (const float*)up, P, rhs, m->bcol_order, i0, i1);
         });
       }
       if (err == cudaSuccess) err = cudaGetLastError();
@@ -1379,7 +1387,7 @@ nsrhs_status nsrhs_assemble(const nsrhs_mesh* m, const nsrhs_params* p, const vo
         auto P = elem_params<float>(p);
         with_flags(flags, [&](auto fl) {
           fwd_mixed_colour_kernel<decltype(fl)::value><<<grid, kThreads, 0, s>>>(
-              N, E, e0, e1, m->col_conn, m->col_geom_f, (const float*)up, P, rhs);
+              N, E, e0, e1, m->col_conn, m->col_rec, (const float*)up, P, rhs);
         });
       }
       NSRHS_TRY(cudaGetLastError());
@@ -1404,7 +1412,7 @@ nsrhs_status nsrhs_assemble(const nsrhs_mesh* m, const nsrhs_params* p, const vo
         err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err == cudaSuccess)
           kern<<<grid, nsrhs::kBlockElems, smem, s>>>(N, E, nb, m->blk_node_off, m->blk_nodes,
-                                                      m->blk_runs, m->blk_lmap,
+                                                      m->blk_runs, m->rec,
                                                       m->geom, (const double*)up, P, rhs,
                                                       nullptr, 0, 0);
       });
@@ -1416,8 +1424,8 @@ nsrhs_status nsrhs_assemble(const nsrhs_mesh* m, const nsrhs_params* p, const vo
         err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err == cudaSuccess)
           kern<<<grid, nsrhs::kBlockElems, smem, s>>>(N, E, nb, m->blk_node_off, m->blk_nodes,
-                                                      m->blk_runs, m->blk_lmap,
-                                                      m->geom_f, (const float*)up, P, rhs,
+                                                      m->blk_runs, m->rec,
+                                                      nullptr, (const float*)up, P, rhs,
                                                       nullptr, 0, 0);
       });
     }
@@ -1435,7 +1443,7 @@ nsrhs_status nsrhs_assemble(const nsrhs_mesh* m, const nsrhs_params* p, const vo
     auto P = elem_params<float>(p);
     with_flags(flags, [&](auto fl) {
       fwd_mixed_atomic_kernel<decltype(fl)::value>
-          <<<grid, kThreads, 0, s>>>(N, E, m->conn, m->geom_f, (const float*)up, P, rhs);
+          <<<grid, kThreads, 0, s>>>(N, E, m->conn, m->rec, (const float*)up, P, rhs);
     });
   }
   return cuda_status(cudaGetLastError());
@@ -1481,12 +1489,12 @@ nsrhs_status nsrhs_assemble_vjp(const nsrhs_mesh* m, const nsrhs_params* p, cons
       const int64_t i0 = ranges[k], i1 = ranges[k + 1];
       const unsigned grid = (unsigned)std::max<int64_t>(
           1, std::min<int64_t>(i1 - i0, (int64_t)sm_count(m->device) * kBlockCtasPerSm));
-      auto launch = [&](auto kern, size_t smem, const auto* geom, const auto* u, const auto* c,
+      auto launch = [&](auto kern, size_t smem, const double* geom, const auto* u, const auto* c,
                         const auto& P) {
         err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err == cudaSuccess)
           kern<<<grid, nsrhs::kBlockElems, smem, s>>>(
-              N, E, nb, m->blk_node_off, m->blk_nodes, m->blk_runs, m->blk_lmap,
+              N, E, nb, m->blk_node_off, m->blk_nodes, m->blk_runs, m->rec,
               geom, u, c, P, grad, coloured ? m->bcol_order : nullptr, i0, i1);
       };
       if (p->precision == NSRHS_FP64) {
@@ -1507,10 +1515,10 @@ nsrhs_status nsrhs_assemble_vjp(const nsrhs_mesh* m, const nsrhs_params* p, cons
           constexpr int F = decltype(fl)::value;
           if (coloured)
             launch(nsrhs::vjp_block_kernel<float, F, true>, nsrhs::block_vjp_smem<float, true>(),
-                   m->geom_f, (const float*)up, (const float*)cot, P);
+                   nullptr, (const float*)up, (const float*)cot, P);
           else
             launch(nsrhs::vjp_block_kernel<float, F, false>, nsrhs::block_vjp_smem<float, false>(),
-                   m->geom_f, (const float*)up, (const float*)cot, P);
+                   nullptr, (const float*)up, (const float*)cot, P);
         });
       }
       if (err == cudaSuccess) err = cudaGetLastError();
@@ -1532,7 +1540,7 @@ nsrhs_status nsrhs_assemble_vjp(const nsrhs_mesh* m, const nsrhs_params* p, cons
         auto P = elem_params<float>(p);
         with_flags(formulation_flags(p), [&](auto fl) {
           vjp_mixed_colour_kernel<decltype(fl)::value><<<grid, kThreads, 0, s>>>(
-              N, E, e0, e1, m->col_conn, m->col_geom_f, (const float*)up, (const float*)cot, P,
+              N, E, e0, e1, m->col_conn, m->col_rec, (const float*)up, (const float*)cot, P,
               grad);
         });
       }
@@ -1551,7 +1559,7 @@ nsrhs_status nsrhs_assemble_vjp(const nsrhs_mesh* m, const nsrhs_params* p, cons
     auto P = elem_params<float>(p);
     with_flags(formulation_flags(p), [&](auto fl) {
       vjp_mixed_atomic_kernel<decltype(fl)::value><<<grid, kThreads, 0, s>>>(
-          N, E, m->conn, m->geom_f, (const float*)up, (const float*)cot, P, grad);
+          N, E, m->conn, m->rec, (const float*)up, (const float*)cot, P, grad);
     });
   }
   return cuda_status(cudaGetLastError());
@@ -1575,14 +1583,14 @@ nsrhs_status nsrhs_assemble_rhs_vjp(const nsrhs_mesh* m, const nsrhs_params* p, 
   if (p->precision == NSRHS_FP64) {
     auto P = elem_params<double>(p);
     with_flags(formulation_flags(p), [&](auto fl) {
-      rhs_vjp_atomic_kernel<double, decltype(fl)::value><<<grid, kThreads, 0, s>>>(
+      rhs_vjp_atomic_kernel<double, decltype(fl)::value, double><<<grid, kThreads, 0, s>>>(
           N, E, m->conn, m->geom, (const double*)up, (const double*)cot, P, rhs, grad);
     });
   } else {
     auto P = elem_params<float>(p);
     with_flags(formulation_flags(p), [&](auto fl) {
-      rhs_vjp_atomic_kernel<float, decltype(fl)::value><<<grid, kThreads, 0, s>>>(
-          N, E, m->conn, m->geom_f, (const float*)up, (const float*)cot, P, rhs, grad);
+      rhs_vjp_atomic_kernel<float, decltype(fl)::value, nsrhs::ElemRecF>
+          <<<grid, kThreads, 0, s>>>(N, E, m->conn, m->rec, (const float*)up, (const float*)cot, P, rhs, grad);
     });
   }
   return cuda_status(cudaGetLastError());
