@@ -148,18 +148,24 @@ __global__ void permute_conn_kernel(int64_t E, const int32_t* __restrict__ in,
 // Per block: sort its (node << 16 | slot) keys (slot = 4 * element-in-block
 // + local node), find the distinct nodes.
 // pass 0 writes counts[b] = number of distinct nodes;
-// pass 1 (node_off = exclusive sum of counts) writes
-//   nodes[node_off[b] + j]        j-th distinct node (ascending)
-//   runs[node_off[b] + b + j]     first sorted position of node j (runs[.. + n] = #valid)
-//   rec[e].lmap[a]                (distinct-node index << 16) | sorted position of
+// pass 1 (node_off = exclusive sum of counts) ranks the block's distinct
+// nodes by the length of their run of contributions, longest first (ties by
+// node), so that the per-node phase hands each warp runs of similar length,
+// and writes
+//   nodes[node_off[b] + r]        the distinct node of rank r
+//   runs[node_off[b] + r]         (first sorted position << 16) | run length of rank r
+//   rec[e].lmap[a]                (rank of the node << 16) | sorted position of
 //                                 (element e, local node a)
 __global__ void __launch_bounds__(kBlockElems)
     block_plan_kernel(int pass, int64_t E, const int32_t* __restrict__ conn,
                       int64_t* __restrict__ counts, const int64_t* __restrict__ node_off,
-                      int32_t* __restrict__ nodes, uint16_t* __restrict__ runs,
+                      int32_t* __restrict__ nodes, uint32_t* __restrict__ runs,
                       ElemRecF* __restrict__ rec) {
   __shared__ unsigned long long key[kBlockSlots];
   __shared__ int part[kBlockElems];
+  __shared__ uint16_t start[kBlockSlots + 1];  // first sorted position of distinct node u
+  __shared__ uint32_t order[kBlockSlots];      // (kBlockSlots - run length) << 16 | u
+  __shared__ uint16_t rank[kBlockSlots];
   const int tid = threadIdx.x;
   const int64_t b = blockIdx.x;
   const int64_t e0 = b * kBlockElems;
@@ -211,28 +217,60 @@ __global__ void __launch_bounds__(kBlockElems)
     return;
   }
   const int64_t off = node_off[b];
+  // distinct index u in ascending node order, and each node's first position
   int u = part[tid] - local - 1;  // distinct index before this thread's first position
-  int n_valid_here = 0;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int i = 4 * tid + r;
+    if (key[i] == ~0ull) continue;
+    u += flag[r];
+    if (flag[r]) start[u] = (uint16_t)i;
+  }
+  if (tid == 0) {
+    // the number of valid positions = elements in the block * 4
+    const int64_t ne = (E - e0) < kBlockElems ? (E - e0) : kBlockElems;
+    start[n_distinct] = (uint16_t)(4 * ne);
+  }
+  __syncthreads();
+  for (int v = tid; v < kBlockSlots; v += kBlockElems)
+    order[v] = v < n_distinct
+                   ? ((uint32_t)(kBlockSlots - (start[v + 1] - start[v])) << 16) | (uint32_t)v
+                   : 0xffffffffu;
+  __syncthreads();
+  // bitonic sort of order[], ascending: longest runs first
+  for (int k = 2; k <= kBlockSlots; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = tid; i < kBlockSlots; i += kBlockElems) {
+        const int ixj = i ^ j;
+        if (ixj > i) {
+          const uint32_t a = order[i], c = order[ixj];
+          const bool up = (i & k) == 0;
+          if ((a > c) == up) {
+            order[i] = c;
+            order[ixj] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  for (int r = tid; r < n_distinct; r += kBlockElems) {
+    const int v = (int)(order[r] & 0xffffu);
+    const int s0 = start[v], len = start[v + 1] - s0;
+    rank[v] = (uint16_t)r;
+    nodes[off + r] = (int32_t)(key[s0] >> 16);
+    runs[off + r] = ((uint32_t)s0 << 16) | (uint32_t)len;
+  }
+  __syncthreads();
+  u = part[tid] - local - 1;
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
     const int i = 4 * tid + r;
     const unsigned long long kk = key[i];
     if (kk == ~0ull) continue;
-    ++n_valid_here;
     u += flag[r];
     const int slot = (int)(kk & 0xffffull);
-    if (flag[r]) {
-      nodes[off + u] = (int32_t)(kk >> 16);
-      runs[off + b + u] = (uint16_t)i;
-    }
-    rec[e0 + (slot >> 2)].lmap[slot & 3] = ((uint32_t)u << 16) | (uint32_t)i;
+    rec[e0 + (slot >> 2)].lmap[slot & 3] = ((uint32_t)rank[u] << 16) | (uint32_t)i;
   }
-  // number of valid positions = elements in the block * 4
-  if (tid == 0) {
-    const int64_t ne = (E - e0) < kBlockElems ? (E - e0) : kBlockElems;
-    runs[off + b + n_distinct] = (uint16_t)(4 * ne);
-  }
-  (void)n_valid_here;
 }
 
 
@@ -281,13 +319,13 @@ struct NodeSumF32x2 {
     c = f32x2_add(c, f32x2_add(f32x2_sub(s, f32x2_sub(t, bp)), f32x2_sub(x, bp)));
     s = t;
   }
-  // one per node and component: the hardware conversion (exact) is cheaper
-  // here than the integer widening used per entry elsewhere
+  // the sum s + c in double: both widened exactly with integer operations,
+  // one double addition (the FP64 pipe is 1/64 of the FP32 rate)
   __device__ __forceinline__ double lo() const {
-    return (double)f32x2_lo(s) + (double)f32x2_lo(c);
+    return widen_f32(f32x2_lo(s)) + widen_f32(f32x2_lo(c));
   }
   __device__ __forceinline__ double hi() const {
-    return (double)f32x2_hi(s) + (double)f32x2_hi(c);
+    return widen_f32(f32x2_hi(s)) + widen_f32(f32x2_hi(c));
   }
 };
 
@@ -367,19 +405,76 @@ __device__ __forceinline__ void block_geometry(const ElemRecF* __restrict__,
   rh = __ldg(geom + 10 * E + e);
 }
 
+// A thread's element record for the block kernels, loaded one block ahead
+// (issued before the per-node phase of the current block, so that its
+// latency is hidden behind that phase and the barrier). AHEAD = 2: the whole
+// float record (geometry and block map); AHEAD = 1: the block map only, the
+// geometry read when the element is computed (measured: the mixed forward,
+// capped at 64 registers, is faster with 1; the adjoint with 2). For R =
+// double the FP64 geometry always comes from the cached double rows.
+template <class R, int AHEAD>
+struct RecAhead;
+template <>
+struct RecAhead<float, 2> {
+  float4 q0, q1, q2;
+  uint4 lm;
+  __device__ __forceinline__ void load(const ElemRecF* __restrict__ rec, int64_t e) {
+    const float4* r = reinterpret_cast<const float4*>(rec + e);
+    q0 = __ldg(r);
+    q1 = __ldg(r + 1);
+    q2 = __ldg(r + 2);
+    lm = __ldg(reinterpret_cast<const uint4*>(rec + e) + 3);
+  }
+  __device__ __forceinline__ void geometry(const ElemRecF* __restrict__, const double* __restrict__,
+                                           int64_t, int64_t, float c[3][3], float& inv_det,
+                                           float& rh) const {
+    c[0][0] = q0.x; c[0][1] = q0.y; c[0][2] = q0.z;
+    c[1][0] = q0.w; c[1][1] = q1.x; c[1][2] = q1.y;
+    c[2][0] = q1.z; c[2][1] = q1.w; c[2][2] = q2.x;
+    inv_det = q2.y;
+    rh = q2.z;
+  }
+};
+template <>
+struct RecAhead<float, 1> {
+  uint4 lm;
+  __device__ __forceinline__ void load(const ElemRecF* __restrict__ rec, int64_t e) {
+    lm = load_rec_lmap(rec, e);
+  }
+  __device__ __forceinline__ void geometry(const ElemRecF* __restrict__ rec,
+                                           const double* __restrict__, int64_t, int64_t e,
+                                           float c[3][3], float& inv_det, float& rh) const {
+    load_rec_geometry(rec, e, c, inv_det, rh);
+  }
+};
+template <int AHEAD>
+struct RecAhead<double, AHEAD> {
+  uint4 lm;
+  __device__ __forceinline__ void load(const ElemRecF* __restrict__ rec, int64_t e) {
+    lm = load_rec_lmap(rec, e);
+  }
+  __device__ __forceinline__ void geometry(const ElemRecF* __restrict__,
+                                           const double* __restrict__ geom, int64_t E, int64_t e,
+                                           double c[3][3], double& inv_det, double& rh) const {
+    block_geometry(nullptr, geom, E, e, c, inv_det, rh);
+  }
+};
+
 // The per-node phase of a block: each distinct node's entries (a contiguous
 // run of sorted positions) summed in a fixed order and added to out [4][N]
-// with one atomic per component. Work item i = (node i / 2, component pair
-// i % 2): two threads per node, so that twice as many threads share the runs
-// and each sums one 64-bit pair.
+// with one atomic per component. Work item i = (node of rank i / 2,
+// component pair i % 2): two threads per node, so that twice as many threads
+// share the runs and each sums one 64-bit pair; nodes come longest run
+// first, so the lanes of a warp loop about equally long.
 template <class R>
-__device__ __forceinline__ void block_node_sums(int64_t N, int64_t b, int64_t off, int nb,
+__device__ __forceinline__ void block_node_sums(int64_t N, int64_t off, int nb,
                                                 const int32_t* __restrict__ nodes,
-                                                const uint16_t* __restrict__ runs, const R* buf,
+                                                const uint32_t* __restrict__ runs, const R* buf,
                                                 double* __restrict__ out) {
   for (int i = threadIdx.x; i < 2 * nb; i += kBlockElems) {
     const int j = i >> 1, h = i & 1;
-    const int r0 = __ldg(runs + off + b + j), r1 = __ldg(runs + off + b + j + 1);
+    const uint32_t rl = __ldg(runs + off + j);
+    const int r0 = (int)(rl >> 16), r1 = r0 + (int)(rl & 0xffffu);
     const int64_t v = __ldg(nodes + off + j);
     double lo, hi;
     Smem<R>::sum_pair(buf, h, r0, r1, lo, hi);
@@ -454,7 +549,7 @@ __device__ __forceinline__ void stage_block(int64_t N, int64_t b,
 template <class R, int FLAGS, bool COLOUR = false>
 __global__ void __launch_bounds__(kBlockElems, block_kernel_min_ctas<R>())
     fwd_block_kernel(int64_t N, int64_t E, int64_t n_blocks, const int64_t* __restrict__ node_off,
-                     const int32_t* __restrict__ nodes, const uint16_t* __restrict__ runs,
+                     const int32_t* __restrict__ nodes, const uint32_t* __restrict__ runs,
                      const ElemRecF* __restrict__ rec, const double* __restrict__ geom64,
                      const R* __restrict__ up, ElemParams<R> P, double* __restrict__ rhs,
                      const int32_t* __restrict__ order = nullptr, int64_t i0 = 0,
@@ -467,16 +562,20 @@ __global__ void __launch_bounds__(kBlockElems, block_kernel_min_ctas<R>())
   const int64_t first = COLOUR ? i0 : 0, last = COLOUR ? i1 : n_blocks;
   auto block_at = [&](int64_t i) -> int64_t { return COLOUR ? (int64_t)__ldg(order + i) : i; };
   int64_t i = first + blockIdx.x;
-  if (i < last) stage_block<R>(N, block_at(i), node_off, nodes, up, nullptr, su0);
+  RecAhead<R, 1> ra;
+  if (i < last) {
+    const int64_t b0 = block_at(i);
+    stage_block<R>(N, b0, node_off, nodes, up, nullptr, su0);
+    if (b0 * kBlockElems + tid < E) ra.load(rec, b0 * kBlockElems + tid);
+  }
   cp_async_commit();
   for (int step = 0; i < last; i += gridDim.x, ++step) {
     R* su = (step & 1) ? su1 : su0;
     const int64_t b = block_at(i);
+    const int64_t bn = i + gridDim.x < last ? block_at(i + gridDim.x) : -1;
     // the next block's copies go into the other buffer, whose last readers
     // finished before the previous step's middle barrier
-    if (i + gridDim.x < last)
-      stage_block<R>(N, block_at(i + gridDim.x), node_off, nodes, up, nullptr,
-                     (step & 1) ? su0 : su1);
+    if (bn >= 0) stage_block<R>(N, bn, node_off, nodes, up, nullptr, (step & 1) ? su0 : su1);
     cp_async_commit();
     const int64_t off = node_off[b];
     const int nb = (int)(node_off[b + 1] - off);
@@ -484,8 +583,8 @@ __global__ void __launch_bounds__(kBlockElems, block_kernel_min_ctas<R>())
     __syncthreads();     // ... for every thread; the previous block's sums are done
     const int64_t e = b * kBlockElems + tid;
     if (e < E) {
-      const uint4 lm = load_rec_lmap(rec, e);
-      const uint32_t lmv[4] = {lm.x, lm.y, lm.z, lm.w};
+      const RecAhead<R, 1> cur = ra;
+      const uint32_t lmv[4] = {cur.lm.x, cur.lm.y, cur.lm.z, cur.lm.w};
       R u[4][3], p[4];
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
@@ -497,14 +596,15 @@ __global__ void __launch_bounds__(kBlockElems, block_kernel_min_ctas<R>())
         p[a] = q[3];
       }
       R c[3][3], inv_det, rh;
-      block_geometry(rec, geom64, E, e, c, inv_det, rh);
+      cur.geometry(rec, geom64, E, e, c, inv_det, rh);
       R F[4][4];
       element_rhs<R, FLAGS>(c, inv_det, rh, u, p, P, F);
 #pragma unroll
       for (int a = 0; a < 4; ++a) Smem<R>::put4(sF, (int)(lmv[a] & 0xffffu), F[a]);
     }
+    if (bn >= 0 && bn * kBlockElems + tid < E) ra.load(rec, bn * kBlockElems + tid);
     __syncthreads();
-    block_node_sums<R>(N, b, off, nb, nodes, runs, sF, rhs);
+    block_node_sums<R>(N, off, nb, nodes, runs, sF, rhs);
   }
   cp_async_wait<0>();
 }
@@ -532,7 +632,7 @@ constexpr int block_vjp_min_ctas() {
 template <class R, int FLAGS, bool COLOUR = false>
 __global__ void __launch_bounds__(kBlockElems, block_vjp_min_ctas<R>())
     vjp_block_kernel(int64_t N, int64_t E, int64_t n_blocks, const int64_t* __restrict__ node_off,
-                     const int32_t* __restrict__ nodes, const uint16_t* __restrict__ runs,
+                     const int32_t* __restrict__ nodes, const uint32_t* __restrict__ runs,
                      const ElemRecF* __restrict__ rec, const double* __restrict__ geom64,
                      const R* __restrict__ up, const R* __restrict__ cot, ElemParams<R> P,
                      double* __restrict__ grad, const int32_t* __restrict__ order, int64_t i0,
@@ -545,16 +645,20 @@ __global__ void __launch_bounds__(kBlockElems, block_vjp_min_ctas<R>())
   const int64_t first = COLOUR ? i0 : 0, last = COLOUR ? i1 : n_blocks;
   auto block_at = [&](int64_t i) -> int64_t { return COLOUR ? (int64_t)__ldg(order + i) : i; };
   int64_t i = first + blockIdx.x;
-  if (i < last) stage_block<R>(N, block_at(i), node_off, nodes, up, cot, sb0);
+  RecAhead<R, 2> ra;
+  if (i < last) {
+    const int64_t b0 = block_at(i);
+    stage_block<R>(N, b0, node_off, nodes, up, cot, sb0);
+    if (b0 * kBlockElems + tid < E) ra.load(rec, b0 * kBlockElems + tid);
+  }
   cp_async_commit();
   for (int step = 0; i < last; i += gridDim.x, ++step) {
     R* su = (step & 1) ? sb1 : sb0;
     const int64_t b = block_at(i);
+    const int64_t bn = i + gridDim.x < last ? block_at(i + gridDim.x) : -1;
     // the other buffer was last read (as entries) in the previous step's sums,
     // which every thread finished before the previous step's last barrier
-    if (i + gridDim.x < last)
-      stage_block<R>(N, block_at(i + gridDim.x), node_off, nodes, up, cot,
-                     (step & 1) ? sb0 : sb1);
+    if (bn >= 0) stage_block<R>(N, bn, node_off, nodes, up, cot, (step & 1) ? sb0 : sb1);
     cp_async_commit();
     const int64_t off = node_off[b];
     const int nb = (int)(node_off[b + 1] - off);
@@ -564,7 +668,8 @@ __global__ void __launch_bounds__(kBlockElems, block_vjp_min_ctas<R>())
     R gu[4][3], gp[4];
     uint4 lm = make_uint4(0u, 0u, 0u, 0u);
     if (e < E) {
-      lm = load_rec_lmap(rec, e);
+      const RecAhead<R, 2> cur = ra;
+      lm = cur.lm;
       const uint32_t lmv[4] = {lm.x, lm.y, lm.z, lm.w};
       R u[4][3], p[4], w[4][4];
 #pragma unroll
@@ -579,7 +684,7 @@ __global__ void __launch_bounds__(kBlockElems, block_vjp_min_ctas<R>())
         Smem<R>::get4(su + 4, 8, lc, w[a]);
       }
       R c[3][3], inv_det, rh;
-      block_geometry(rec, geom64, E, e, c, inv_det, rh);
+      cur.geometry(rec, geom64, E, e, c, inv_det, rh);
       element_vjp<R, FLAGS>(c, inv_det, rh, u, p, w, P, gu, gp);
     }
     __syncthreads();  // the staged values are no longer read: reuse su for the entries
@@ -591,8 +696,9 @@ __global__ void __launch_bounds__(kBlockElems, block_vjp_min_ctas<R>())
         Smem<R>::put4(su, (int)(lmv[a] & 0xffffu), g4);
       }
     }
+    if (bn >= 0 && bn * kBlockElems + tid < E) ra.load(rec, bn * kBlockElems + tid);
     __syncthreads();
-    block_node_sums<R>(N, b, off, nb, nodes, runs, su, grad);
+    block_node_sums<R>(N, off, nb, nodes, runs, su, grad);
     __syncthreads();  // the sums have read su before it is staged into again
   }
   cp_async_wait<0>();

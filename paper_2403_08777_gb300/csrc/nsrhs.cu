@@ -60,7 +60,7 @@ struct nsrhs_mesh {
   int64_t n_blocks = 0;
   int64_t* blk_node_off = nullptr;  // [n_blocks + 1]
   int32_t* blk_nodes = nullptr;     // [blk_node_off[n_blocks]]
-  uint16_t* blk_runs = nullptr;     // [blk_node_off[n_blocks] + n_blocks]
+  uint32_t* blk_runs = nullptr;     // [blk_node_off[n_blocks]] (first position << 16) | length
   double* inv_mass = nullptr;       // [N] 1 / lumped mass
   double* mass = nullptr;           // [N] lumped mass sum_e V_e / 4
   // Colour-major copy for the COLOUR scatter (colour.cuh), built when the
@@ -1005,7 +1005,7 @@ nsrhs_status build_blocks(nsrhs_mesh* m, cudaStream_t s) {
   NSRHS_TRY(cudaMemcpyAsync(&total, m->blk_node_off + nb, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   NSRHS_TRY(cudaStreamSynchronize(s));
   if ((st = mesh_alloc(m, &m->blk_nodes, (size_t)total)) != NSRHS_OK) return st;
-  if ((st = mesh_alloc(m, &m->blk_runs, (size_t)(total + nb))) != NSRHS_OK) return st;
+  if ((st = mesh_alloc(m, &m->blk_runs, (size_t)total)) != NSRHS_OK) return st;
   nsrhs::block_plan_kernel<<<(unsigned)nb, nsrhs::kBlockElems, 0, s>>>(
       1, E, m->conn, nullptr, m->blk_node_off, m->blk_nodes, m->blk_runs, m->rec);
   NSRHS_TRY(cudaGetLastError());
