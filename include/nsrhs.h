@@ -73,7 +73,13 @@ typedef enum {
   NSRHS_SCATTER_ATOMIC = 1, /* one double-precision atomic add per entry */
   NSRHS_SCATTER_BLOCK = 2,  /* per-block node-local accumulation in shared
                                memory, one atomic per (block, node, component);
-                               forward and adjoint */
+                               forward and adjoint. The shared-memory stages
+                               are sized by the mesh's largest block (its
+                               distinct nodes); where the FP64 adjoint's stages
+                               cannot fit one CTA (a block of 256 elements
+                               touching more than about 670 distinct nodes,
+                               e.g. disconnected elements), that call returns
+                               NSRHS_EUNSUPPORTED */
   NSRHS_SCATTER_COLOUR = 3, /* element colouring: elements sharing a node have
                                different colours; one launch per colour, whose
                                atomic adds never meet at one address, so the

@@ -465,17 +465,17 @@ struct RecAhead<double, AHEAD> {
 // with one atomic per component. Work item i = (node of rank i / 2,
 // component pair i % 2): two threads per node, so that twice as many threads
 // share the runs and each sums one 64-bit pair; nodes come longest run
-// first, so the lanes of a warp loop about equally long.
+// first, so the lanes of a warp loop about equally long. The block's node
+// ids and runs come from its pipeline stage (shared memory).
 template <class R>
-__device__ __forceinline__ void block_node_sums(int64_t N, int64_t off, int nb,
-                                                const int32_t* __restrict__ nodes,
-                                                const uint32_t* __restrict__ runs, const R* buf,
+__device__ __forceinline__ void block_node_sums(int64_t N, int nb, const int32_t* ids,
+                                                const uint32_t* rl, const R* buf,
                                                 double* __restrict__ out) {
   for (int i = threadIdx.x; i < 2 * nb; i += kBlockElems) {
     const int j = i >> 1, h = i & 1;
-    const uint32_t rl = __ldg(runs + off + j);
-    const int r0 = (int)(rl >> 16), r1 = r0 + (int)(rl & 0xffffu);
-    const int64_t v = __ldg(nodes + off + j);
+    const uint32_t r = rl[j];
+    const int r0 = (int)(r >> 16), r1 = r0 + (int)(r & 0xffffu);
+    const int64_t v = ids[j];
     double lo, hi;
     Smem<R>::sum_pair(buf, h, r0, r1, lo, hi);
     atomicAdd(out + (2 * h) * N + v, lo);
@@ -483,22 +483,41 @@ __device__ __forceinline__ void block_node_sums(int64_t N, int64_t off, int nb,
   }
 }
 
-// Shared memory of the forward block kernel (below), and the resident CTAs
-// per SM the compiler must allow (register cap): the float kernel is
-// latency-bound between its barrier-separated phases, so more CTAs per SM
-// help; the double kernel is bound by the FP64 pipe.
-template <class R, bool COLOUR>
-constexpr size_t block_kernel_smem() {
-  return 12 * kBlockSlots * sizeof(R);
+// The gather pipeline of the block kernels: kStages shared-memory stages per
+// CTA, the copies of a block issued kStages - 1 blocks before it is computed
+// (one block of lead left the staged gathers' latency exposed once the
+// element arithmetic was cheap). A stage holds, for at most `cap` distinct
+// nodes (the mesh's largest block, rounded up to a multiple of 32), the
+// nodal records [cap][W] (W = 4: u, v, w, p; W = 8: and the cotangent), then
+// the node ids [cap] and the runs [cap] of the block. After the stages, the
+// element entries [kBlockSlots][4] by sorted position.
+#ifndef NSRHS_BLOCK_STAGES
+#define NSRHS_BLOCK_STAGES 4
+#endif
+constexpr int kStages = NSRHS_BLOCK_STAGES;
+
+template <class R, int W>
+__host__ __device__ constexpr size_t stage_bytes(int cap) {
+  return (size_t)cap * (W * sizeof(R) + 2 * sizeof(uint32_t));
+}
+template <class R, int W>
+__host__ __device__ constexpr size_t block_smem_bytes(int cap) {
+  return kStages * stage_bytes<R, W>(cap) + (size_t)kBlockSlots * 4 * sizeof(R);
 }
 
+// Resident CTAs per SM the compiler must allow (register cap): the float
+// kernels are latency-bound between their barrier-separated phases, so more
+// CTAs per SM help; the double kernels are bound by the FP64 pipe.
 template <class R>
 constexpr int block_kernel_min_ctas() {
   return sizeof(R) == 4 ? NSRHS_BLOCK_MIN_CTAS_F32 : 2;
 }
+template <class R>
+constexpr int block_vjp_min_ctas() {
+  return sizeof(R) == 4 ? 2 : 1;
+}
 
-// Asynchronous global-to-shared copies (cp.async): the gathers of the next
-// block are in flight while the current block computes.
+// Asynchronous global-to-shared copies (cp.async).
 template <int BYTES>
 __device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -513,23 +532,29 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(PENDING) : "memory");
 }
 
-// Issues the copies of block b's nodal (u, v, w, p) into buf [kBlockSlots][4]
-// (and, with cot, the cotangent into buf [kBlockSlots][8] columns 4..7).
-template <class R>
+// Issues the copies of block b into one pipeline stage: its node ids (stored
+// from the registers that address the gathers), runs, and nodal records
+// (and, for W = 8, the cotangent at columns 4..7).
+template <class R, int W>
 __device__ __forceinline__ void stage_block(int64_t N, int64_t b,
                                             const int64_t* __restrict__ node_off,
                                             const int32_t* __restrict__ nodes,
+                                            const uint32_t* __restrict__ runs,
                                             const R* __restrict__ up, const R* __restrict__ cot,
-                                            R* buf) {
+                                            unsigned char* stage, int cap) {
   const int64_t off = __ldg(node_off + b);
   const int nb = (int)(__ldg(node_off + b + 1) - off);
-  const int stride = cot ? 8 : 4;
+  R* vals = reinterpret_cast<R*>(stage);
+  int32_t* ids = reinterpret_cast<int32_t*>(stage + (size_t)cap * W * sizeof(R));
+  uint32_t* rl = reinterpret_cast<uint32_t*>(ids + cap);
   for (int j = threadIdx.x; j < nb; j += kBlockElems) {
-    const int64_t v = __ldg(nodes + off + j);
-    R* slot = buf + stride * j;
+    const int32_t v = __ldg(nodes + off + j);
+    ids[j] = v;
+    cp_async<4>(rl + j, runs + off + j);
+    R* slot = vals + W * j;
 #pragma unroll
     for (int k = 0; k < 4; ++k) cp_async<sizeof(R)>(slot + k, up + k * N + v);
-    if (cot) {
+    if constexpr (W == 8) {
 #pragma unroll
       for (int k = 0; k < 4; ++k) cp_async<sizeof(R)>(slot + 4 + k, cot + k * N + v);
     }
@@ -538,9 +563,13 @@ __device__ __forceinline__ void stage_block(int64_t N, int64_t b,
 
 // Forward assembly with block-staged gathers and scatters; R is the element
 // arithmetic type (float: mixed form, double: FP64 form). Dynamic shared
-// memory: block_kernel_smem<R, COLOUR>() bytes: two staging buffers for the
-// nodal values (the next block's copies land in one while the current block
-// computes from the other) and one for the element entries.
+// memory: block_smem_bytes<R, 4>(cap) bytes.
+//
+// Per block: the block's stage has landed (wait + barrier); the copies of
+// the block kStages - 1 ahead are issued into the stage the previous block
+// used; each thread computes its element from the staged nodal records and
+// writes its 16 entries at their sorted positions; barrier; the per-node
+// sums and atomics.
 //
 // COLOUR: the CTAs process the blocks order[i0 .. i1) of one block colour (no
 // two share a node, so every address receives at most one atomic in the
@@ -550,46 +579,50 @@ template <class R, int FLAGS, bool COLOUR = false>
 __global__ void __launch_bounds__(kBlockElems, block_kernel_min_ctas<R>())
     fwd_block_kernel(int64_t N, int64_t E, int64_t n_blocks, const int64_t* __restrict__ node_off,
                      const int32_t* __restrict__ nodes, const uint32_t* __restrict__ runs,
-                     const ElemRecF* __restrict__ rec, const double* __restrict__ geom64,
+                     int cap, const ElemRecF* __restrict__ rec, const double* __restrict__ geom64,
                      const R* __restrict__ up, ElemParams<R> P, double* __restrict__ rhs,
                      const int32_t* __restrict__ order = nullptr, int64_t i0 = 0,
                      int64_t i1 = 0) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  R* su0 = reinterpret_cast<R*>(smem_raw);  // [kBlockSlots][4] nodal u, v, w, p (even steps)
-  R* su1 = su0 + 4 * kBlockSlots;            // the same (odd steps)
-  R* sF = su1 + 4 * kBlockSlots;             // [kBlockSlots][4] element entries by position
+  const size_t sbytes = stage_bytes<R, 4>(cap);
+  R* sF = reinterpret_cast<R*>(smem_raw + kStages * sbytes);  // [kBlockSlots][4] entries
   const int tid = threadIdx.x;
   const int64_t first = COLOUR ? i0 : 0, last = COLOUR ? i1 : n_blocks;
   auto block_at = [&](int64_t i) -> int64_t { return COLOUR ? (int64_t)__ldg(order + i) : i; };
   int64_t i = first + blockIdx.x;
-  RecAhead<R, 1> ra;
-  if (i < last) {
-    const int64_t b0 = block_at(i);
-    stage_block<R>(N, b0, node_off, nodes, up, nullptr, su0);
-    if (b0 * kBlockElems + tid < E) ra.load(rec, b0 * kBlockElems + tid);
+#pragma unroll 1
+  for (int k = 0; k < kStages - 1; ++k) {
+    const int64_t ik = i + (int64_t)k * gridDim.x;
+    if (ik < last)
+      stage_block<R, 4>(N, block_at(ik), node_off, nodes, runs, up, nullptr,
+                        smem_raw + k * sbytes, cap);
+    cp_async_commit();
   }
-  cp_async_commit();
+  RecAhead<R, 1> ra;
+  if (i < last && block_at(i) * kBlockElems + tid < E) ra.load(rec, block_at(i) * kBlockElems + tid);
   for (int step = 0; i < last; i += gridDim.x, ++step) {
-    R* su = (step & 1) ? su1 : su0;
     const int64_t b = block_at(i);
     const int64_t bn = i + gridDim.x < last ? block_at(i + gridDim.x) : -1;
-    // the next block's copies go into the other buffer, whose last readers
-    // finished before the previous step's middle barrier
-    if (bn >= 0) stage_block<R>(N, bn, node_off, nodes, up, nullptr, (step & 1) ? su0 : su1);
-    cp_async_commit();
-    const int64_t off = node_off[b];
-    const int nb = (int)(node_off[b + 1] - off);
-    cp_async_wait<1>();  // this block's copies (all but the newest group) have landed
-    __syncthreads();     // ... for every thread; the previous block's sums are done
+    unsigned char* st = smem_raw + (step % kStages) * sbytes;
+    cp_async_wait<kStages - 2>();  // this block's copies (the oldest pending group) have landed
+    __syncthreads();               // ... for every thread; the previous block's sums are done
+    {
+      const int64_t ia = i + (int64_t)(kStages - 1) * gridDim.x;
+      if (ia < last)
+        stage_block<R, 4>(N, block_at(ia), node_off, nodes, runs, up, nullptr,
+                          smem_raw + ((step + kStages - 1) % kStages) * sbytes, cap);
+      cp_async_commit();
+    }
     const int64_t e = b * kBlockElems + tid;
     if (e < E) {
       const RecAhead<R, 1> cur = ra;
       const uint32_t lmv[4] = {cur.lm.x, cur.lm.y, cur.lm.z, cur.lm.w};
+      const R* vals = reinterpret_cast<const R*>(st);
       R u[4][3], p[4];
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
         R q[4];
-        Smem<R>::get4(su, 4, (int)(lmv[a] >> 16), q);
+        Smem<R>::get4(vals, 4, (int)(lmv[a] >> 16), q);
         u[a][0] = q[0];
         u[a][1] = q[1];
         u[a][2] = q[2];
@@ -603,103 +636,92 @@ __global__ void __launch_bounds__(kBlockElems, block_kernel_min_ctas<R>())
       for (int a = 0; a < 4; ++a) Smem<R>::put4(sF, (int)(lmv[a] & 0xffffu), F[a]);
     }
     if (bn >= 0 && bn * kBlockElems + tid < E) ra.load(rec, bn * kBlockElems + tid);
+    const int nb = (int)(__ldg(node_off + b + 1) - __ldg(node_off + b));
     __syncthreads();
-    block_node_sums<R>(N, off, nb, nodes, runs, sF, rhs);
+    const int32_t* ids = reinterpret_cast<const int32_t*>(st + (size_t)cap * 4 * sizeof(R));
+    block_node_sums<R>(N, nb, ids, reinterpret_cast<const uint32_t*>(ids + cap), sF, rhs);
   }
   cp_async_wait<0>();
 }
 
 // Adjoint with block-staged gathers and scatters: the reverse of the forward
 // block kernel. Per block the nodal (u, p) and the cotangent of its distinct
-// nodes are staged in shared memory (double-buffered: the next block's
-// copies are in flight while the current one computes), each thread runs one
-// element's reverse sweep, the 16 gradient entries go back to shared memory
-// at their sorted positions (over the current block's staged values, after a
-// barrier), and each node's entries are summed in a fixed order and added
-// with one atomic per component (COLOUR: blocks of one colour per launch, so
-// that the summation order is fixed). Dynamic shared memory:
-// block_vjp_smem<R, COLOUR>() bytes.
-template <class R, bool COLOUR>
-constexpr size_t block_vjp_smem() {
-  return 16 * kBlockSlots * sizeof(R);
-}
-
-template <class R>
-constexpr int block_vjp_min_ctas() {
-  return sizeof(R) == 4 ? 2 : 1;
-}
-
+// nodes come through the same pipeline (W = 8), each thread runs one
+// element's reverse sweep, the 16 gradient entries go to shared memory at
+// their sorted positions, and each node's entries are summed in a fixed
+// order and added with one atomic per component (COLOUR: blocks of one
+// colour per launch, so that the summation order is fixed). Dynamic shared
+// memory: block_smem_bytes<R, 8>(cap) bytes.
 template <class R, int FLAGS, bool COLOUR = false>
 __global__ void __launch_bounds__(kBlockElems, block_vjp_min_ctas<R>())
     vjp_block_kernel(int64_t N, int64_t E, int64_t n_blocks, const int64_t* __restrict__ node_off,
                      const int32_t* __restrict__ nodes, const uint32_t* __restrict__ runs,
-                     const ElemRecF* __restrict__ rec, const double* __restrict__ geom64,
+                     int cap, const ElemRecF* __restrict__ rec, const double* __restrict__ geom64,
                      const R* __restrict__ up, const R* __restrict__ cot, ElemParams<R> P,
                      double* __restrict__ grad, const int32_t* __restrict__ order, int64_t i0,
                      int64_t i1) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  // two staging buffers [kBlockSlots][8]: u, v, w, p, then the cotangent
-  R* sb0 = reinterpret_cast<R*>(smem_raw);
-  R* sb1 = sb0 + 8 * kBlockSlots;
+  const size_t sbytes = stage_bytes<R, 8>(cap);
+  R* sF = reinterpret_cast<R*>(smem_raw + kStages * sbytes);  // [kBlockSlots][4] entries
   const int tid = threadIdx.x;
   const int64_t first = COLOUR ? i0 : 0, last = COLOUR ? i1 : n_blocks;
   auto block_at = [&](int64_t i) -> int64_t { return COLOUR ? (int64_t)__ldg(order + i) : i; };
   int64_t i = first + blockIdx.x;
-  RecAhead<R, 2> ra;
-  if (i < last) {
-    const int64_t b0 = block_at(i);
-    stage_block<R>(N, b0, node_off, nodes, up, cot, sb0);
-    if (b0 * kBlockElems + tid < E) ra.load(rec, b0 * kBlockElems + tid);
+#pragma unroll 1
+  for (int k = 0; k < kStages - 1; ++k) {
+    const int64_t ik = i + (int64_t)k * gridDim.x;
+    if (ik < last)
+      stage_block<R, 8>(N, block_at(ik), node_off, nodes, runs, up, cot, smem_raw + k * sbytes,
+                        cap);
+    cp_async_commit();
   }
-  cp_async_commit();
+  RecAhead<R, 2> ra;
+  if (i < last && block_at(i) * kBlockElems + tid < E) ra.load(rec, block_at(i) * kBlockElems + tid);
   for (int step = 0; i < last; i += gridDim.x, ++step) {
-    R* su = (step & 1) ? sb1 : sb0;
     const int64_t b = block_at(i);
     const int64_t bn = i + gridDim.x < last ? block_at(i + gridDim.x) : -1;
-    // the other buffer was last read (as entries) in the previous step's sums,
-    // which every thread finished before the previous step's last barrier
-    if (bn >= 0) stage_block<R>(N, bn, node_off, nodes, up, cot, (step & 1) ? sb0 : sb1);
-    cp_async_commit();
-    const int64_t off = node_off[b];
-    const int nb = (int)(node_off[b + 1] - off);
-    cp_async_wait<1>();
+    unsigned char* st = smem_raw + (step % kStages) * sbytes;
+    cp_async_wait<kStages - 2>();
     __syncthreads();
+    {
+      const int64_t ia = i + (int64_t)(kStages - 1) * gridDim.x;
+      if (ia < last)
+        stage_block<R, 8>(N, block_at(ia), node_off, nodes, runs, up, cot,
+                          smem_raw + ((step + kStages - 1) % kStages) * sbytes, cap);
+      cp_async_commit();
+    }
     const int64_t e = b * kBlockElems + tid;
-    R gu[4][3], gp[4];
-    uint4 lm = make_uint4(0u, 0u, 0u, 0u);
     if (e < E) {
       const RecAhead<R, 2> cur = ra;
-      lm = cur.lm;
-      const uint32_t lmv[4] = {lm.x, lm.y, lm.z, lm.w};
+      const uint32_t lmv[4] = {cur.lm.x, cur.lm.y, cur.lm.z, cur.lm.w};
+      const R* vals = reinterpret_cast<const R*>(st);
       R u[4][3], p[4], w[4][4];
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
         const int lc = (int)(lmv[a] >> 16);
         R q[4];
-        Smem<R>::get4(su, 8, lc, q);
+        Smem<R>::get4(vals, 8, lc, q);
         u[a][0] = q[0];
         u[a][1] = q[1];
         u[a][2] = q[2];
         p[a] = q[3];
-        Smem<R>::get4(su + 4, 8, lc, w[a]);
+        Smem<R>::get4(vals + 4, 8, lc, w[a]);
       }
       R c[3][3], inv_det, rh;
       cur.geometry(rec, geom64, E, e, c, inv_det, rh);
+      R gu[4][3], gp[4];
       element_vjp<R, FLAGS>(c, inv_det, rh, u, p, w, P, gu, gp);
-    }
-    __syncthreads();  // the staged values are no longer read: reuse su for the entries
-    if (e < E) {
-      const uint32_t lmv[4] = {lm.x, lm.y, lm.z, lm.w};
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
         const R g4[4] = {gu[a][0], gu[a][1], gu[a][2], gp[a]};
-        Smem<R>::put4(su, (int)(lmv[a] & 0xffffu), g4);
+        Smem<R>::put4(sF, (int)(lmv[a] & 0xffffu), g4);
       }
     }
     if (bn >= 0 && bn * kBlockElems + tid < E) ra.load(rec, bn * kBlockElems + tid);
+    const int nb = (int)(__ldg(node_off + b + 1) - __ldg(node_off + b));
     __syncthreads();
-    block_node_sums<R>(N, off, nb, nodes, runs, su, grad);
-    __syncthreads();  // the sums have read su before it is staged into again
+    const int32_t* ids = reinterpret_cast<const int32_t*>(st + (size_t)cap * 8 * sizeof(R));
+    block_node_sums<R>(N, nb, ids, reinterpret_cast<const uint32_t*>(ids + cap), sF, grad);
   }
   cp_async_wait<0>();
 }

@@ -61,6 +61,7 @@ struct nsrhs_mesh {
   int64_t* blk_node_off = nullptr;  // [n_blocks + 1]
   int32_t* blk_nodes = nullptr;     // [blk_node_off[n_blocks]]
   uint32_t* blk_runs = nullptr;     // [blk_node_off[n_blocks]] (first position << 16) | length
+  int blk_cap = 0;                  // staging capacity: the largest block's distinct nodes, rounded up
   double* inv_mass = nullptr;       // [N] 1 / lumped mass
   double* mass = nullptr;           // [N] lumped mass sum_e V_e / 4
   // Colour-major copy for the COLOUR scatter (colour.cuh), built when the
@@ -120,6 +121,15 @@ int sm_count(int device) {
   if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || n <= 0)
     n = 152;
   return n;
+}
+
+// The largest dynamic shared memory one CTA may use on `device`.
+size_t smem_limit(int device) {
+  int v = 0;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess ||
+      v <= 0)
+    v = 48 * 1024;
+  return (size_t)v;
 }
 
 // Grid for a grid-stride loop over n items: a whole number of waves of
@@ -881,6 +891,21 @@ nsrhs_status check_params(const nsrhs_params* p) {
   return NSRHS_OK;
 }
 
+// Whether the block kernels' shared memory (W values per staged node: 4 for
+// the forward, 8 for the adjoint) fits one CTA on the mesh's device; a mesh
+// whose largest block touches very many distinct nodes may not fit the FP64
+// adjoint's pipeline (NSRHS_EUNSUPPORTED).
+bool block_smem_fits(const nsrhs_mesh* m, const nsrhs_params* p, int W) {
+  size_t need;
+  if (p->precision == NSRHS_FP64)
+    need = W == 4 ? nsrhs::block_smem_bytes<double, 4>(m->blk_cap)
+                  : nsrhs::block_smem_bytes<double, 8>(m->blk_cap);
+  else
+    need = W == 4 ? nsrhs::block_smem_bytes<float, 4>(m->blk_cap)
+                  : nsrhs::block_smem_bytes<float, 8>(m->blk_cap);
+  return need <= smem_limit(m->device);
+}
+
 // The geometry-recompute path exists for the FP64 atomic forward and adjoint.
 bool recompute_supported(const nsrhs_params* p) {
   return p->precision == NSRHS_FP64 &&
@@ -1001,9 +1026,23 @@ nsrhs_status build_blocks(nsrhs_mesh* m, cudaStream_t s) {
     NSRHS_TRY(cub::DeviceScan::ExclusiveSum(tmp.p, tmp_bytes, counts.as<int64_t>(),
                                             m->blk_node_off, (int)nb + 1, s));
   }
-  int64_t total = 0;
+  // the largest block's distinct-node count sizes the staging buffers
+  DevBuf dmax, tmp2;
+  NSRHS_TRY(dmax.alloc(sizeof(int64_t)));
+  {
+    size_t tmp_bytes = 0;
+    NSRHS_TRY(cub::DeviceReduce::Max(nullptr, tmp_bytes, counts.as<int64_t>(), dmax.as<int64_t>(),
+                                     (int)nb, s));
+    NSRHS_TRY(tmp2.alloc(tmp_bytes));
+    NSRHS_TRY(cub::DeviceReduce::Max(tmp2.p, tmp_bytes, counts.as<int64_t>(), dmax.as<int64_t>(),
+                                     (int)nb, s));
+  }
+  int64_t total = 0, max_distinct = 0;
   NSRHS_TRY(cudaMemcpyAsync(&total, m->blk_node_off + nb, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  NSRHS_TRY(cudaMemcpyAsync(&max_distinct, dmax.p, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   NSRHS_TRY(cudaStreamSynchronize(s));
+  if (max_distinct < 1 || max_distinct > nsrhs::kBlockSlots) return NSRHS_ECUDA;
+  m->blk_cap = (int)std::min<int64_t>(nsrhs::kBlockSlots, (max_distinct + 31) / 32 * 32);
   if ((st = mesh_alloc(m, &m->blk_nodes, (size_t)total)) != NSRHS_OK) return st;
   if ((st = mesh_alloc(m, &m->blk_runs, (size_t)total)) != NSRHS_OK) return st;
   nsrhs::block_plan_kernel<<<(unsigned)nb, nsrhs::kBlockElems, 0, s>>>(
@@ -1327,6 +1366,11 @@ nsrhs_status nsrhs_assemble(const nsrhs_mesh* m, const nsrhs_params* p, const vo
       (p->scatter == NSRHS_SCATTER_BLOCK_COLOUR && m->bcol_order == nullptr))
     return NSRHS_EUNSUPPORTED;
   if (p->geometry == NSRHS_GEOM_RECOMPUTE && !recompute_supported(p)) return NSRHS_EUNSUPPORTED;
+  const bool block_path = p->scatter == NSRHS_SCATTER_BLOCK ||
+                          p->scatter == NSRHS_SCATTER_BLOCK_COLOUR ||
+                          (p->scatter == NSRHS_SCATTER_AUTO && p->precision == NSRHS_MIXED);
+  if (p->geometry == NSRHS_GEOM_CACHED && block_path && !block_smem_fits(m, p, 4))
+    return NSRHS_EUNSUPPORTED;
   NSRHS_TRY(cudaMemsetAsync(rhs, 0, sizeof(double) * 4 * N, s));
   if (p->geometry == NSRHS_GEOM_RECOMPUTE) {
     auto P = elem_params<double>(p);
@@ -1347,24 +1391,24 @@ nsrhs_status nsrhs_assemble(const nsrhs_mesh* m, const nsrhs_params* p, const vo
           1, std::min<int64_t>(i1 - i0, (int64_t)sm_count(m->device) * kBlockCtasPerSm));
       if (p->precision == NSRHS_FP64) {
         auto P = elem_params<double>(p);
-        const size_t smem = nsrhs::block_kernel_smem<double, true>();
+        const size_t smem = nsrhs::block_smem_bytes<double, 4>(m->blk_cap);
         with_flags(flags, [&](auto fl) {
           auto kern = nsrhs::fwd_block_kernel<double, decltype(fl)::value, true>;
           err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
           if (err == cudaSuccess)
             kern<<<grid, nsrhs::kBlockElems, smem, s>>>(
-                N, E, nb, m->blk_node_off, m->blk_nodes, m->blk_runs, m->rec,
+                N, E, nb, m->blk_node_off, m->blk_nodes, m->blk_runs, m->blk_cap, m->rec,
                 m->geom, (const double*)up, P, rhs, m->bcol_order, i0, i1);
         });
       } else {
         auto P = elem_params<float>(p);
-        const size_t smem = nsrhs::block_kernel_smem<float, true>();
+        const size_t smem = nsrhs::block_smem_bytes<float, 4>(m->blk_cap);
         with_flags(flags, [&](auto fl) {
           auto kern = nsrhs::fwd_block_kernel<float, decltype(fl)::value, true>;
           err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
           if (err == cudaSuccess)
             kern<<<grid, nsrhs::kBlockElems, smem, s>>>(
-                N, E, nb, m->blk_node_off, m->blk_nodes, m->blk_runs, m->rec,
+                N, E, nb, m->blk_node_off, m->blk_nodes, m->blk_runs, m->blk_cap, m->rec,
                 nullptr, (const float*)up, P, rhs, m->bcol_order, i0, i1);
         });
       }
@@ -1406,25 +1450,25 @@ nsrhs_status nsrhs_assemble(const nsrhs_mesh* m, const nsrhs_params* p, const vo
     cudaError_t err = cudaSuccess;
     if (p->precision == NSRHS_FP64) {
       auto P = elem_params<double>(p);
-      const size_t smem = nsrhs::block_kernel_smem<double, false>();
+      const size_t smem = nsrhs::block_smem_bytes<double, 4>(m->blk_cap);
       with_flags(flags, [&](auto fl) {
         auto kern = nsrhs::fwd_block_kernel<double, decltype(fl)::value>;
         err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err == cudaSuccess)
           kern<<<grid, nsrhs::kBlockElems, smem, s>>>(N, E, nb, m->blk_node_off, m->blk_nodes,
-                                                      m->blk_runs, m->rec,
+                                                      m->blk_runs, m->blk_cap, m->rec,
                                                       m->geom, (const double*)up, P, rhs,
                                                       nullptr, 0, 0);
       });
     } else {
       auto P = elem_params<float>(p);
-      const size_t smem = nsrhs::block_kernel_smem<float, false>();
+      const size_t smem = nsrhs::block_smem_bytes<float, 4>(m->blk_cap);
       with_flags(flags, [&](auto fl) {
         auto kern = nsrhs::fwd_block_kernel<float, decltype(fl)::value>;
         err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err == cudaSuccess)
           kern<<<grid, nsrhs::kBlockElems, smem, s>>>(N, E, nb, m->blk_node_off, m->blk_nodes,
-                                                      m->blk_runs, m->rec,
+                                                      m->blk_runs, m->blk_cap, m->rec,
                                                       nullptr, (const float*)up, P, rhs,
                                                       nullptr, 0, 0);
       });
@@ -1462,6 +1506,11 @@ nsrhs_status nsrhs_assemble_vjp(const nsrhs_mesh* m, const nsrhs_params* p, cons
       (p->scatter == NSRHS_SCATTER_BLOCK_COLOUR && m->bcol_order == nullptr))
     return NSRHS_EUNSUPPORTED;
   if (p->geometry == NSRHS_GEOM_RECOMPUTE && !recompute_supported(p)) return NSRHS_EUNSUPPORTED;
+  const bool block_path = p->scatter == NSRHS_SCATTER_BLOCK ||
+                          p->scatter == NSRHS_SCATTER_BLOCK_COLOUR ||
+                          (p->scatter == NSRHS_SCATTER_AUTO && p->precision == NSRHS_MIXED);
+  if (p->geometry == NSRHS_GEOM_CACHED && block_path && !block_smem_fits(m, p, 8))
+    return NSRHS_EUNSUPPORTED;
   NSRHS_TRY(cudaMemsetAsync(grad, 0, sizeof(double) * 4 * N, s));
   const int flags = formulation_flags(p);
   if (p->geometry == NSRHS_GEOM_RECOMPUTE) {
@@ -1494,7 +1543,7 @@ nsrhs_status nsrhs_assemble_vjp(const nsrhs_mesh* m, const nsrhs_params* p, cons
         err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err == cudaSuccess)
           kern<<<grid, nsrhs::kBlockElems, smem, s>>>(
-              N, E, nb, m->blk_node_off, m->blk_nodes, m->blk_runs, m->rec,
+              N, E, nb, m->blk_node_off, m->blk_nodes, m->blk_runs, m->blk_cap, m->rec,
               geom, u, c, P, grad, coloured ? m->bcol_order : nullptr, i0, i1);
       };
       if (p->precision == NSRHS_FP64) {
@@ -1502,11 +1551,11 @@ nsrhs_status nsrhs_assemble_vjp(const nsrhs_mesh* m, const nsrhs_params* p, cons
         with_flags(flags, [&](auto fl) {
           constexpr int F = decltype(fl)::value;
           if (coloured)
-            launch(nsrhs::vjp_block_kernel<double, F, true>, nsrhs::block_vjp_smem<double, true>(),
+            launch(nsrhs::vjp_block_kernel<double, F, true>, nsrhs::block_smem_bytes<double, 8>(m->blk_cap),
                    m->geom, (const double*)up, (const double*)cot, P);
           else
             launch(nsrhs::vjp_block_kernel<double, F, false>,
-                   nsrhs::block_vjp_smem<double, false>(), m->geom, (const double*)up,
+                   nsrhs::block_smem_bytes<double, 8>(m->blk_cap), m->geom, (const double*)up,
                    (const double*)cot, P);
         });
       } else {
@@ -1514,10 +1563,10 @@ nsrhs_status nsrhs_assemble_vjp(const nsrhs_mesh* m, const nsrhs_params* p, cons
         with_flags(flags, [&](auto fl) {
           constexpr int F = decltype(fl)::value;
           if (coloured)
-            launch(nsrhs::vjp_block_kernel<float, F, true>, nsrhs::block_vjp_smem<float, true>(),
+            launch(nsrhs::vjp_block_kernel<float, F, true>, nsrhs::block_smem_bytes<float, 8>(m->blk_cap),
                    nullptr, (const float*)up, (const float*)cot, P);
           else
-            launch(nsrhs::vjp_block_kernel<float, F, false>, nsrhs::block_vjp_smem<float, false>(),
+            launch(nsrhs::vjp_block_kernel<float, F, false>, nsrhs::block_smem_bytes<float, 8>(m->blk_cap),
                    nullptr, (const float*)up, (const float*)cot, P);
         });
       }

@@ -111,6 +111,35 @@ def test_ragged_element_counts(dev):
             m.close()
 
 
+def test_block_scatter_on_disconnected_elements(dev):
+    """600 tets that share no node: every block touches 1024 distinct nodes,
+    the largest staging capacity. FP64 forward and the mixed forward and
+    adjoint on the block scatter match the oracle; the FP64 adjoint's block
+    stages do not fit one CTA there, which the call reports."""
+    rng = np.random.default_rng(21)
+    E = 600
+    base = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]], float) * 0.1
+    X = base[None, :, :] + rng.uniform(-0.5, 0.5, size=(E, 1, 3)) + rng.uniform(-0.01, 0.01, (E, 4, 3))
+    coords = np.ascontiguousarray(X.reshape(-1, 3).T)
+    conn = np.ascontiguousarray(np.arange(4 * E, dtype=np.int32).reshape(E, 4).T)
+    up = rng.normal(size=(4, 4 * E))
+    w = mg.Workload("disjoint", 1, coords, conn, up, 1.0, 1e-2)
+    ref = oracle.assemble(coords, conn, up, 1.0, 1e-2)
+    cot = mg.normal((4, 4 * E), seed=mg.SEED_COT)
+    gref = oracle.vjp(coords, conn, up, cot, 1.0, 1e-2)
+    c_d, n_d, up_d, cot_d = on_dev(dev, coords, conn, up, cot)
+    m = ns.Mesh(c_d, n_d)
+    check_fp64(m.assemble(up_d, ns.Params(scatter="block")).cpu().numpy(), ref)
+    pm = ns.Params(scatter="block", precision="mixed")
+    assert relerr(m.assemble(up_d.float(), pm).cpu().numpy(), ref) <= TOL_MIXED
+    assert relerr(m.assemble_vjp(up_d.float(), cot_d.float(), pm).cpu().numpy(), gref) <= 1e-6
+    with pytest.raises(_abi.NSRHSError):
+        m.assemble_vjp(up_d, cot_d, ns.Params(scatter="block"))
+    g = m.assemble_vjp(up_d, cot_d, ns.Params()).cpu().numpy()   # atomic: fine
+    assert relerr(g, gref) <= TOL_VJP_ORACLE
+    m.close()
+
+
 def test_single_reference_tet_closed_form(dev):
     X = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]], float)
     U = np.zeros((4, 4))
