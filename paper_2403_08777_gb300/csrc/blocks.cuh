@@ -37,32 +37,40 @@ namespace nsrhs {
 constexpr int kBlockElems = NSRHS_BLOCK_ELEMS;  // elements per block = threads per CTA
 constexpr int kBlockSlots = 4 * kBlockElems;     // at most this many distinct nodes
 
-// Per-element record of the block kernels and the mixed form, 64 bytes (four
-// 16-byte loads): the element geometry rounded to float (cofactor vectors
-// c_k at g[3k + d], 1/detJ at g[9], detJ^(-1/3) at g[10]; computed in double
-// once per mesh) and, per local node a, lmap[a] = (index of the node among the
-// block's distinct nodes << 16) | position of the element's contribution to
-// it in the block's node-sorted order.
-struct __align__(16) ElemRecF {
-  float g[12];  // g[11] unused
-  uint32_t lmap[4];
+// Per-element record of the block kernels and the mixed form, 64 bytes in
+// four 16-byte chunks: chunks 0-2 the element geometry rounded to float
+// (cofactor vectors c_k at words 3k + d, 1/detJ at word 9, detJ^(-1/3) at
+// word 10, word 11 unused; computed in double once per mesh), chunk 3 the
+// block map: per local node a, (index of the node among the block's distinct
+// nodes << 16) | position of the element's contribution to it in the block's
+// node-sorted order. Records are stored chunk-major within each block of
+// kBlockElems elements, so that the threads of a warp, one element each, read
+// chunk k of consecutive elements as one contiguous 512-byte access:
+// element e's chunk k is RecChunk number rec_index(e, k).
+struct __align__(16) RecChunk {
+  uint32_t w[4];
 };
-static_assert(sizeof(ElemRecF) == 64, "ElemRecF layout");
+__host__ __device__ __forceinline__ int64_t rec_index(int64_t e, int k) {
+  return ((e / kBlockElems) * 4 + k) * kBlockElems + (e % kBlockElems);
+}
+// RecChunks to allocate for n elements (whole blocks)
+inline int64_t rec_chunks(int64_t n) { return (n + kBlockElems - 1) / kBlockElems * 4 * kBlockElems; }
 
 // Loads of one record: the float geometry (three 16-byte loads) and the
 // block map (one).
-__device__ __forceinline__ void load_rec_geometry(const ElemRecF* __restrict__ rec, int64_t e,
+__device__ __forceinline__ void load_rec_geometry(const RecChunk* __restrict__ rec, int64_t e,
                                                   float c[3][3], float& inv_det, float& rh) {
-  const float4* r = reinterpret_cast<const float4*>(rec + e);
-  const float4 a = __ldg(r), b = __ldg(r + 1), d = __ldg(r + 2);
+  const float4 a = __ldg(reinterpret_cast<const float4*>(rec + rec_index(e, 0)));
+  const float4 b = __ldg(reinterpret_cast<const float4*>(rec + rec_index(e, 1)));
+  const float4 d = __ldg(reinterpret_cast<const float4*>(rec + rec_index(e, 2)));
   c[0][0] = a.x; c[0][1] = a.y; c[0][2] = a.z;
   c[1][0] = a.w; c[1][1] = b.x; c[1][2] = b.y;
   c[2][0] = b.z; c[2][1] = b.w; c[2][2] = d.x;
   inv_det = d.y;
   rh = d.z;
 }
-__device__ __forceinline__ uint4 load_rec_lmap(const ElemRecF* __restrict__ rec, int64_t e) {
-  return __ldg(reinterpret_cast<const uint4*>(rec + e) + 3);
+__device__ __forceinline__ uint4 load_rec_lmap(const RecChunk* __restrict__ rec, int64_t e) {
+  return __ldg(reinterpret_cast<const uint4*>(rec + rec_index(e, 3)));
 }
 
 // ---- setup ----
@@ -160,7 +168,7 @@ __global__ void __launch_bounds__(kBlockElems)
     block_plan_kernel(int pass, int64_t E, const int32_t* __restrict__ conn,
                       int64_t* __restrict__ counts, const int64_t* __restrict__ node_off,
                       int32_t* __restrict__ nodes, uint32_t* __restrict__ runs,
-                      ElemRecF* __restrict__ rec) {
+                      RecChunk* __restrict__ rec) {
   __shared__ unsigned long long key[kBlockSlots];
   __shared__ int part[kBlockElems];
   __shared__ uint16_t start[kBlockSlots + 1];  // first sorted position of distinct node u
@@ -269,7 +277,7 @@ __global__ void __launch_bounds__(kBlockElems)
     if (kk == ~0ull) continue;
     u += flag[r];
     const int slot = (int)(kk & 0xffffull);
-    rec[e0 + (slot >> 2)].lmap[slot & 3] = ((uint32_t)rank[u] << 16) | (uint32_t)i;
+    rec[rec_index(e0 + (slot >> 2), 3)].w[slot & 3] = ((uint32_t)rank[u] << 16) | (uint32_t)i;
   }
 }
 
@@ -388,12 +396,12 @@ struct Smem<double> {
 
 // Geometry of element e for the block kernels: float from the element record
 // (mixed form), double from the cached [11][E] rows (FP64 form).
-__device__ __forceinline__ void block_geometry(const ElemRecF* __restrict__ rec,
+__device__ __forceinline__ void block_geometry(const RecChunk* __restrict__ rec,
                                                const double* __restrict__, int64_t, int64_t e,
                                                float c[3][3], float& inv_det, float& rh) {
   load_rec_geometry(rec, e, c, inv_det, rh);
 }
-__device__ __forceinline__ void block_geometry(const ElemRecF* __restrict__,
+__device__ __forceinline__ void block_geometry(const RecChunk* __restrict__,
                                                const double* __restrict__ geom, int64_t E,
                                                int64_t e, double c[3][3], double& inv_det,
                                                double& rh) {
@@ -418,14 +426,13 @@ template <>
 struct RecAhead<float, 2> {
   float4 q0, q1, q2;
   uint4 lm;
-  __device__ __forceinline__ void load(const ElemRecF* __restrict__ rec, int64_t e) {
-    const float4* r = reinterpret_cast<const float4*>(rec + e);
-    q0 = __ldg(r);
-    q1 = __ldg(r + 1);
-    q2 = __ldg(r + 2);
-    lm = __ldg(reinterpret_cast<const uint4*>(rec + e) + 3);
+  __device__ __forceinline__ void load(const RecChunk* __restrict__ rec, int64_t e) {
+    q0 = __ldg(reinterpret_cast<const float4*>(rec + rec_index(e, 0)));
+    q1 = __ldg(reinterpret_cast<const float4*>(rec + rec_index(e, 1)));
+    q2 = __ldg(reinterpret_cast<const float4*>(rec + rec_index(e, 2)));
+    lm = load_rec_lmap(rec, e);
   }
-  __device__ __forceinline__ void geometry(const ElemRecF* __restrict__, const double* __restrict__,
+  __device__ __forceinline__ void geometry(const RecChunk* __restrict__, const double* __restrict__,
                                            int64_t, int64_t, float c[3][3], float& inv_det,
                                            float& rh) const {
     c[0][0] = q0.x; c[0][1] = q0.y; c[0][2] = q0.z;
@@ -438,10 +445,10 @@ struct RecAhead<float, 2> {
 template <>
 struct RecAhead<float, 1> {
   uint4 lm;
-  __device__ __forceinline__ void load(const ElemRecF* __restrict__ rec, int64_t e) {
+  __device__ __forceinline__ void load(const RecChunk* __restrict__ rec, int64_t e) {
     lm = load_rec_lmap(rec, e);
   }
-  __device__ __forceinline__ void geometry(const ElemRecF* __restrict__ rec,
+  __device__ __forceinline__ void geometry(const RecChunk* __restrict__ rec,
                                            const double* __restrict__, int64_t, int64_t e,
                                            float c[3][3], float& inv_det, float& rh) const {
     load_rec_geometry(rec, e, c, inv_det, rh);
@@ -450,10 +457,10 @@ struct RecAhead<float, 1> {
 template <int AHEAD>
 struct RecAhead<double, AHEAD> {
   uint4 lm;
-  __device__ __forceinline__ void load(const ElemRecF* __restrict__ rec, int64_t e) {
+  __device__ __forceinline__ void load(const RecChunk* __restrict__ rec, int64_t e) {
     lm = load_rec_lmap(rec, e);
   }
-  __device__ __forceinline__ void geometry(const ElemRecF* __restrict__,
+  __device__ __forceinline__ void geometry(const RecChunk* __restrict__,
                                            const double* __restrict__ geom, int64_t E, int64_t e,
                                            double c[3][3], double& inv_det, double& rh) const {
     block_geometry(nullptr, geom, E, e, c, inv_det, rh);
@@ -579,7 +586,7 @@ template <class R, int FLAGS, bool COLOUR = false>
 __global__ void __launch_bounds__(kBlockElems, block_kernel_min_ctas<R>())
     fwd_block_kernel(int64_t N, int64_t E, int64_t n_blocks, const int64_t* __restrict__ node_off,
                      const int32_t* __restrict__ nodes, const uint32_t* __restrict__ runs,
-                     int cap, const ElemRecF* __restrict__ rec, const double* __restrict__ geom64,
+                     int cap, const RecChunk* __restrict__ rec, const double* __restrict__ geom64,
                      const R* __restrict__ up, ElemParams<R> P, double* __restrict__ rhs,
                      const int32_t* __restrict__ order = nullptr, int64_t i0 = 0,
                      int64_t i1 = 0) {
@@ -656,7 +663,7 @@ template <class R, int FLAGS, bool COLOUR = false>
 __global__ void __launch_bounds__(kBlockElems, block_vjp_min_ctas<R>())
     vjp_block_kernel(int64_t N, int64_t E, int64_t n_blocks, const int64_t* __restrict__ node_off,
                      const int32_t* __restrict__ nodes, const uint32_t* __restrict__ runs,
-                     int cap, const ElemRecF* __restrict__ rec, const double* __restrict__ geom64,
+                     int cap, const RecChunk* __restrict__ rec, const double* __restrict__ geom64,
                      const R* __restrict__ up, const R* __restrict__ cot, ElemParams<R> P,
                      double* __restrict__ grad, const int32_t* __restrict__ order, int64_t i0,
                      int64_t i1) {

@@ -33,6 +33,7 @@
 
 #include <cstdint>
 #include <cuda_runtime.h>
+#include "blocks.cuh"
 
 namespace nsrhs {
 
@@ -168,6 +169,19 @@ __global__ void permute_rows_kernel(int rows, int64_t E, const int32_t* __restri
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t e = perm[i];
     for (int r = 0; r < rows; ++r) dst[r * E + i] = src[r * E + e];
+  }
+}
+
+// Element records in a permuted order: element i of out is element perm[i]
+// of in (the four chunks of each, at their chunk-major places).
+__global__ void permute_records_kernel(int64_t E, const int32_t* __restrict__ perm,
+                                       const RecChunk* __restrict__ in,
+                                       RecChunk* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < E;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = perm[i];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) out[rec_index(i, k)] = in[rec_index(e, k)];
   }
 }
 

@@ -51,9 +51,10 @@ struct nsrhs_mesh {
   // it depends on the mesh only, and one streamed 88-byte record costs far
   // less on GB300 than the ~40 FP64 instructions that recompute it.
   double* geom = nullptr;
-  // Per-element records [E] (blocks.cuh): the same geometry rounded to float
-  // (the mixed form) and the block map of the block kernels.
-  nsrhs::ElemRecF* rec = nullptr;
+  // Per-element records (blocks.cuh; chunk-major per block of elements): the
+  // same geometry rounded to float (the mixed form) and the block map of the
+  // block kernels.
+  nsrhs::RecChunk* rec = nullptr;
   // Element blocks (blocks.cuh): elements are stored in Morton order of
   // their centroids; per block of kBlockElems elements its distinct nodes,
   // their contribution runs and the local connectivity.
@@ -70,7 +71,7 @@ struct nsrhs_mesh {
   std::vector<int64_t> col_off;
   int32_t* col_conn = nullptr;      // [4][E]
   double* col_geom = nullptr;       // [kGeomRows][E]
-  nsrhs::ElemRecF* col_rec = nullptr;  // [E] records in colour-major order
+  nsrhs::RecChunk* col_rec = nullptr;  // the records of the colour-major order
   uint8_t* colour = nullptr;        // [E] colour of each element (Morton order)
   int32_t* elem_order = nullptr;    // [E] caller's index of each element (Morton order)
   // Block colouring for the BLOCK_COLOUR scatter: block colour k is the
@@ -377,7 +378,7 @@ nsrhs_status check_scratch_address(CheckPartial** out) {
 // block map the block planning fills in afterwards).
 __global__ void geometry_kernel(int64_t N, int64_t E, const double* __restrict__ coords,
                                 const int32_t* __restrict__ conn, double* __restrict__ geom,
-                                nsrhs::ElemRecF* __restrict__ rec) {
+                                nsrhs::RecChunk* __restrict__ rec) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E;
        e += (int64_t)gridDim.x * blockDim.x) {
     double X[4][3];
@@ -396,16 +397,18 @@ __global__ void geometry_kernel(int64_t N, int64_t E, const double* __restrict__
       for (int d = 0; d < 3; ++d) g[3 * k + d] = c[k][d];
     g[9] = inv_det;
     g[10] = rh;
-    nsrhs::ElemRecF r;
+    float gf[12];
 #pragma unroll
     for (int q = 0; q < kGeomRows; ++q) {
       geom[q * E + e] = g[q];
-      r.g[q] = __double2float_rn(g[q]);
+      gf[q] = __double2float_rn(g[q]);
     }
-    r.g[11] = 0.0f;
+    gf[11] = 0.0f;
 #pragma unroll
-    for (int a = 0; a < 4; ++a) r.lmap[a] = 0u;
-    rec[e] = r;
+    for (int k = 0; k < 3; ++k)
+      *reinterpret_cast<float4*>(rec + nsrhs::rec_index(e, k)) =
+          make_float4(gf[4 * k], gf[4 * k + 1], gf[4 * k + 2], gf[4 * k + 3]);
+    *reinterpret_cast<uint4*>(rec + nsrhs::rec_index(e, 3)) = make_uint4(0u, 0u, 0u, 0u);
   }
 }
 
@@ -607,7 +610,7 @@ __global__ void __launch_bounds__(kThreads)
 template <int FLAGS, bool COLOUR>
 __device__ __forceinline__ void fwd_mixed_element(int64_t N, int64_t E, int64_t e,
                                                   const int32_t* __restrict__ conn,
-                                                  const nsrhs::ElemRecF* __restrict__ rec,
+                                                  const nsrhs::RecChunk* __restrict__ rec,
                                                   const float* __restrict__ up,
                                                   const ElemParams<float>& P,
                                                   double* __restrict__ rhs) {
@@ -634,7 +637,7 @@ __device__ __forceinline__ void fwd_mixed_element(int64_t N, int64_t E, int64_t 
 template <int FLAGS>
 __global__ void __launch_bounds__(kThreads)
     fwd_mixed_atomic_kernel(int64_t N, int64_t E, const int32_t* __restrict__ conn,
-                            const nsrhs::ElemRecF* __restrict__ rec, const float* __restrict__ up,
+                            const nsrhs::RecChunk* __restrict__ rec, const float* __restrict__ up,
                             ElemParams<float> P, double* __restrict__ rhs) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E;
        e += (int64_t)gridDim.x * blockDim.x)
@@ -645,7 +648,7 @@ template <int FLAGS>
 __global__ void __launch_bounds__(kThreads)
     fwd_mixed_colour_kernel(int64_t N, int64_t E, int64_t e0, int64_t e1,
                             const int32_t* __restrict__ conn,
-                            const nsrhs::ElemRecF* __restrict__ rec, const float* __restrict__ up,
+                            const nsrhs::RecChunk* __restrict__ rec, const float* __restrict__ up,
                             ElemParams<float> P, double* __restrict__ rhs) {
   for (int64_t e = e0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < e1;
        e += (int64_t)gridDim.x * blockDim.x)
@@ -728,7 +731,7 @@ __global__ void __launch_bounds__(kThreads, NSRHS_VJP_COLOUR_MIN_CTAS)
 template <int FLAGS, bool COLOUR>
 __device__ __forceinline__ void vjp_mixed_element(int64_t N, int64_t E, int64_t e,
                                                   const int32_t* __restrict__ conn,
-                                                  const nsrhs::ElemRecF* __restrict__ rec,
+                                                  const nsrhs::RecChunk* __restrict__ rec,
                                                   const float* __restrict__ up,
                                                   const float* __restrict__ cot,
                                                   const ElemParams<float>& P,
@@ -761,7 +764,7 @@ __device__ __forceinline__ void vjp_mixed_element(int64_t N, int64_t E, int64_t 
 template <int FLAGS>
 __global__ void __launch_bounds__(kThreads)
     vjp_mixed_atomic_kernel(int64_t N, int64_t E, const int32_t* __restrict__ conn,
-                            const nsrhs::ElemRecF* __restrict__ rec, const float* __restrict__ up,
+                            const nsrhs::RecChunk* __restrict__ rec, const float* __restrict__ up,
                             const float* __restrict__ cot, ElemParams<float> P,
                             double* __restrict__ grad) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E;
@@ -773,7 +776,7 @@ template <int FLAGS>
 __global__ void __launch_bounds__(kThreads)
     vjp_mixed_colour_kernel(int64_t N, int64_t E, int64_t e0, int64_t e1,
                             const int32_t* __restrict__ conn,
-                            const nsrhs::ElemRecF* __restrict__ rec, const float* __restrict__ up,
+                            const nsrhs::RecChunk* __restrict__ rec, const float* __restrict__ up,
                             const float* __restrict__ cot, ElemParams<float> P,
                             double* __restrict__ grad) {
   for (int64_t e = e0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < e1;
@@ -806,7 +809,7 @@ __global__ void __launch_bounds__(kThreads, NSRHS_VJP_MIN_CTAS)
       for (int k = 0; k < 4; ++k) w[a][k] = ldg(cot + k * N + v[a]);
     }
     R c[3][3], inv_det, rh;
-    nsrhs::block_geometry(reinterpret_cast<const nsrhs::ElemRecF*>(geom),
+    nsrhs::block_geometry(reinterpret_cast<const nsrhs::RecChunk*>(geom),
                           reinterpret_cast<const double*>(geom), E, e, c, inv_det, rh);
     R F[4][4], gu[4][3], gp[4];
     nsrhs::element_rhs_vjp<R, FLAGS>(c, inv_det, rh, u, p, w, P, F, gu, gp);
@@ -1118,15 +1121,14 @@ nsrhs_status build_colouring(nsrhs_mesh* m, cudaStream_t s) {
                                             8, s));
   if ((st = mesh_alloc(m, &m->col_conn, 4 * (size_t)E)) != NSRHS_OK) return st;
   if ((st = mesh_alloc(m, &m->col_geom, kGeomRows * (size_t)E)) != NSRHS_OK) return st;
-  if ((st = mesh_alloc(m, &m->col_rec, (size_t)E)) != NSRHS_OK) return st;
+  if ((st = mesh_alloc(m, &m->col_rec, (size_t)nsrhs::rec_chunks(E))) != NSRHS_OK) return st;
   const int32_t* perm = ids_sorted.as<int32_t>();
   nsrhs::permute_rows_kernel<int32_t><<<grid, kThreads, 0, s>>>(4, E, perm, m->conn, m->col_conn);
   NSRHS_TRY(cudaGetLastError());
   nsrhs::permute_rows_kernel<double><<<grid, kThreads, 0, s>>>(kGeomRows, E, perm, m->geom,
                                                                m->col_geom);
   NSRHS_TRY(cudaGetLastError());
-  nsrhs::permute_rows_kernel<nsrhs::ElemRecF><<<grid, kThreads, 0, s>>>(1, E, perm, m->rec,
-                                                                        m->col_rec);
+  nsrhs::permute_records_kernel<<<grid, kThreads, 0, s>>>(E, perm, m->rec, m->col_rec);
   NSRHS_TRY(cudaGetLastError());
   NSRHS_TRY(cudaStreamSynchronize(s));
   m->info.n_colours = n_col;
@@ -1252,7 +1254,7 @@ nsrhs_status mesh_build(nsrhs_mesh* m, const double* coords, const int32_t* conn
   if ((st = morton_reorder(m, m->elem_order, s)) != NSRHS_OK) return st;
   // Cached geometry (double and float) of every element.
   if ((st = mesh_alloc(m, &m->geom, kGeomRows * (size_t)E)) != NSRHS_OK) return st;
-  if ((st = mesh_alloc(m, &m->rec, (size_t)E)) != NSRHS_OK) return st;
+  if ((st = mesh_alloc(m, &m->rec, (size_t)nsrhs::rec_chunks(E))) != NSRHS_OK) return st;
   geometry_kernel<<<grid_for(E, m->device, 8), kThreads, 0, s>>>(N, E, m->coords, m->conn,
                                                                  m->geom, m->rec);
   NSRHS_TRY(cudaGetLastError());
@@ -1638,7 +1640,7 @@ nsrhs_status nsrhs_assemble_rhs_vjp(const nsrhs_mesh* m, const nsrhs_params* p, 
   } else {
     auto P = elem_params<float>(p);
     with_flags(formulation_flags(p), [&](auto fl) {
-      rhs_vjp_atomic_kernel<float, decltype(fl)::value, nsrhs::ElemRecF>
+      rhs_vjp_atomic_kernel<float, decltype(fl)::value, nsrhs::RecChunk>
           <<<grid, kThreads, 0, s>>>(N, E, m->conn, m->rec, (const float*)up, (const float*)cot, P, rhs, grad);
     });
   }

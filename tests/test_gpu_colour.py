@@ -103,10 +103,10 @@ def test_colouring_is_valid(dev, kind, n, order):
     plain = ns.Mesh(coords, conn)
     assert plain.info()["n_colours"] == 0 and plain.info()["n_block_colours"] == 0
     # colour-major copy (connectivity, double geometry, 64-byte element
-    # records), element colours and order; block colours and the per-colour
-    # block lists
+    # records stored in whole blocks of 256), element colours and order;
+    # block colours and the per-colour block lists
     assert (info["device_bytes"] - plain.info()["device_bytes"] ==
-            (16 + 88 + 64 + 1 + 4) * w.n_elems + 5 * info["n_blocks"])
+            (16 + 88 + 1 + 4) * w.n_elems + (64 * 256 + 5) * info["n_blocks"])
     for mm in (m, m2, plain):
         mm.close()
 
