@@ -156,14 +156,17 @@ __global__ void permute_conn_kernel(int64_t E, const int32_t* __restrict__ in,
 // Per block: sort its (node << 16 | slot) keys (slot = 4 * element-in-block
 // + local node), find the distinct nodes.
 // pass 0 writes counts[b] = number of distinct nodes;
-// pass 1 (node_off = exclusive sum of counts) ranks the block's distinct
-// nodes by the length of their run of contributions, longest first (ties by
-// node), so that the per-node phase hands each warp runs of similar length,
-// and writes
-//   nodes[node_off[b] + r]        the distinct node of rank r
-//   runs[node_off[b] + r]         (first sorted position << 16) | run length of rank r
-//   rec[e].lmap[a]                (rank of the node << 16) | sorted position of
-//                                 (element e, local node a)
+// pass 1 (node_off = exclusive sum of counts) writes
+//   nodes[node_off[b] + u]        the u-th distinct node in ascending order (the
+//                                 staging order: neighbouring lanes gather
+//                                 neighbouring ids)
+//   runs[node_off[b] + r]         the run of the node of rank r, the nodes
+//                                 ranked by the length of their run of
+//                                 contributions, longest first (ties by node),
+//                                 so that the per-node phase hands each warp
+//                                 runs of similar length:
+//                                 (first sorted position << 21) | (length << 10) | u
+//   block map of (element e, local node a)   (u << 16) | its sorted position
 __global__ void __launch_bounds__(kBlockElems)
     block_plan_kernel(int pass, int64_t E, const int32_t* __restrict__ conn,
                       int64_t* __restrict__ counts, const int64_t* __restrict__ node_off,
@@ -173,7 +176,6 @@ __global__ void __launch_bounds__(kBlockElems)
   __shared__ int part[kBlockElems];
   __shared__ uint16_t start[kBlockSlots + 1];  // first sorted position of distinct node u
   __shared__ uint32_t order[kBlockSlots];      // (kBlockSlots - run length) << 16 | u
-  __shared__ uint16_t rank[kBlockSlots];
   const int tid = threadIdx.x;
   const int64_t b = blockIdx.x;
   const int64_t e0 = b * kBlockElems;
@@ -264,11 +266,9 @@ __global__ void __launch_bounds__(kBlockElems)
   for (int r = tid; r < n_distinct; r += kBlockElems) {
     const int v = (int)(order[r] & 0xffffu);
     const int s0 = start[v], len = start[v + 1] - s0;
-    rank[v] = (uint16_t)r;
-    nodes[off + r] = (int32_t)(key[s0] >> 16);
-    runs[off + r] = ((uint32_t)s0 << 16) | (uint32_t)len;
+    nodes[off + v] = (int32_t)(key[s0] >> 16);
+    runs[off + r] = ((uint32_t)s0 << 21) | ((uint32_t)len << 10) | (uint32_t)v;
   }
-  __syncthreads();
   u = part[tid] - local - 1;
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(kBlockElems)
     if (kk == ~0ull) continue;
     u += flag[r];
     const int slot = (int)(kk & 0xffffull);
-    rec[rec_index(e0 + (slot >> 2), 3)].w[slot & 3] = ((uint32_t)rank[u] << 16) | (uint32_t)i;
+    rec[rec_index(e0 + (slot >> 2), 3)].w[slot & 3] = ((uint32_t)u << 16) | (uint32_t)i;
   }
 }
 
@@ -473,7 +473,8 @@ struct RecAhead<double, AHEAD> {
 // component pair i % 2): two threads per node, so that twice as many threads
 // share the runs and each sums one 64-bit pair; nodes come longest run
 // first, so the lanes of a warp loop about equally long. The block's node
-// ids and runs come from its pipeline stage (shared memory).
+// ids (in staging order) and runs (in rank order, each naming its node's
+// staging index) come from its pipeline stage (shared memory).
 template <class R>
 __device__ __forceinline__ void block_node_sums(int64_t N, int nb, const int32_t* ids,
                                                 const uint32_t* rl, const R* buf,
@@ -481,8 +482,8 @@ __device__ __forceinline__ void block_node_sums(int64_t N, int nb, const int32_t
   for (int i = threadIdx.x; i < 2 * nb; i += kBlockElems) {
     const int j = i >> 1, h = i & 1;
     const uint32_t r = rl[j];
-    const int r0 = (int)(r >> 16), r1 = r0 + (int)(r & 0xffffu);
-    const int64_t v = ids[j];
+    const int r0 = (int)(r >> 21), r1 = r0 + (int)((r >> 10) & 0x7ffu);
+    const int64_t v = ids[r & 0x3ffu];
     double lo, hi;
     Smem<R>::sum_pair(buf, h, r0, r1, lo, hi);
     atomicAdd(out + (2 * h) * N + v, lo);
