@@ -3,21 +3,22 @@
 // Setup (once per mesh): elements are put in Morton order of their centroids,
 // so that consecutive elements are close in space, and cut into blocks of
 // kBlockElems elements. For every block the sorted list of the distinct nodes
-// it touches and, per distinct node, its run [runs[j], runs[j + 1]) in the
-// block's contributions sorted by node are stored; per element and local
-// node, its distinct-node index and the position of its contribution in that
-// sorted order (lmap = index << 16 | position, in the element's record).
+// it touches is stored, and a run table: per distinct node, the run of its
+// contributions in the block's contributions sorted by node, ranked longest
+// run first; per element and local node, the node's index in the block's list
+// and the position of its contribution in that sorted order (the block map,
+// in the element's record).
 //
-// Assembly (per call): each CTA walks its blocks; for a block it loads the
-// nodal values of the distinct nodes once into shared memory (as cp.async
-// copies issued one block ahead, double-buffered), each thread computes one
-// element from shared memory and writes its 16 entries to shared memory at
-// their sorted positions, and each distinct node's entries (a contiguous run)
-// are summed in a fixed order and added to the global RHS with one atomic per
-// component (for coloured blocks, launched colour by colour, these never meet
-// at one address, so their order is fixed). The global
-// atomics drop from 16 per element to 4 per (block, distinct node), and the
-// sums inside a block do not depend on scheduling.
+// Assembly (per call): each CTA walks its blocks; the nodal values of a
+// block's distinct nodes come into shared memory once (as cp.async copies
+// issued three blocks ahead, through a 4-stage pipeline), each thread
+// computes one element from shared memory and writes its 16 entries to
+// shared memory at their sorted positions, and each distinct node's entries
+// (a contiguous run) are summed in a fixed order and added to the global RHS
+// with one atomic per component (for coloured blocks, launched colour by
+// colour, these never meet at one address, so their order is fixed). The
+// global atomics drop from 16 per element to 4 per (block, distinct node),
+// and the sums inside a block do not depend on scheduling.
 #pragma once
 
 #include <cstdint>
@@ -358,11 +359,14 @@ struct Smem<float> {
                                                   double& lo, double& hi) {
     const unsigned long long* e = reinterpret_cast<const unsigned long long*>(buf) + h;
     NodeSumF32x2 acc;
+    // the next two entries are loaded ahead of the one being added
     unsigned long long x = r0 < r1 ? e[2 * r0] : 0ull;
+    unsigned long long y = r0 + 1 < r1 ? e[2 * r0 + 2] : 0ull;
     for (int q = r0; q < r1; ++q) {
-      const unsigned long long next = q + 1 < r1 ? e[2 * (q + 1)] : 0ull;
+      const unsigned long long next = q + 2 < r1 ? e[2 * (q + 2)] : 0ull;
       acc.add(x);
-      x = next;
+      x = y;
+      y = next;
     }
     lo = acc.lo();
     hi = acc.hi();
