@@ -421,9 +421,9 @@ __device__ __forceinline__ void block_geometry(const RecChunk* __restrict__,
 // (issued before the per-node phase of the current block, so that its
 // latency is hidden behind that phase and the barrier). AHEAD = 2: the whole
 // float record (geometry and block map); AHEAD = 1: the block map only, the
-// geometry read when the element is computed (measured: the mixed forward,
-// capped at 64 registers, is faster with 1; the adjoint with 2). For R =
-// double the FP64 geometry always comes from the cached double rows.
+// geometry read when the element is computed (measured: both mixed kernels,
+// capped at 64 and 80 registers, are faster with 1). For R = double the FP64
+// geometry always comes from the cached double rows.
 template <class R, int AHEAD>
 struct RecAhead;
 template <>
@@ -526,7 +526,7 @@ constexpr int block_kernel_min_ctas() {
 }
 template <class R>
 constexpr int block_vjp_min_ctas() {
-  return sizeof(R) == 4 ? 2 : 1;
+  return sizeof(R) == 4 ? 3 : 1;
 }
 
 // Asynchronous global-to-shared copies (cp.async).
@@ -656,6 +656,33 @@ __global__ void __launch_bounds__(kBlockElems, block_kernel_min_ctas<R>())
   cp_async_wait<0>();
 }
 
+// The adjoint's reverse sweep re-reads an element's nodal velocities and
+// cotangent from the staged [slot][8] records at its phase boundaries (the
+// empty asm with a memory clobber keeps the compiler from reusing the first
+// loads), so they are not held in registers across the sweep: the float
+// adjoint then fits 3 CTAs per SM (80 registers) instead of 2 (128).
+template <class R>
+struct StagedReload {
+  const R* vals;
+  const uint32_t* lmv;
+  __device__ __forceinline__ void u(R (&uu)[4][3]) const {
+    asm volatile("" ::: "memory");
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      R q[4];
+      Smem<R>::get4(vals, 8, (int)(lmv[a] >> 16), q);
+      uu[a][0] = q[0];
+      uu[a][1] = q[1];
+      uu[a][2] = q[2];
+    }
+  }
+  __device__ __forceinline__ void w(R (&ww)[4][4]) const {
+    asm volatile("" ::: "memory");
+#pragma unroll
+    for (int a = 0; a < 4; ++a) Smem<R>::get4(vals + 4, 8, (int)(lmv[a] >> 16), ww[a]);
+  }
+};
+
 // Adjoint with block-staged gathers and scatters: the reverse of the forward
 // block kernel. Per block the nodal (u, p) and the cotangent of its distinct
 // nodes come through the same pipeline (W = 8), each thread runs one
@@ -687,7 +714,7 @@ __global__ void __launch_bounds__(kBlockElems, block_vjp_min_ctas<R>())
                         cap);
     cp_async_commit();
   }
-  RecAhead<R, 2> ra;
+  RecAhead<R, 1> ra;
   if (i < last && block_at(i) * kBlockElems + tid < E) ra.load(rec, block_at(i) * kBlockElems + tid);
   for (int step = 0; i < last; i += gridDim.x, ++step) {
     const int64_t b = block_at(i);
@@ -704,7 +731,7 @@ __global__ void __launch_bounds__(kBlockElems, block_vjp_min_ctas<R>())
     }
     const int64_t e = b * kBlockElems + tid;
     if (e < E) {
-      const RecAhead<R, 2> cur = ra;
+      const RecAhead<R, 1> cur = ra;
       const uint32_t lmv[4] = {cur.lm.x, cur.lm.y, cur.lm.z, cur.lm.w};
       const R* vals = reinterpret_cast<const R*>(st);
       R u[4][3], p[4], w[4][4];
@@ -722,7 +749,10 @@ __global__ void __launch_bounds__(kBlockElems, block_vjp_min_ctas<R>())
       R c[3][3], inv_det, rh;
       cur.geometry(rec, geom64, E, e, c, inv_det, rh);
       R gu[4][3], gp[4];
-      element_vjp<R, FLAGS>(c, inv_det, rh, u, p, w, P, gu, gp);
+      if constexpr (sizeof(R) == 4)
+        element_vjp<R, FLAGS>(c, inv_det, rh, u, p, w, P, gu, gp, StagedReload<R>{vals, lmv});
+      else
+        element_vjp<R, FLAGS>(c, inv_det, rh, u, p, w, P, gu, gp);
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
         const R g4[4] = {gu[a][0], gu[a][1], gu[a][2], gp[a]};

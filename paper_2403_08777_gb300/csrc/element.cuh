@@ -361,11 +361,34 @@ __device__ __forceinline__ void element_rhs(const R c[3][3], R inv_det, R rh, co
 // WITH_F: also write the element's forward outputs F (element_outputs) from
 // the recomputed intermediates, so that one pass yields the RHS entries and
 // the vector-Jacobian product at the same state.
-template <class R, int FLAGS, bool WITH_F>
+//
+// RL: where the nodal velocities u and the cotangent w come from again at
+// three points of the sweep (before the reverse part, before Gbar, before the
+// final gradient): NoReload keeps the values given; a caller that holds them
+// in shared memory can re-read them there, so that they are not live in
+// registers across the whole sweep (the block adjoint fits one CTA more per
+// SM that way).
+struct NoReload {
+  template <class R>
+  __device__ __forceinline__ void u(R (&)[4][3]) const {}
+  template <class R>
+  __device__ __forceinline__ void w(R (&)[4][4]) const {}
+};
+
+template <class R, int FLAGS, bool WITH_F, class RL = NoReload>
 __device__ __forceinline__ void element_vjp_impl(const R c[3][3], R inv_det, R rh,
-                                                 const R u[4][3], const R p[4], const R w[4][4],
-                                                 const ElemParams<R>& P, R gu[4][3], R gpo[4],
-                                                 R (*F)[4]) {
+                                                 const R u_in[4][3], const R p[4],
+                                                 const R w_in[4][4], const ElemParams<R>& P,
+                                                 R gu[4][3], R gpo[4], R (*F)[4],
+                                                 const RL& rl = RL()) {
+  R u[4][3], w[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) u[a][i] = u_in[a][i];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) w[a][k] = w_in[a][k];
+  }
   using M = MathOps<R>;
   constexpr bool VREMAN = (FLAGS & kVreman) != 0;
   constexpr bool SKEW = (FLAGS & kSkew) != 0;
@@ -480,6 +503,7 @@ __device__ __forceinline__ void element_vjp_impl(const R c[3][3], R inv_det, R r
   }
 
   // ---- reverse ----
+  rl.w(w);
   // Omega = sum_a wm_a c_a^T and cw = sum_a wc_a c_a, with c_0 = -(c_1 + c_2 + c_3)
   R Om[3][3], cw[3];
   {
@@ -570,6 +594,8 @@ __device__ __forceinline__ void element_vjp_impl(const R c[3][3], R inv_det, R r
   const R staub = fmac(Rb[2], gp[2], fmac(Rb[1], gp[1], Rb[0] * gp[0]));
   // Gbar = Omega Qp' + Rq T^T + sum_a wm_a v_a^T - (sum_a wc_a)/24 I,
   // Qp' = a2 Q + a1 I, v_a = -(rho/120)(u_a + S_u)
+  rl.u(u);
+  rl.w(w);
   R Gb[3][3];
   {
     const R Qp[3][3] = {{fmac(a2, Q00, a1), a2 * Q01, a2 * Q02},
@@ -683,6 +709,7 @@ __device__ __forceinline__ void element_vjp_impl(const R c[3][3], R inv_det, R r
   // Gh = sum_a u_a c_a^T, S = sum_a u_a, u_g = QB S + (QA - QB) u_g, and the
   // convection's -(rho/120) Gh (S + u_a): gu_a = Gb c_a + Sbar + Hm^T wm_a + (QA-QB) ugb_a
   // with Hm = -(rho/120) Gh and Sbar = Hm^T sum_a wm_a + QB sum_g ugb_g.
+  rl.w(w);
   {
     const R m120 = P.rho * (R)(SKEW ? -1.0 / 240.0 : -1.0 / 120.0);
     R Hm[3][3];
@@ -732,11 +759,11 @@ __device__ __forceinline__ void element_vjp_impl(const R c[3][3], R inv_det, R r
   gpo[0] = fmac((R)4, pq, -gsum);
 }
 
-template <class R, int FLAGS>
+template <class R, int FLAGS, class RL = NoReload>
 __device__ __forceinline__ void element_vjp(const R c[3][3], R inv_det, R rh, const R u[4][3],
                                             const R p[4], const R w[4][4], const ElemParams<R>& P,
-                                            R gu[4][3], R gpo[4]) {
-  element_vjp_impl<R, FLAGS, false>(c, inv_det, rh, u, p, w, P, gu, gpo, nullptr);
+                                            R gu[4][3], R gpo[4], const RL& rl = RL()) {
+  element_vjp_impl<R, FLAGS, false, RL>(c, inv_det, rh, u, p, w, P, gu, gpo, nullptr, rl);
 }
 
 // The element RHS F and the vector-Jacobian product (gu, gpo) of w at the
