@@ -73,7 +73,7 @@ FLOPS_GEOMETRY = 43
 # the element count (traffic grows in proportion). None once a kernel has
 # changed since its counters were taken.
 DRAM_BYTES_PER_TET = {"fwd_fp64": 158.3, "vjp_fp64": 187.9,
-                      "fwd_mixed": 92.1, "vjp_mixed": 111.6}
+                      "fwd_mixed": 92.7, "vjp_mixed": 106.7}
 
 # Algorithmic (compulsory) bytes per tet with ideal node reuse (N/E = 0.1686
 # on the Kuhn mesh): connectivity or block map 16, cached geometry 88 (f64) or
@@ -663,10 +663,10 @@ MIXED_KERNELS = {"fwd_mixed": "fwd_block_kernel<float,0>", "vjp_mixed": "vjp_blo
 # What ncu shows stopping them (128^3 captures of the current kernels).
 MIXED_LIMITER = {
     "fwd_mixed": "issue latency between barrier phases at 4 CTAs/SM (64 registers): "
-                 "issue 65 %, L1/TEX 68 % (half of the shared wavefronts bank conflicts), "
-                 "FMA 42 %, DRAM 38 %; top stalls long scoreboard, barrier",
-    "vjp_mixed": "latency at 2 CTAs/SM (128 registers): issue 49 %, warps active 25 %, "
-                 "L1/TEX 48 %, FMA 37 %, DRAM 25 %; top stalls long scoreboard, barrier"}
+                 "issue 67 %, L1/TEX 78 % (half of the shared wavefronts bank conflicts), "
+                 "FMA 44 %, DRAM 40 %; top stalls barrier, long scoreboard",
+    "vjp_mixed": "latency at 3 CTAs/SM (80 registers): issue 59 %, warps active 34 %, "
+                 "L1/TEX 71 %, FMA 43 %, DRAM 28 %; top stalls long scoreboard, barrier"}
 
 
 def mixed_roofline(key, ms, n_elems, fp32_peak, hbm_peak):

@@ -421,8 +421,9 @@ __device__ __forceinline__ void block_geometry(const RecChunk* __restrict__,
 // (issued before the per-node phase of the current block, so that its
 // latency is hidden behind that phase and the barrier). AHEAD = 2: the whole
 // float record (geometry and block map); AHEAD = 1: the block map only, the
-// geometry read when the element is computed (measured: both mixed kernels,
-// capped at 64 and 80 registers, are faster with 1). For R = double the FP64
+// geometry read when the element is computed (measured: the mixed forward,
+// whose element routine re-reads u from shared memory, is faster with 2; the
+// mixed adjoint, capped at 80 registers, with 1). For R = double the FP64
 // geometry always comes from the cached double rows.
 template <class R, int AHEAD>
 struct RecAhead;
@@ -573,6 +574,35 @@ __device__ __forceinline__ void stage_block(int64_t N, int64_t b,
   }
 }
 
+// The float element routines re-read an element's nodal velocities (and
+// cotangent) from the staged [slot][W] records at their phase boundaries
+// (the empty asm with a memory clobber keeps the compiler from reusing the
+// first loads), so they are not held in registers across the routine: the
+// mixed forward then takes the whole element record one block ahead within
+// its 64 registers, and the mixed adjoint fits 3 CTAs per SM (80 registers)
+// instead of 2 (128).
+template <class R, int W>
+struct StagedReload {
+  const R* vals;
+  const uint32_t* lmv;
+  __device__ __forceinline__ void u(R (&uu)[4][3]) const {
+    asm volatile("" ::: "memory");
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      R q[4];
+      Smem<R>::get4(vals, W, (int)(lmv[a] >> 16), q);
+      uu[a][0] = q[0];
+      uu[a][1] = q[1];
+      uu[a][2] = q[2];
+    }
+  }
+  __device__ __forceinline__ void w(R (&ww)[4][4]) const {
+    asm volatile("" ::: "memory");
+#pragma unroll
+    for (int a = 0; a < 4; ++a) Smem<R>::get4(vals + 4, W, (int)(lmv[a] >> 16), ww[a]);
+  }
+};
+
 // Forward assembly with block-staged gathers and scatters; R is the element
 // arithmetic type (float: mixed form, double: FP64 form). Dynamic shared
 // memory: block_smem_bytes<R, 4>(cap) bytes.
@@ -610,7 +640,7 @@ __global__ void __launch_bounds__(kBlockElems, block_kernel_min_ctas<R>())
                         smem_raw + k * sbytes, cap);
     cp_async_commit();
   }
-  RecAhead<R, 1> ra;
+  RecAhead<R, 2> ra;
   if (i < last && block_at(i) * kBlockElems + tid < E) ra.load(rec, block_at(i) * kBlockElems + tid);
   for (int step = 0; i < last; i += gridDim.x, ++step) {
     const int64_t b = block_at(i);
@@ -627,7 +657,7 @@ __global__ void __launch_bounds__(kBlockElems, block_kernel_min_ctas<R>())
     }
     const int64_t e = b * kBlockElems + tid;
     if (e < E) {
-      const RecAhead<R, 1> cur = ra;
+      const RecAhead<R, 2> cur = ra;
       const uint32_t lmv[4] = {cur.lm.x, cur.lm.y, cur.lm.z, cur.lm.w};
       const R* vals = reinterpret_cast<const R*>(st);
       R u[4][3], p[4];
@@ -643,7 +673,10 @@ __global__ void __launch_bounds__(kBlockElems, block_kernel_min_ctas<R>())
       R c[3][3], inv_det, rh;
       cur.geometry(rec, geom64, E, e, c, inv_det, rh);
       R F[4][4];
-      element_rhs<R, FLAGS>(c, inv_det, rh, u, p, P, F);
+      if constexpr (sizeof(R) == 4)
+        element_rhs<R, FLAGS>(c, inv_det, rh, u, p, P, F, StagedReload<R, 4>{vals, lmv});
+      else
+        element_rhs<R, FLAGS>(c, inv_det, rh, u, p, P, F);
 #pragma unroll
       for (int a = 0; a < 4; ++a) Smem<R>::put4(sF, (int)(lmv[a] & 0xffffu), F[a]);
     }
@@ -655,33 +688,6 @@ __global__ void __launch_bounds__(kBlockElems, block_kernel_min_ctas<R>())
   }
   cp_async_wait<0>();
 }
-
-// The adjoint's reverse sweep re-reads an element's nodal velocities and
-// cotangent from the staged [slot][8] records at its phase boundaries (the
-// empty asm with a memory clobber keeps the compiler from reusing the first
-// loads), so they are not held in registers across the sweep: the float
-// adjoint then fits 3 CTAs per SM (80 registers) instead of 2 (128).
-template <class R>
-struct StagedReload {
-  const R* vals;
-  const uint32_t* lmv;
-  __device__ __forceinline__ void u(R (&uu)[4][3]) const {
-    asm volatile("" ::: "memory");
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      R q[4];
-      Smem<R>::get4(vals, 8, (int)(lmv[a] >> 16), q);
-      uu[a][0] = q[0];
-      uu[a][1] = q[1];
-      uu[a][2] = q[2];
-    }
-  }
-  __device__ __forceinline__ void w(R (&ww)[4][4]) const {
-    asm volatile("" ::: "memory");
-#pragma unroll
-    for (int a = 0; a < 4; ++a) Smem<R>::get4(vals + 4, 8, (int)(lmv[a] >> 16), ww[a]);
-  }
-};
 
 // Adjoint with block-staged gathers and scatters: the reverse of the forward
 // block kernel. Per block the nodal (u, p) and the cotangent of its distinct
@@ -750,7 +756,7 @@ __global__ void __launch_bounds__(kBlockElems, block_vjp_min_ctas<R>())
       cur.geometry(rec, geom64, E, e, c, inv_det, rh);
       R gu[4][3], gp[4];
       if constexpr (sizeof(R) == 4)
-        element_vjp<R, FLAGS>(c, inv_det, rh, u, p, w, P, gu, gp, StagedReload<R>{vals, lmv});
+        element_vjp<R, FLAGS>(c, inv_det, rh, u, p, w, P, gu, gp, StagedReload<R, 8>{vals, lmv});
       else
         element_vjp<R, FLAGS>(c, inv_det, rh, u, p, w, P, gu, gp);
 #pragma unroll

@@ -238,6 +238,19 @@ __device__ __forceinline__ void element_outputs(const R c[3][3], R inv_det, cons
   }
 }
 
+// Where an element routine takes the nodal velocities u (and, in the
+// reverse sweep, the cotangent w) from again at its phase boundaries:
+// NoReload keeps the values it was given; a caller that holds them in shared
+// memory can re-read them there instead, so that they are not live in
+// registers across the whole routine (the block kernels fit their register
+// caps that way).
+struct NoReload {
+  template <class R>
+  __device__ __forceinline__ void u(R (&)[4][3]) const {}
+  template <class R>
+  __device__ __forceinline__ void w(R (&)[4][4]) const {}
+};
+
 // Forward element RHS. u[a][i], p[a] nodal values; F[a][0..2] momentum,
 // F[a][3] continuity. FLAGS: kVreman | kSkew | kTauElem.
 // Skew-symmetric variant: the Galerkin convection becomes
@@ -245,9 +258,16 @@ __device__ __forceinline__ void element_outputs(const R c[3][3], R inv_det, cons
 // (rho/48) P c_a with P = sum_g u_g u_g^T, folded into K.
 // Per-element tau: tau from |S_u/4|; then sum_g tau = 4 tau, T = tau S_u
 // (sum_g u_g = S_u) and Q = tau P.
-template <class R, int FLAGS>
-__device__ __forceinline__ void element_rhs(const R c[3][3], R inv_det, R rh, const R u[4][3],
-                                            const R p[4], const ElemParams<R>& P, R F[4][4]) {
+// RL: u again before the element outputs (see NoReload).
+template <class R, int FLAGS, class RL = NoReload>
+__device__ __forceinline__ void element_rhs(const R c[3][3], R inv_det, R rh, const R u_in[4][3],
+                                            const R p[4], const ElemParams<R>& P, R F[4][4],
+                                            const RL& rl = RL()) {
+  R u[4][3];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) u[a][i] = u_in[a][i];
   using M = MathOps<R>;
   constexpr bool VREMAN = (FLAGS & kVreman) != 0;
   constexpr bool SKEW = (FLAGS & kSkew) != 0;
@@ -349,6 +369,7 @@ __device__ __forceinline__ void element_rhs(const R c[3][3], R inv_det, R rh, co
   }
   const R Qv[6] = {Q00, Q11, Q22, Q01, Q02, Q12};
   const R Pv[6] = {P00, P11, P22, P01, P02, P12};
+  rl.u(u);
   element_outputs<R, FLAGS>(c, inv_det, u, G, gp, S, psum, trG, mu_eff, stau, T, Qv, Pv, P, F);
 }
 
@@ -364,16 +385,7 @@ __device__ __forceinline__ void element_rhs(const R c[3][3], R inv_det, R rh, co
 //
 // RL: where the nodal velocities u and the cotangent w come from again at
 // three points of the sweep (before the reverse part, before Gbar, before the
-// final gradient): NoReload keeps the values given; a caller that holds them
-// in shared memory can re-read them there, so that they are not live in
-// registers across the whole sweep (the block adjoint fits one CTA more per
-// SM that way).
-struct NoReload {
-  template <class R>
-  __device__ __forceinline__ void u(R (&)[4][3]) const {}
-  template <class R>
-  __device__ __forceinline__ void w(R (&)[4][4]) const {}
-};
+// final gradient; see NoReload).
 
 template <class R, int FLAGS, bool WITH_F, class RL = NoReload>
 __device__ __forceinline__ void element_vjp_impl(const R c[3][3], R inv_det, R rh,
