@@ -531,6 +531,13 @@ def run_ours(args):
     forms["vjp_mixed"] = {"ms": mvjp, "tets_per_s": w.n_elems / (mvjp * 1e-3),
                           "speedup_vs_fp64_vjp": vjp_med / mvjp,
                           "err_vs_oracle_32cube": mixed_vjp_error_32()}
+    # the mixed one-pass call (block scatter) against the two mixed calls
+    mop = _timed(lambda: mesh.assemble_rhs_vjp(up32, cot32, pmx, out=out2), dev, stream, args)
+    mfwd = _timed(lambda: mesh.assemble(up32, pmx, out=rhs), dev, stream, args)
+    forms["rhs_vjp_one_pass_mixed"] = {
+        "ms": mop, "tets_per_s": w.n_elems / (mop * 1e-3), "kernel": "rhs_vjp_block_kernel<float,0>",
+        "separate_ms": {"fwd_mixed": mfwd, "vjp_mixed": mvjp},
+        "vs_separate_calls": (mfwd + mvjp) / mop}
     del up32, cot32
     # element-matrix comparison path (the pre-restructuring form, Sec. V-A)
     mesh.assemble_elmat(up, p, out=rhs)
@@ -945,8 +952,9 @@ def _measured_hbm():
 
 
 def run_profile(args):
-    """A short launch sequence for a profiler: the forward and the adjoint of
-    one form, --warmup then --steps times each, on the --n mesh."""
+    """A short launch sequence for a profiler: the forward, the adjoint and
+    the one-pass call of one form, --warmup then --steps times each, on the
+    --n mesh."""
     import torch
     import paper_2403_08777_gb300 as ns
     w = workload(args.n)
@@ -962,6 +970,9 @@ def run_profile(args):
         mesh.assemble(up, p, out=out)
     for _ in range(args.warmup + args.steps):
         mesh.assemble_vjp(up, cot, p, out=out)
+    out2 = (out, torch.empty_like(out))
+    for _ in range(args.warmup + args.steps):
+        mesh.assemble_rhs_vjp(up, cot, p, out=out2)
     torch.cuda.synchronize(dev)
     mesh.close()
     return 0

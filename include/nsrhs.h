@@ -76,9 +76,10 @@ typedef enum {
                                forward and adjoint. The shared-memory stages
                                are sized by the mesh's largest block (its
                                distinct nodes); where the FP64 adjoint's stages
-                               cannot fit one CTA (a block of 256 elements
-                               touching more than about 670 distinct nodes,
-                               e.g. disconnected elements), that call returns
+                               cannot fit one CTA (with 227 KB per CTA, a block
+                               of 256 elements touching more than 768 distinct
+                               nodes, 736 for the one-pass call, e.g.
+                               disconnected elements), that call returns
                                NSRHS_EUNSUPPORTED */
   NSRHS_SCATTER_COLOUR = 3, /* element colouring: elements sharing a node have
                                different colours; one launch per colour, whose
@@ -222,8 +223,13 @@ nsrhs_status nsrhs_assemble_vjp(const nsrhs_mesh* m, const nsrhs_params* p, cons
  * cotangent before the RHS is needed: residual and adjoint-residual sweeps
  * of steady adjoint solvers, one-shot optimisation, Newton-Krylov with a
  * transposed product. Types and layouts as nsrhs_assemble / _vjp; rhs and
- * grad must be distinct and are overwritten. Scatter AUTO or ATOMIC only
- * (others: NSRHS_EUNSUPPORTED).
+ * grad must be distinct and are overwritten. Scatter AUTO (atomics for
+ * NSRHS_FP64, blocks for NSRHS_MIXED), ATOMIC, BLOCK or BLOCK_COLOUR (the
+ * block stages hold the cotangent beside (u, p) and two entry buffers, the
+ * element RHS and its gradient, summed per node by the same runs;
+ * NSRHS_EUNSUPPORTED where they do not fit a CTA's shared memory, as for the
+ * FP64 adjoint). NSRHS_SCATTER_COLOUR and NSRHS_GEOM_RECOMPUTE:
+ * NSRHS_EUNSUPPORTED.
  */
 nsrhs_status nsrhs_assemble_rhs_vjp(const nsrhs_mesh* m, const nsrhs_params* p, const void* up,
                                     const void* cot, double* rhs, double* grad, void* stream);

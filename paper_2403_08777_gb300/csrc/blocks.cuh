@@ -514,8 +514,8 @@ __host__ __device__ constexpr size_t stage_bytes(int cap) {
   return (size_t)cap * (W * sizeof(R) + 2 * sizeof(uint32_t));
 }
 template <class R, int W>
-__host__ __device__ constexpr size_t block_smem_bytes(int cap) {
-  return kStages * stage_bytes<R, W>(cap) + (size_t)kBlockSlots * 4 * sizeof(R);
+__host__ __device__ constexpr size_t block_smem_bytes(int cap, int entry_buffers = 1) {
+  return kStages * stage_bytes<R, W>(cap) + (size_t)entry_buffers * kBlockSlots * 4 * sizeof(R);
 }
 
 // Resident CTAs per SM the compiler must allow (register cap): the float
@@ -689,25 +689,43 @@ __global__ void __launch_bounds__(kBlockElems, block_kernel_min_ctas<R>())
   cp_async_wait<0>();
 }
 
+// The one-pass kernel's element policy: Base's re-reads, and the element
+// RHS stored at its sorted positions in the RHS entry buffer as soon as the
+// routine has it, before the reverse part.
+template <class R, class Base>
+struct PutRhs : Base {
+  R* sFr;
+  const uint32_t* lm;
+  __device__ __forceinline__ void f(const R (*F)[4]) const {
+#pragma unroll
+    for (int a = 0; a < 4; ++a) Smem<R>::put4(sFr, (int)(lm[a] & 0xffffu), F[a]);
+  }
+};
+
 // Adjoint with block-staged gathers and scatters: the reverse of the forward
 // block kernel. Per block the nodal (u, p) and the cotangent of its distinct
 // nodes come through the same pipeline (W = 8), each thread runs one
 // element's reverse sweep, the 16 gradient entries go to shared memory at
 // their sorted positions, and each node's entries are summed in a fixed
 // order and added with one atomic per component (COLOUR: blocks of one
-// colour per launch, so that the summation order is fixed). Dynamic shared
-// memory: block_smem_bytes<R, 8>(cap) bytes.
-template <class R, int FLAGS, bool COLOUR = false>
-__global__ void __launch_bounds__(kBlockElems, block_vjp_min_ctas<R>())
-    vjp_block_kernel(int64_t N, int64_t E, int64_t n_blocks, const int64_t* __restrict__ node_off,
-                     const int32_t* __restrict__ nodes, const uint32_t* __restrict__ runs,
-                     int cap, const RecChunk* __restrict__ rec, const double* __restrict__ geom64,
-                     const R* __restrict__ up, const R* __restrict__ cot, ElemParams<R> P,
-                     double* __restrict__ grad, const int32_t* __restrict__ order, int64_t i0,
-                     int64_t i1) {
+// colour per launch, so that the summation order is fixed).
+//
+// WITH_F: the one-pass form; the element routine also yields the element
+// RHS, which goes to a second entry buffer and is summed per node into rhs
+// by the same runs. Dynamic shared memory: block_smem_bytes<R, 8>(cap, 1 +
+// WITH_F) bytes.
+template <class R, int FLAGS, bool COLOUR, bool WITH_F>
+__device__ __forceinline__ void vjp_block_body(
+    int64_t N, int64_t E, int64_t n_blocks, const int64_t* __restrict__ node_off,
+    const int32_t* __restrict__ nodes, const uint32_t* __restrict__ runs, int cap,
+    const RecChunk* __restrict__ rec, const double* __restrict__ geom64,
+    const R* __restrict__ up, const R* __restrict__ cot, const ElemParams<R>& P,
+    double* __restrict__ rhs, double* __restrict__ grad, const int32_t* __restrict__ order,
+    int64_t i0, int64_t i1) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const size_t sbytes = stage_bytes<R, 8>(cap);
-  R* sF = reinterpret_cast<R*>(smem_raw + kStages * sbytes);  // [kBlockSlots][4] entries
+  R* sG = reinterpret_cast<R*>(smem_raw + kStages * sbytes);  // [kBlockSlots][4] gradient entries
+  R* sFr = sG + kBlockSlots * 4;                                // [kBlockSlots][4] RHS entries (WITH_F)
   const int tid = threadIdx.x;
   const int64_t first = COLOUR ? i0 : 0, last = COLOUR ? i1 : n_blocks;
   auto block_at = [&](int64_t i) -> int64_t { return COLOUR ? (int64_t)__ldg(order + i) : i; };
@@ -755,23 +773,61 @@ __global__ void __launch_bounds__(kBlockElems, block_vjp_min_ctas<R>())
       R c[3][3], inv_det, rh;
       cur.geometry(rec, geom64, E, e, c, inv_det, rh);
       R gu[4][3], gp[4];
-      if constexpr (sizeof(R) == 4)
-        element_vjp<R, FLAGS>(c, inv_det, rh, u, p, w, P, gu, gp, StagedReload<R, 8>{vals, lmv});
-      else
-        element_vjp<R, FLAGS>(c, inv_det, rh, u, p, w, P, gu, gp);
+      if constexpr (WITH_F) {
+        R F[4][4];
+        if constexpr (sizeof(R) == 4)
+          element_rhs_vjp<R, FLAGS>(c, inv_det, rh, u, p, w, P, F, gu, gp,
+                                    PutRhs<R, StagedReload<R, 8>>{{vals, lmv}, sFr, lmv});
+        else
+          element_rhs_vjp<R, FLAGS>(c, inv_det, rh, u, p, w, P, F, gu, gp,
+                                    PutRhs<R, NoReload>{{}, sFr, lmv});
+      } else {
+        if constexpr (sizeof(R) == 4)
+          element_vjp<R, FLAGS>(c, inv_det, rh, u, p, w, P, gu, gp, StagedReload<R, 8>{vals, lmv});
+        else
+          element_vjp<R, FLAGS>(c, inv_det, rh, u, p, w, P, gu, gp);
+      }
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
         const R g4[4] = {gu[a][0], gu[a][1], gu[a][2], gp[a]};
-        Smem<R>::put4(sF, (int)(lmv[a] & 0xffffu), g4);
+        Smem<R>::put4(sG, (int)(lmv[a] & 0xffffu), g4);
       }
     }
     if (bn >= 0 && bn * kBlockElems + tid < E) ra.load(rec, bn * kBlockElems + tid);
     const int nb = (int)(__ldg(node_off + b + 1) - __ldg(node_off + b));
     __syncthreads();
     const int32_t* ids = reinterpret_cast<const int32_t*>(st + (size_t)cap * 8 * sizeof(R));
-    block_node_sums<R>(N, nb, ids, reinterpret_cast<const uint32_t*>(ids + cap), sF, grad);
+    const uint32_t* rl = reinterpret_cast<const uint32_t*>(ids + cap);
+    if constexpr (WITH_F) block_node_sums<R>(N, nb, ids, rl, sFr, rhs);
+    block_node_sums<R>(N, nb, ids, rl, sG, grad);
   }
   cp_async_wait<0>();
+}
+
+template <class R, int FLAGS, bool COLOUR = false>
+__global__ void __launch_bounds__(kBlockElems, block_vjp_min_ctas<R>())
+    vjp_block_kernel(int64_t N, int64_t E, int64_t n_blocks, const int64_t* __restrict__ node_off,
+                     const int32_t* __restrict__ nodes, const uint32_t* __restrict__ runs,
+                     int cap, const RecChunk* __restrict__ rec, const double* __restrict__ geom64,
+                     const R* __restrict__ up, const R* __restrict__ cot, ElemParams<R> P,
+                     double* __restrict__ grad, const int32_t* __restrict__ order, int64_t i0,
+                     int64_t i1) {
+  vjp_block_body<R, FLAGS, COLOUR, false>(N, E, n_blocks, node_off, nodes, runs, cap, rec, geom64,
+                                          up, cot, P, nullptr, grad, order, i0, i1);
+}
+
+// The RHS and the adjoint at the same state in one pass (see vjp_block_body).
+template <class R, int FLAGS, bool COLOUR = false>
+__global__ void __launch_bounds__(kBlockElems, block_vjp_min_ctas<R>())
+    rhs_vjp_block_kernel(int64_t N, int64_t E, int64_t n_blocks,
+                         const int64_t* __restrict__ node_off, const int32_t* __restrict__ nodes,
+                         const uint32_t* __restrict__ runs, int cap,
+                         const RecChunk* __restrict__ rec, const double* __restrict__ geom64,
+                         const R* __restrict__ up, const R* __restrict__ cot, ElemParams<R> P,
+                         double* __restrict__ rhs, double* __restrict__ grad,
+                         const int32_t* __restrict__ order, int64_t i0, int64_t i1) {
+  vjp_block_body<R, FLAGS, COLOUR, true>(N, E, n_blocks, node_off, nodes, runs, cap, rec, geom64,
+                                         up, cot, P, rhs, grad, order, i0, i1);
 }
 
 }  // namespace nsrhs

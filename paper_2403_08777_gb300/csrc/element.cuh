@@ -243,12 +243,17 @@ __device__ __forceinline__ void element_outputs(const R c[3][3], R inv_det, cons
 // NoReload keeps the values it was given; a caller that holds them in shared
 // memory can re-read them there instead, so that they are not live in
 // registers across the whole routine (the block kernels fit their register
-// caps that way).
+// caps that way). f: where the one-pass routine hands its element RHS once
+// it is complete (before the reverse part); NoReload leaves it in F for the
+// caller, a block kernel stores it to shared memory at once so that F is
+// not live across the reverse sweep.
 struct NoReload {
   template <class R>
   __device__ __forceinline__ void u(R (&)[4][3]) const {}
   template <class R>
   __device__ __forceinline__ void w(R (&)[4][4]) const {}
+  template <class R>
+  __device__ __forceinline__ void f(const R (*)[4]) const {}
 };
 
 // Forward element RHS. u[a][i], p[a] nodal values; F[a][0..2] momentum,
@@ -512,6 +517,7 @@ __device__ __forceinline__ void element_vjp_impl(const R c[3][3], R inv_det, R r
     const R psum = (p[0] + p[1]) + (p[2] + p[3]);
     const R trG = G[0][0] + G[1][1] + G[2][2];
     element_outputs<R, FLAGS>(c, inv_det, u, G, gp, S, psum, trG, mu_eff, stau, T, Qv, Pv, P, F);
+    rl.f(F);
   }
 
   // ---- reverse ----
@@ -780,12 +786,12 @@ __device__ __forceinline__ void element_vjp(const R c[3][3], R inv_det, R rh, co
 
 // The element RHS F and the vector-Jacobian product (gu, gpo) of w at the
 // same state in one pass: the forward intermediates are computed once.
-template <class R, int FLAGS>
+template <class R, int FLAGS, class RL = NoReload>
 __device__ __forceinline__ void element_rhs_vjp(const R c[3][3], R inv_det, R rh,
                                                 const R u[4][3], const R p[4], const R w[4][4],
                                                 const ElemParams<R>& P, R F[4][4], R gu[4][3],
-                                                R gpo[4]) {
-  element_vjp_impl<R, FLAGS, true>(c, inv_det, rh, u, p, w, P, gu, gpo, F);
+                                                R gpo[4], const RL& rl = RL()) {
+  element_vjp_impl<R, FLAGS, true, RL>(c, inv_det, rh, u, p, w, P, gu, gpo, F, rl);
 }
 
 }  // namespace nsrhs

@@ -898,14 +898,14 @@ nsrhs_status check_params(const nsrhs_params* p) {
 // the forward, 8 for the adjoint) fits one CTA on the mesh's device; a mesh
 // whose largest block touches very many distinct nodes may not fit the FP64
 // adjoint's pipeline (NSRHS_EUNSUPPORTED).
-bool block_smem_fits(const nsrhs_mesh* m, const nsrhs_params* p, int W) {
+bool block_smem_fits(const nsrhs_mesh* m, const nsrhs_params* p, int W, int entry_buffers = 1) {
   size_t need;
   if (p->precision == NSRHS_FP64)
-    need = W == 4 ? nsrhs::block_smem_bytes<double, 4>(m->blk_cap)
-                  : nsrhs::block_smem_bytes<double, 8>(m->blk_cap);
+    need = W == 4 ? nsrhs::block_smem_bytes<double, 4>(m->blk_cap, entry_buffers)
+                  : nsrhs::block_smem_bytes<double, 8>(m->blk_cap, entry_buffers);
   else
-    need = W == 4 ? nsrhs::block_smem_bytes<float, 4>(m->blk_cap)
-                  : nsrhs::block_smem_bytes<float, 8>(m->blk_cap);
+    need = W == 4 ? nsrhs::block_smem_bytes<float, 4>(m->blk_cap, entry_buffers)
+                  : nsrhs::block_smem_bytes<float, 8>(m->blk_cap, entry_buffers);
   return need <= smem_limit(m->device);
 }
 
@@ -1621,25 +1621,79 @@ nsrhs_status nsrhs_assemble_rhs_vjp(const nsrhs_mesh* m, const nsrhs_params* p, 
   if (!is_live(m) || !up || !cot || !rhs || !grad || rhs == grad) return NSRHS_EINVAL;
   nsrhs_status st = check_params(p);
   if (st != NSRHS_OK) return st;
-  if (p->scatter != NSRHS_SCATTER_AUTO && p->scatter != NSRHS_SCATTER_ATOMIC)
+  if (p->scatter == NSRHS_SCATTER_COLOUR) return NSRHS_EUNSUPPORTED;
+  if (p->scatter == NSRHS_SCATTER_BLOCK_COLOUR && m->bcol_order == nullptr)
     return NSRHS_EUNSUPPORTED;
   if (p->geometry != NSRHS_GEOM_CACHED) return NSRHS_EUNSUPPORTED;
+  // AUTO: atomics for the FP64 form, blocks for the mixed form (as for the
+  // separate calls)
+  const bool block = p->scatter == NSRHS_SCATTER_BLOCK ||
+                     p->scatter == NSRHS_SCATTER_BLOCK_COLOUR ||
+                     (p->scatter == NSRHS_SCATTER_AUTO && p->precision == NSRHS_MIXED);
+  if (block && !block_smem_fits(m, p, 8, 2)) return NSRHS_EUNSUPPORTED;
   cudaStream_t s = (cudaStream_t)stream;
   DeviceGuard dg(m->device);
   if (!dg.ok) return NSRHS_ECUDA;
   const int64_t N = m->n_nodes, E = m->n_elems;
   NSRHS_TRY(cudaMemsetAsync(rhs, 0, sizeof(double) * 4 * N, s));
   NSRHS_TRY(cudaMemsetAsync(grad, 0, sizeof(double) * 4 * N, s));
+  const int flags = formulation_flags(p);
+  if (block) {
+    const bool coloured = p->scatter == NSRHS_SCATTER_BLOCK_COLOUR;
+    const int64_t nb = m->n_blocks;
+    std::vector<int64_t> ranges = coloured ? m->bcol_off : std::vector<int64_t>{0, nb};
+    cudaError_t err = cudaSuccess;
+    for (size_t k = 0; k + 1 < ranges.size() && err == cudaSuccess; ++k) {
+      const int64_t i0 = ranges[k], i1 = ranges[k + 1];
+      const unsigned grid = (unsigned)std::max<int64_t>(
+          1, std::min<int64_t>(i1 - i0, (int64_t)sm_count(m->device) * kBlockCtasPerSm));
+      auto launch = [&](auto kern, size_t smem, const double* geom, const auto* u, const auto* c,
+                        const auto& P) {
+        err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err == cudaSuccess)
+          kern<<<grid, nsrhs::kBlockElems, smem, s>>>(
+              N, E, nb, m->blk_node_off, m->blk_nodes, m->blk_runs, m->blk_cap, m->rec, geom, u,
+              c, P, rhs, grad, coloured ? m->bcol_order : nullptr, i0, i1);
+      };
+      if (p->precision == NSRHS_FP64) {
+        auto P = elem_params<double>(p);
+        const size_t smem = nsrhs::block_smem_bytes<double, 8>(m->blk_cap, 2);
+        with_flags(flags, [&](auto fl) {
+          constexpr int F = decltype(fl)::value;
+          if (coloured)
+            launch(nsrhs::rhs_vjp_block_kernel<double, F, true>, smem, m->geom, (const double*)up,
+                   (const double*)cot, P);
+          else
+            launch(nsrhs::rhs_vjp_block_kernel<double, F, false>, smem, m->geom,
+                   (const double*)up, (const double*)cot, P);
+        });
+      } else {
+        auto P = elem_params<float>(p);
+        const size_t smem = nsrhs::block_smem_bytes<float, 8>(m->blk_cap, 2);
+        with_flags(flags, [&](auto fl) {
+          constexpr int F = decltype(fl)::value;
+          if (coloured)
+            launch(nsrhs::rhs_vjp_block_kernel<float, F, true>, smem, nullptr, (const float*)up,
+                   (const float*)cot, P);
+          else
+            launch(nsrhs::rhs_vjp_block_kernel<float, F, false>, smem, nullptr, (const float*)up,
+                   (const float*)cot, P);
+        });
+      }
+      if (err == cudaSuccess) err = cudaGetLastError();
+    }
+    return cuda_status(err);
+  }
   const unsigned grid = grid_for(E, m->device, 16);
   if (p->precision == NSRHS_FP64) {
     auto P = elem_params<double>(p);
-    with_flags(formulation_flags(p), [&](auto fl) {
+    with_flags(flags, [&](auto fl) {
       rhs_vjp_atomic_kernel<double, decltype(fl)::value, double><<<grid, kThreads, 0, s>>>(
           N, E, m->conn, m->geom, (const double*)up, (const double*)cot, P, rhs, grad);
     });
   } else {
     auto P = elem_params<float>(p);
-    with_flags(formulation_flags(p), [&](auto fl) {
+    with_flags(flags, [&](auto fl) {
       rhs_vjp_atomic_kernel<float, decltype(fl)::value, nsrhs::RecChunk>
           <<<grid, kThreads, 0, s>>>(N, E, m->conn, m->rec, (const float*)up, (const float*)cot, P, rhs, grad);
     });

@@ -101,6 +101,8 @@ def test_fullsize_one_pass_mixed_adjoint_and_colourings(dev):
     assert err(r, ref) <= 1e-12 and err(g, gref) <= 1e-12
     pm = ns.Params(rho=w.rho, mu=w.mu, precision="mixed")
     assert err(m.assemble_vjp(up.float(), cot.float(), pm), gref) <= 1e-6
+    r, g = m.assemble_rhs_vjp(up.float(), cot.float(), pm)   # mixed one pass: blocks
+    assert err(r, ref) <= 1e-5 and err(g, gref) <= 1e-6
     assert err(m.assemble(up, ns.Params(rho=w.rho, mu=w.mu, scatter="colour")), ref) <= 1e-12
     assert err(m.assemble_vjp(up, cot, ns.Params(rho=w.rho, mu=w.mu, scatter="colour")),
                gref) <= 1e-12

@@ -137,6 +137,14 @@ def test_block_scatter_on_disconnected_elements(dev):
         m.assemble_vjp(up_d, cot_d, ns.Params(scatter="block"))
     g = m.assemble_vjp(up_d, cot_d, ns.Params()).cpu().numpy()   # atomic: fine
     assert relerr(g, gref) <= TOL_VJP_ORACLE
+    # the one-pass call: the mixed block stages (two entry buffers) fit, the
+    # FP64 ones do not
+    r1, g1 = m.assemble_rhs_vjp(up_d.float(), cot_d.float(), pm)
+    assert relerr(r1.cpu().numpy(), ref) <= TOL_MIXED
+    assert relerr(g1.cpu().numpy(), gref) <= 1e-6
+    with pytest.raises(_abi.NSRHSError) as ei:
+        m.assemble_rhs_vjp(up_d, cot_d, ns.Params(scatter="block"))
+    assert ei.value.status == _abi.EUNSUPPORTED
     m.close()
 
 
@@ -505,26 +513,48 @@ def test_mixed_precision_adjoint(dev, cv, conv):
     m.close()
 
 
+@pytest.mark.parametrize("scatter", ["auto", "atomic", "block", "block_colour"])
 @pytest.mark.parametrize("cv,conv,tau", [(0.0, "convective", "gauss"), (0.07, "convective", "gauss"),
                                          (0.0, "skew", "gauss"), (0.07, "skew", "element")])
-def test_one_pass_rhs_and_vjp(dev, cv, conv, tau):
+def test_one_pass_rhs_and_vjp(dev, cv, conv, tau, scatter):
     """nsrhs_assemble_rhs_vjp: both outputs against the oracle (FP64 and
-    mixed), on a mesh with a ragged element count."""
+    mixed; auto is atomic for FP64 and blocks for mixed), on a mesh with a
+    ragged element count."""
     w = mg.make_workload(11, jitter=0.2, order="random", mu=1e-3, mag_max=3.0, c_vreman=cv)
     okw = dict(c_vreman=cv, skew=conv == "skew", tau_elem=tau == "element")
     ref = oracle.assemble(w.coords, w.conn, w.up, w.rho, w.mu, **okw)
     cot = mg.normal((4, w.n_nodes), seed=mg.SEED_COT)
     gref = oracle.vjp(w.coords, w.conn, w.up, cot, w.rho, w.mu, **okw)
     coords, conn, up, cot_d = on_dev(dev, w.coords, w.conn, w.up, cot)
-    m = ns.Mesh(coords, conn)
-    p = ns.Params(rho=w.rho, mu=w.mu, c_vreman=cv, convection=conv, tau=tau)
-    r, g = m.assemble_rhs_vjp(up, cot_d, p)
+    m = ns.Mesh(coords, conn, colour=scatter == "block_colour")
+    kw = dict(rho=w.rho, mu=w.mu, c_vreman=cv, convection=conv, tau=tau, scatter=scatter)
+    r, g = m.assemble_rhs_vjp(up, cot_d, ns.Params(**kw))
     check_fp64(r.cpu().numpy(), ref)
     assert relerr(g.cpu().numpy(), gref) <= TOL_VJP_ORACLE
-    pm = ns.Params(rho=w.rho, mu=w.mu, c_vreman=cv, convection=conv, tau=tau, precision="mixed")
+    pm = ns.Params(precision="mixed", **kw)
     r, g = m.assemble_rhs_vjp(up.float(), cot_d.float(), pm)
     assert relerr(r.cpu().numpy(), ref) <= TOL_MIXED
     assert relerr(g.cpu().numpy(), gref) <= TOL_VJP_FD
+    if scatter == "block_colour":   # fixed summation order: bitwise repeatable
+        r2, g2 = m.assemble_rhs_vjp(up.float(), cot_d.float(), pm)
+        assert torch.equal(r, r2) and torch.equal(g, g2)
+    m.close()
+
+
+def test_one_pass_blocks_match_separate_calls(dev):
+    """The one-pass block kernel's two outputs against the separate block
+    calls at the same state: the same staged gathers and per-node sums, the
+    element RHS taken from the adjoint's recomputation, so they agree to
+    rounding (FP64) and to the float element arithmetic (mixed)."""
+    w = mg.make_workload(14, jitter=0.2, order="rcm", mu=1e-3, mag_max=2.0)
+    cot = mg.normal((4, w.n_nodes), seed=mg.SEED_COT)
+    coords, conn, up, cot_d = on_dev(dev, w.coords, w.conn, w.up, cot)
+    m = ns.Mesh(coords, conn)
+    for prec, u, c, tol in (("fp64", up, cot_d, 1e-13), ("mixed", up.float(), cot_d.float(), 1e-6)):
+        p = ns.Params(rho=w.rho, mu=w.mu, scatter="block", precision=prec)
+        r, g = m.assemble_rhs_vjp(u, c, p)
+        assert relerr(r.cpu().numpy(), m.assemble(u, p).cpu().numpy()) <= tol
+        assert relerr(g.cpu().numpy(), m.assemble_vjp(u, c, p).cpu().numpy()) <= tol
     m.close()
 
 
@@ -537,7 +567,10 @@ def test_one_pass_argument_errors(dev):
         m.assemble_rhs_vjp(up, up, ns.Params(), out=(out, out))
     assert ei.value.status == _abi.EINVAL
     with pytest.raises(ns.NSRHSError) as ei:
-        m.assemble_rhs_vjp(up, up, ns.Params(scatter="block"))
+        m.assemble_rhs_vjp(up, up, ns.Params(scatter="colour"))
+    assert ei.value.status == _abi.EUNSUPPORTED
+    with pytest.raises(ns.NSRHSError) as ei:   # no block colouring on this mesh
+        m.assemble_rhs_vjp(up, up, ns.Params(scatter="block_colour"))
     assert ei.value.status == _abi.EUNSUPPORTED
     m.close()
 
