@@ -496,6 +496,29 @@ __device__ __forceinline__ void block_node_sums(int64_t N, int nb, const int32_t
   }
 }
 
+// The one-pass kernel's per-node sums: as block_node_sums for two entry
+// buffers (the element RHS and its gradient) at once, so that each thread
+// reads its node's run once and carries two independent summation chains.
+template <class R>
+__device__ __forceinline__ void block_node_sums2(int64_t N, int nb, const int32_t* ids,
+                                                 const uint32_t* rl, const R* bufA,
+                                                 double* __restrict__ outA, const R* bufB,
+                                                 double* __restrict__ outB) {
+  for (int i = threadIdx.x; i < 2 * nb; i += kBlockElems) {
+    const int j = i >> 1, h = i & 1;
+    const uint32_t r = rl[j];
+    const int r0 = (int)(r >> 21), r1 = r0 + (int)((r >> 10) & 0x7ffu);
+    const int64_t v = ids[r & 0x3ffu];
+    double lo, hi, lo2, hi2;
+    Smem<R>::sum_pair(bufA, h, r0, r1, lo, hi);
+    Smem<R>::sum_pair(bufB, h, r0, r1, lo2, hi2);
+    atomicAdd(outA + (2 * h) * N + v, lo);
+    atomicAdd(outA + (2 * h + 1) * N + v, hi);
+    atomicAdd(outB + (2 * h) * N + v, lo2);
+    atomicAdd(outB + (2 * h + 1) * N + v, hi2);
+  }
+}
+
 // The gather pipeline of the block kernels: kStages shared-memory stages per
 // CTA, the copies of a block issued kStages - 1 blocks before it is computed
 // (one block of lead left the staged gathers' latency exposed once the
@@ -712,7 +735,7 @@ struct PutRhs : Base {
 //
 // WITH_F: the one-pass form; the element routine also yields the element
 // RHS, which goes to a second entry buffer and is summed per node into rhs
-// by the same runs. Dynamic shared memory: block_smem_bytes<R, 8>(cap, 1 +
+// by the same runs (block_node_sums2). Dynamic shared memory: block_smem_bytes<R, 8>(cap, 1 +
 // WITH_F) bytes.
 template <class R, int FLAGS, bool COLOUR, bool WITH_F>
 __device__ __forceinline__ void vjp_block_body(
@@ -798,8 +821,10 @@ __device__ __forceinline__ void vjp_block_body(
     __syncthreads();
     const int32_t* ids = reinterpret_cast<const int32_t*>(st + (size_t)cap * 8 * sizeof(R));
     const uint32_t* rl = reinterpret_cast<const uint32_t*>(ids + cap);
-    if constexpr (WITH_F) block_node_sums<R>(N, nb, ids, rl, sFr, rhs);
-    block_node_sums<R>(N, nb, ids, rl, sG, grad);
+    if constexpr (WITH_F)
+      block_node_sums2<R>(N, nb, ids, rl, sFr, rhs, sG, grad);
+    else
+      block_node_sums<R>(N, nb, ids, rl, sG, grad);
   }
   cp_async_wait<0>();
 }
