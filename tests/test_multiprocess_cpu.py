@@ -4,8 +4,12 @@
   and the rate counts the units of every rank.
 * The partitioned assembly a multi-GPU run would use (§VII of the paper: the
   assembly is trivially parallel): every rank assembles its own slice of the
-  elements and one sum over ranks of the nodal vectors (the interface-node
-  exchange) gives the full RHS. Checked with the oracle.
+  elements and one sum over ranks of the nodal vectors gives the full RHS.
+  Checked with the oracle.
+* The same with the package's slab partition: every rank assembles its
+  sub-mesh over its owned and ghost nodes only, and one all-reduce of the
+  interface rows (exchange_interface) makes every local row equal to the
+  whole mesh's, for the RHS and the VJP.
 """
 import multiprocessing as mp
 import os
@@ -36,6 +40,23 @@ def _worker(rank, world, port, task, q):
             t = bench.max_over_ranks(10.0 + 5.0 * rank, world, torch.device("cpu"))
             rate = bench.whole_job_rate(1000, world, t / 1e3)
             q.put((rank, t, rate))
+        elif task == "slab":
+            import meshgen as mg
+            import oracle
+            from paper_2403_08777_gb300 import partition as pt
+            w = mg.make_workload(6, jitter=0.2, order="random", mu=1e-3, mag_max=2.0)
+            cot = mg.normal((4, w.n_nodes), seed=mg.SEED_COT)
+            part = pt.slab_partition(w.coords, w.conn, world)[rank]
+            lc, lu = part.local(w.coords), part.local(w.up)
+            r = torch.from_numpy(oracle.assemble(lc, part.conn, lu, w.rho, w.mu))
+            g = torch.from_numpy(oracle.vjp(lc, part.conn, lu, part.local(cot), w.rho, w.mu))
+            pt.exchange_interface(r, part, dist.all_reduce)
+            pt.exchange_interface(g, part, dist.all_reduce)
+            full = oracle.assemble(w.coords, w.conn, w.up, w.rho, w.mu)[:, part.nodes]
+            gfull = oracle.vjp(w.coords, w.conn, w.up, cot, w.rho, w.mu)[:, part.nodes]
+            err = max(float(np.abs(r.numpy() - full).max() / np.abs(full).max()),
+                      float(np.abs(g.numpy() - gfull).max() / np.abs(gfull).max()))
+            q.put((rank, err, part.n_iface))
         else:
             import meshgen as mg
             import oracle
@@ -77,3 +98,11 @@ def test_bench_reductions_gloo():
 def test_partitioned_assembly_interface_sum_gloo():
     for _, err, scale in _run("partition"):
         assert err <= 1e-14 * scale
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_slab_partition_exchange_gloo(world):
+    out = _run("slab", world)
+    for _, err, n_iface in out:
+        assert n_iface > 0
+        assert err <= 1e-13
