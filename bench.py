@@ -537,7 +537,9 @@ def run_ours(args):
     forms["rhs_vjp_one_pass_mixed"] = {
         "ms": mop, "tets_per_s": w.n_elems / (mop * 1e-3), "kernel": "rhs_vjp_block_kernel<float,0>",
         "separate_ms": {"fwd_mixed": mfwd, "vjp_mixed": mvjp},
-        "vs_separate_calls": (mfwd + mvjp) / mop}
+        "vs_separate_calls": (mfwd + mvjp) / mop,
+        "tflops_fp32": flops["rhs_vjp"] * w.n_elems / (mop * 1e-3) / 1e12,
+        "frac_fp32_probe": flops["rhs_vjp"] * w.n_elems / (mop * 1e-3) / 1e12 / fp32_probe}
     del up32, cot32
     # element-matrix comparison path (the pre-restructuring form, Sec. V-A)
     mesh.assemble_elmat(up, p, out=rhs)
