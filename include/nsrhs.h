@@ -77,8 +77,8 @@ typedef enum {
                                are sized by the mesh's largest block (its
                                distinct nodes); where the FP64 adjoint's stages
                                cannot fit one CTA (with 227 KB per CTA, a block
-                               of 256 elements touching more than 768 distinct
-                               nodes, 736 for the one-pass call, e.g.
+                               of 256 elements touching more than 672 distinct
+                               nodes, 576 for the one-pass call, e.g.
                                disconnected elements), that call returns
                                NSRHS_EUNSUPPORTED */
   NSRHS_SCATTER_COLOUR = 3, /* element colouring: elements sharing a node have
