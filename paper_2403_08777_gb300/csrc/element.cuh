@@ -457,7 +457,7 @@ __device__ __forceinline__ void element_vjp_impl(const R c[3][3], R inv_det, R r
   R bS[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) bS[i] = (R)kQB * S[i];
-  R tau[4], yr[4];  // tau_g and 1/|u_g| (0 where u_g = 0)
+  R tau[4], kyr[4];  // tau_g and k2/|u_g| (0 where u_g = 0)
   R stau = (R)0, T[3] = {(R)0, (R)0, (R)0};
   R Q00 = (R)0, Q11 = (R)0, Q22 = (R)0, Q01 = (R)0, Q02 = (R)0, Q12 = (R)0;
   R P00 = (R)0, P11 = (R)0, P22 = (R)0, P01 = (R)0, P02 = (R)0, P12 = (R)0;
@@ -474,8 +474,9 @@ __device__ __forceinline__ void element_vjp_impl(const R c[3][3], R inv_det, R r
     for (int i = 0; i < 3; ++i) ug[i] = fmac((R)(kQA - kQB), u[g][i], bS[i]);
     if constexpr (!TAUE) {
       const R s = fmac(ug[2], ug[2], fmac(ug[1], ug[1], ug[0] * ug[0]));
-      yr[g] = M::rsqrt_(s);
-      tau[g] = M::rcp(fmac(k2, s * yr[g], k1));
+      // k2 |u_g| = (k2 / |u_g|) s: the reverse sweep reuses k2 / |u_g|
+      kyr[g] = k2 * M::rsqrt_(s);
+      tau[g] = M::rcp(fmac(kyr[g], s, k1));
       stau += tau[g];
       R tu[3];
 #pragma unroll
@@ -545,13 +546,9 @@ __device__ __forceinline__ void element_vjp_impl(const R c[3][3], R inv_det, R r
   const R a1 = -s6 * mu_eff;
   const R a2 = -s6 * (P.rho * P.rho * (R)0.25);
   const R b4 = -s6 * (P.rho * (R)0.25);
-  // Rbar = -(inv_det/24) cw, Rq = rho Rbar
-  R Rb[3], Rq[3];
-#pragma unroll
-  for (int j = 0; j < 3; ++j) {
-    Rb[j] = -s24 * cw[j];
-    Rq[j] = P.rho * Rb[j];
-  }
+  // Rbar = -(inv_det/24) cw is not formed: it enters as stau Rbar
+  // (-s24 stau cw), Rbar . gph, rho G^T Rbar = b4 G^T cw and rho Rbar T^T =
+  // cw (b4 T)^T, since b4 = -rho inv_det/24
   // pressure mean: pbar-bar / 4 = tr(Omega)/24
   const R pq = (Om[0][0] + Om[1][1] + Om[2][2]) * (R)(1.0 / 24.0);
   // mu_eff-bar = <Wbar, G> with Wbar = -(inv_det/6) Omega
@@ -583,34 +580,31 @@ __device__ __forceinline__ void element_vjp_impl(const R c[3][3], R inv_det, R r
         Qh[i][j] = Qh[j][i] = a2h * acc;
       }
   }
-  // Tbar = b4 Omega^T gph + G^T Rq ; staubar = Rbar . gph ; gpbar = b4 Omega T + stau Rbar
-  R Tb[3], gpb[3];
+  // Tbar = b4 (Omega^T gph + G^T cw) ; staubar = Rbar . gph ; gpbar = Omega (b4 T) + stau Rbar
+  R Tb[3], gpb[3], bT[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) bT[i] = b4 * T[i];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    R acc = Om[0][j] * gp[0];
+    acc = fmac(Om[1][j], gp[1], acc);
+    acc = fmac(Om[2][j], gp[2], acc);
+    acc = fmac(G[0][j], cw[0], acc);
+    acc = fmac(G[1][j], cw[1], acc);
+    Tb[j] = b4 * fmac(G[2][j], cw[2], acc);
+  }
   {
-    R gq[3], bT[3];
+    const R sRb = -s24 * stau;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      gq[i] = b4 * gp[i];
-      bT[i] = b4 * T[i];
-    }
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      R acc = Om[0][j] * gq[0];
-      acc = fmac(Om[1][j], gq[1], acc);
-      acc = fmac(Om[2][j], gq[2], acc);
-      acc = fmac(G[0][j], Rq[0], acc);
-      acc = fmac(G[1][j], Rq[1], acc);
-      Tb[j] = fmac(G[2][j], Rq[2], acc);
-    }
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      R acc = stau * Rb[i];
+      R acc = sRb * cw[i];
       acc = fmac(Om[i][0], bT[0], acc);
       acc = fmac(Om[i][1], bT[1], acc);
       gpb[i] = fmac(Om[i][2], bT[2], acc);
     }
   }
-  const R staub = fmac(Rb[2], gp[2], fmac(Rb[1], gp[1], Rb[0] * gp[0]));
-  // Gbar = Omega Qp' + Rq T^T + sum_a wm_a v_a^T - (sum_a wc_a)/24 I,
+  const R staub = -s24 * fmac(cw[2], gp[2], fmac(cw[1], gp[1], cw[0] * gp[0]));
+  // Gbar = Omega Qp' + rho Rbar T^T + sum_a wm_a v_a^T - (sum_a wc_a)/24 I,
   // Qp' = a2 Q + a1 I, v_a = -(rho/120)(u_a + S_u)
   rl.u(u);
   rl.w(w);
@@ -632,7 +626,7 @@ __device__ __forceinline__ void element_vjp_impl(const R c[3][3], R inv_det, R r
     for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
-        R acc = (i == j) ? fmac(Rq[i], T[j], -wc24) : Rq[i] * T[j];
+        R acc = (i == j) ? fmac(cw[i], bT[j], -wc24) : cw[i] * bT[j];
         acc = fmac(Om[i][0], Qp[0][j], acc);
         acc = fmac(Om[i][1], Qp[1][j], acc);
         acc = fmac(Om[i][2], Qp[2][j], acc);
@@ -691,7 +685,7 @@ __device__ __forceinline__ void element_vjp_impl(const R c[3][3], R inv_det, R r
       const R taub = fmac(ug[2], QT[2], fmac(ug[1], QT[1], fmac(ug[0], QT[0], staub)));
       const R db = -(tau[g] * tau[g]) * taub;  // d(1/d)
       mub = fmac(crh2, db, mub);
-      const R sc = (k2 * yr[g]) * db;           // d|u_g| / du_g = u_g / |u_g|
+      const R sc = kyr[g] * db;                 // d|u_g| / du_g = u_g / |u_g|
 #pragma unroll
       for (int i = 0; i < 3; ++i)
         ugb[g][i] = fmac(tau[g], fmac((R)2, QT[i], -Tb[i]), sc * ug[i]);
@@ -744,14 +738,16 @@ __device__ __forceinline__ void element_vjp_impl(const R c[3][3], R inv_det, R r
       for (int i = 0; i < 3; ++i) acc = fmac(Hm[i][j], (w[0][i] + w[1][i]) + (w[2][i] + w[3][i]), acc);
       Sb[j] = acc;
     }
-    R zsum[3] = {(R)0, (R)0, (R)0};
+    // Gb c_a as a chain from Sb; c_0 = -(c_1 + c_2 + c_3)
+    R cs[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) cs[j] = (c[0][j] + c[1][j]) + c[2][j];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
-        const R z = fmac(Gb[i][2], c[k][2], fmac(Gb[i][1], c[k][1], Gb[i][0] * c[k][0]));
-        zsum[i] += z;
-        R acc = fmac((R)(kQA - kQB), ugb[k + 1][i], z + Sb[i]);
+        R acc = fmac(Gb[i][2], c[k][2], fmac(Gb[i][1], c[k][1], fmac(Gb[i][0], c[k][0], Sb[i])));
+        acc = fmac((R)(kQA - kQB), ugb[k + 1][i], acc);
         acc = fmac(Hm[0][i], w[k + 1][0], acc);
         acc = fmac(Hm[1][i], w[k + 1][1], acc);
         gu[k + 1][i] = fmac(Hm[2][i], w[k + 1][2], acc);
@@ -759,7 +755,8 @@ __device__ __forceinline__ void element_vjp_impl(const R c[3][3], R inv_det, R r
     }
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      R acc = fmac((R)(kQA - kQB), ugb[0][i], Sb[i] - zsum[i]);
+      R acc = fmac(-Gb[i][2], cs[2], fmac(-Gb[i][1], cs[1], fmac(-Gb[i][0], cs[0], Sb[i])));
+      acc = fmac((R)(kQA - kQB), ugb[0][i], acc);
       acc = fmac(Hm[0][i], w[0][0], acc);
       acc = fmac(Hm[1][i], w[0][1], acc);
       gu[0][i] = fmac(Hm[2][i], w[0][2], acc);
