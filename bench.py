@@ -51,8 +51,8 @@ UNIT = "tets/s"
 # (tests/test_flop_count.py keeps these numbers in step with the source).
 # The element geometry (43 flops per tet) is computed once per mesh and
 # cached, so it is not part of a call.
-FLOPS_PER_TET = {"fwd": 518, "vjp": 1095, "rhs_vjp": 1390}
-FLOPS_PER_TET_VREMAN = {"fwd": 571, "vjp": 1240, "rhs_vjp": 1535}
+FLOPS_PER_TET = {"fwd": 513, "vjp": 1095, "rhs_vjp": 1385}
+FLOPS_PER_TET_VREMAN = {"fwd": 567, "vjp": 1241, "rhs_vjp": 1532}
 
 # The METHOD's own operation count per tet and call (the oracle's definition
 # recorded as an expression DAG with constants folded and common

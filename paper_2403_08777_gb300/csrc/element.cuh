@@ -162,23 +162,29 @@ __device__ __forceinline__ void element_outputs(const R c[3][3], R inv_det, cons
   // K = pbar/6 I - inv_det/6 [Gh (mu_eff I + rho^2/4 Q) + rho/4 gph T^T], with the
   // scalar factors folded into Qp and gq before the 3x3 product so that each
   // entry is one chain of fused multiply-adds.
-  const R s6 = inv_det * (R)(1.0 / 6.0);
-  const R a2 = -s6 * (P.rho * P.rho * (R)0.25);
-  const R a1 = -s6 * mu_eff;
-  const R b4 = -s6 * (P.rho * (R)0.25);
+  // from s24 = inv_det/24 (exactly inv_det/6 scaled by 1/4, so these equal
+  // -(inv_det/6) (rho^2/4), -(inv_det/6) mu_eff and -(inv_det/6) (rho/4))
+  const R s24 = inv_det * (R)(1.0 / 24.0);
+  const R a2 = s24 * -(P.rho * P.rho);
+  const R a1 = s24 * ((R)-4 * mu_eff);
+  const R b4 = s24 * -P.rho;
   const R Qp[3][3] = {{fmac(a2, Q00, a1), a2 * Q01, a2 * Q02},
                       {a2 * Q01, fmac(a2, Q11, a1), a2 * Q12},
                       {a2 * Q02, a2 * Q12, fmac(a2, Q22, a1)}};
   const R pb6 = psum * (R)(1.0 / 24.0);
   const R Pm[3][3] = {{P00, P01, P02}, {P01, P11, P12}, {P02, P12, P22}};
   const R r48 = P.rho * (R)(1.0 / 48.0);
+  // sTT = (inv_det/24) rho T = -b4 T serves both the continuity's Rs and
+  // K's b4 gph T^T term (as -gph sTT^T)
+  R sTT[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) sTT[j] = -b4 * T[j];
   R K[3][3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    const R gq = b4 * gp[i];
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-      R acc = (i == j) ? fmac(gq, T[j], pb6) : gq * T[j];
+      R acc = (i == j) ? fmac(-gp[i], sTT[j], pb6) : -gp[i] * sTT[j];
       if constexpr (SKEW) acc = fmac(r48, Pm[i][j], acc);
       acc = fmac(G[i][0], Qp[0][j], acc);
       acc = fmac(G[i][1], Qp[1][j], acc);
@@ -186,14 +192,7 @@ __device__ __forceinline__ void element_outputs(const R c[3][3], R inv_det, cons
     }
   }
   // Rs = inv_det/24 (rho Gh T + stau gph)
-  const R s24 = inv_det * (R)(1.0 / 24.0);
   const R sg = s24 * stau;
-  R sTT[3];
-  {
-    const R sT = s24 * P.rho;
-#pragma unroll
-    for (int j = 0; j < 3; ++j) sTT[j] = sT * T[j];
-  }
   R Rs[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
@@ -541,11 +540,11 @@ __device__ __forceinline__ void element_vjp_impl(const R c[3][3], R inv_det, R r
       cw[j] = fmac(dw[2][3], c[2][j], fmac(dw[1][3], c[1][j], dw[0][3] * c[0][j]));
   }
   const R wcs = (w[0][3] + w[1][3]) + (w[2][3] + w[3][3]);
-  const R s6 = inv_det * (R)(1.0 / 6.0);
   const R s24 = inv_det * (R)(1.0 / 24.0);
-  const R a1 = -s6 * mu_eff;
-  const R a2 = -s6 * (P.rho * P.rho * (R)0.25);
-  const R b4 = -s6 * (P.rho * (R)0.25);
+  const R s6 = (R)4 * s24;  // = inv_det/6 exactly
+  const R a1 = s24 * ((R)-4 * mu_eff);
+  const R a2 = s24 * -(P.rho * P.rho);
+  const R b4 = s24 * -P.rho;
   // Rbar = -(inv_det/24) cw is not formed: it enters as stau Rbar
   // (-s24 stau cw), Rbar . gph, rho G^T Rbar = b4 G^T cw and rho Rbar T^T =
   // cw (b4 T)^T, since b4 = -rho inv_det/24
