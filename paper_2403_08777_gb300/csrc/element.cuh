@@ -309,9 +309,9 @@ __device__ __forceinline__ void element_rhs(const R c[3][3], R inv_det, R rh, co
     B = fmac(bm[0][0], bm[2][2], fmac(-bm[0][2], bm[0][2], B));
     B = fmac(bm[0][0], bm[1][1], fmac(-bm[0][1], bm[0][1], B));
     if (A > (R)0 && B > (R)0) {
-      // nu_t = c h^2 sqrt(B_G/A_G) = c h^2 inv_det sqrt(B/A)
-      const R h2 = M::rcp(rh * rh);
-      mu_eff = fmac(P.rho * P.c_vreman, h2 * inv_det * M::sqrt_(B * M::rcp(A)), P.mu);
+      // nu_t = c h^2 sqrt(B_G/A_G) = c h^2 inv_det sqrt(B/A), and with
+      // h = detJ^(1/3), h^2 inv_det = detJ^(-1/3) = rh
+      mu_eff = fmac(P.rho * P.c_vreman, rh * M::sqrt_(B * M::rcp(A)), P.mu);
     }
   }
   const R k1 = (P.c1 * mu_eff) * (rh * rh);
@@ -431,21 +431,17 @@ __device__ __forceinline__ void element_vjp_impl(const R c[3][3], R inv_det, R r
   R b00 = (R)0, b11 = (R)0, b22 = (R)0, b01 = (R)0, b02 = (R)0, b12 = (R)0;
   bool vactive = false;
   if constexpr (VREMAN) {
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) vA += G[i][j] * G[i][j];
     b00 = G[0][0] * G[0][0] + G[0][1] * G[0][1] + G[0][2] * G[0][2];
     b11 = G[1][0] * G[1][0] + G[1][1] * G[1][1] + G[1][2] * G[1][2];
     b22 = G[2][0] * G[2][0] + G[2][1] * G[2][1] + G[2][2] * G[2][2];
     b01 = G[0][0] * G[1][0] + G[0][1] * G[1][1] + G[0][2] * G[1][2];
     b02 = G[0][0] * G[2][0] + G[0][1] * G[2][1] + G[0][2] * G[2][2];
     b12 = G[1][0] * G[2][0] + G[1][1] * G[2][1] + G[1][2] * G[2][2];
+    vA = (b00 + b11) + b22;
     R vB = b00 * b11 - b01 * b01 + b00 * b22 - b02 * b02 + b11 * b22 - b12 * b12;
     if (vA > (R)0 && vB > (R)0) {
       vactive = true;
-      R h2 = M::rcp(rh * rh);
-      vscale = P.rho * P.c_vreman * h2 * inv_det;
+      vscale = (P.rho * P.c_vreman) * rh;  // rho c h^2 inv_det = rho c detJ^(-1/3)
       vphi = M::sqrt_(vB * M::rcp(vA));
       mu_eff = P.mu + vscale * vphi;
     }
