@@ -52,7 +52,7 @@ UNIT = "tets/s"
 # The element geometry (43 flops per tet) is computed once per mesh and
 # cached, so it is not part of a call.
 FLOPS_PER_TET = {"fwd": 513, "vjp": 1095, "rhs_vjp": 1385}
-FLOPS_PER_TET_VREMAN = {"fwd": 564, "vjp": 1222, "rhs_vjp": 1513}
+FLOPS_PER_TET_VREMAN = {"fwd": 564, "vjp": 1216, "rhs_vjp": 1507}
 
 # The METHOD's own operation count per tet and call (the oracle's definition
 # recorded as an expression DAG with constants folded and common

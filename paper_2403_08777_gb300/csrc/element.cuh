@@ -698,20 +698,22 @@ __device__ __forceinline__ void element_vjp_impl(const R c[3][3], R inv_det, R r
 #pragma unroll
     for (int i = 0; i < 3; ++i) Usum[i] += ugb[g][i];
   }
-  // Vreman: mu_eff = mu + vscale sqrt(B/A):
-  // d phi / d Gh = (P - phi^2 I) Gh / (phi A), P = tr(beta) I - beta
+  // Vreman: mu_eff = mu + vscale phi, phi = sqrt(B/A):
+  // d phi / d Gh = (P - phi^2 I) Gh / (phi A), P = tr(beta) I - beta, tr(beta) = A;
+  // Gbar += f (P - phi^2 I) Gh with f = mub vscale / (phi A) folded into the
+  // matrix, so that each entry is one FMA chain
   if (VREMAN && vactive) {
-    R f = mub * vscale * M::rcp(vphi * vA);
-    R tb = b00 + b11 + b22;
-    R phi2 = vphi * vphi;
-    const R Pm[3][3] = {{tb - b00 - phi2, -b01, -b02},
-                        {-b01, tb - b11 - phi2, -b12},
-                        {-b02, -b12, tb - b22 - phi2}};
+    const R f = mub * vscale * M::rcp(vphi * vA);
+    const R t = f * (vA - vphi * vphi);
+    const R fb01 = -f * b01, fb02 = -f * b02, fb12 = -f * b12;
+    const R fP[3][3] = {{fmac(-f, b00, t), fb01, fb02},
+                        {fb01, fmac(-f, b11, t), fb12},
+                        {fb02, fb12, fmac(-f, b22, t)}};
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int j = 0; j < 3; ++j)
-        Gb[i][j] += f * (Pm[i][0] * G[0][j] + Pm[i][1] * G[1][j] + Pm[i][2] * G[2][j]);
+        Gb[i][j] = fmac(fP[i][2], G[2][j], fmac(fP[i][1], G[1][j], fmac(fP[i][0], G[0][j], Gb[i][j])));
   }
   // Gh = sum_a u_a c_a^T, S = sum_a u_a, u_g = QB S + (QA - QB) u_g, and the
   // convection's -(rho/120) Gh (S + u_a): gu_a = Gb c_a + Sbar + Hm^T wm_a + (QA-QB) ugb_a
