@@ -160,10 +160,10 @@ __device__ __forceinline__ void element_outputs(const R c[3][3], R inv_det, cons
   const R Q00 = Qv[0], Q11 = Qv[1], Q22 = Qv[2], Q01 = Qv[3], Q02 = Qv[4], Q12 = Qv[5];
   const R P00 = Pv[0], P11 = Pv[1], P22 = Pv[2], P01 = Pv[3], P02 = Pv[4], P12 = Pv[5];
   // K = pbar/6 I - inv_det/6 [Gh (mu_eff I + rho^2/4 Q) + rho/4 gph T^T], with the
-  // scalar factors folded into Qp and gq before the 3x3 product so that each
-  // entry is one chain of fused multiply-adds.
-  // from s24 = inv_det/24 (exactly inv_det/6 scaled by 1/4, so these equal
-  // -(inv_det/6) (rho^2/4), -(inv_det/6) mu_eff and -(inv_det/6) (rho/4))
+  // scalar factors folded into Qp and sTT before the 3x3 product so that each
+  // entry is one chain of fused multiply-adds. a2, a1 and b4 come from
+  // s24 = inv_det/24 (exactly inv_det/6 scaled by 1/4, so they equal
+  // -(inv_det/6) (rho^2/4), -(inv_det/6) mu_eff and -(inv_det/6) (rho/4)).
   const R s24 = inv_det * (R)(1.0 / 24.0);
   const R a2 = s24 * -(P.rho * P.rho);
   const R a1 = s24 * ((R)-4 * mu_eff);

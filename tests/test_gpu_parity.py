@@ -464,7 +464,8 @@ def test_lumped_mass_and_explicit_steps_match_oracle(dev):
 @pytest.mark.parametrize("n,order", [(10, "rcm"), (16, "random")])
 def test_unstructured_delaunay_mesh(dev, n, order):
     """Delaunay mesh of a jittered lattice (varying valence, no hex-block
-    structure): FP64 atomic and block, mixed, adjoint and a variant."""
+    structure): FP64 atomic and block, mixed, adjoint, a variant, the mixed
+    adjoint and the one-pass call (mixed, and FP64 on blocks)."""
     w = mg.make_unstructured(n, order=order, mu=1e-3, mag_max=2.0)
     coords, conn, up = on_dev(dev, w.coords, w.conn, w.up)
     m = ns.Mesh(coords, conn)
@@ -479,6 +480,19 @@ def test_unstructured_delaunay_mesh(dev, n, order):
     assert relerr(g, oracle.vjp(w.coords, w.conn, w.up, cot, w.rho, w.mu)) <= TOL_VJP_ORACLE
     sk = m.assemble(up, ns.Params(rho=w.rho, mu=w.mu, convection="skew")).cpu().numpy()
     check_fp64(sk, oracle.assemble(w.coords, w.conn, w.up, w.rho, w.mu, skew=True))
+    # the mixed adjoint and the one-pass call on the block scatter (irregular
+    # runs: node valences vary)
+    gref = oracle.vjp(w.coords, w.conn, w.up, cot, w.rho, w.mu)
+    pm = ns.Params(rho=w.rho, mu=w.mu, precision="mixed")
+    cot32 = torch.from_numpy(cot).to(dev).float()
+    assert relerr(m.assemble_vjp(up.float(), cot32, pm).cpu().numpy(), gref) <= TOL_VJP_FD
+    r1, g1 = m.assemble_rhs_vjp(up.float(), cot32, pm)
+    assert relerr(r1.cpu().numpy(), ref) <= TOL_MIXED
+    assert relerr(g1.cpu().numpy(), gref) <= TOL_VJP_FD
+    r2, g2 = m.assemble_rhs_vjp(up, torch.from_numpy(cot).to(dev),
+                                ns.Params(rho=w.rho, mu=w.mu, scatter="block"))
+    check_fp64(r2.cpu().numpy(), ref)
+    assert relerr(g2.cpu().numpy(), gref) <= TOL_VJP_ORACLE
     m.close()
 
 
