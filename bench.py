@@ -72,8 +72,8 @@ FLOPS_GEOMETRY = 43
 # ncu capture of each kernel on the 128^3-hex RCM mesh, scaled to a launch by
 # the element count (traffic grows in proportion). None once a kernel has
 # changed since its counters were taken.
-DRAM_BYTES_PER_TET = {"fwd_fp64": 158.3, "vjp_fp64": 187.9,
-                      "fwd_mixed": 92.7, "vjp_mixed": 106.7}
+DRAM_BYTES_PER_TET = {"fwd_fp64": 157.7, "vjp_fp64": 187.9,
+                      "fwd_mixed": 92.4, "vjp_mixed": 106.6}
 
 # Algorithmic (compulsory) bytes per tet with ideal node reuse (N/E = 0.1686
 # on the Kuhn mesh): connectivity or block map 16, cached geometry 88 (f64) or
