@@ -516,6 +516,18 @@ def run_ours(args):
         "ms": op_ms, "tets_per_s": w.n_elems / (op_ms * 1e-3),
         "tflops": flops["rhs_vjp"] * w.n_elems / (op_ms * 1e-3) / 1e12,
         "vs_separate_calls": (fwd_med + vjp_med) / op_ms}
+    # the forward and the adjoint through the differentiable call
+    # (NSRHSFunction: forward, then backward with the cotangent)
+    upr = up.detach().clone().requires_grad_(True)
+
+    def fwd_bwd():
+        upr.grad = None
+        ns.assemble(mesh, upr, p).backward(cot)
+
+    ag_ms = _timed(fwd_bwd, dev, stream, args)
+    forms["fwd_vjp_autograd"] = {"ms": ag_ms, "tets_per_s": w.n_elems / (ag_ms * 1e-3),
+                                 "vs_direct_calls": (fwd_med + vjp_med) / ag_ms}
+    del upr
     # mixed-precision adjoint (float sweep, double accumulation)
     up32, cot32 = up.float(), cot.float()
     pmx = ns.Params(rho=w.rho, mu=w.mu, c_vreman=w.c_vreman, precision="mixed")
