@@ -228,8 +228,10 @@ nsrhs_status nsrhs_assemble_vjp(const nsrhs_mesh* m, const nsrhs_params* p, cons
  * block stages hold the cotangent beside (u, p) and two entry buffers, the
  * element RHS and its gradient, summed per node by the same runs;
  * NSRHS_EUNSUPPORTED where they do not fit a CTA's shared memory, as for the
- * FP64 adjoint). NSRHS_SCATTER_COLOUR and NSRHS_GEOM_RECOMPUTE:
- * NSRHS_EUNSUPPORTED.
+ * FP64 adjoint). NSRHS_SCATTER_COLOUR, NSRHS_GEOM_RECOMPUTE, and
+ * BLOCK_COLOUR on a mesh created without colouring: NSRHS_EUNSUPPORTED.
+ * A null pointer, a destroyed or foreign mesh, or rhs == grad: NSRHS_EINVAL.
+ * On either error nothing is written.
  */
 nsrhs_status nsrhs_assemble_rhs_vjp(const nsrhs_mesh* m, const nsrhs_params* p, const void* up,
                                     const void* cot, double* rhs, double* grad, void* stream);
