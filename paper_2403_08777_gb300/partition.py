@@ -22,7 +22,10 @@ This module is that host-side bookkeeping:
 * interface_rows / apply_interface / exchange_interface: gather a local
   RHS's interface rows into a [4, n_iface] buffer, sum the buffers over the
   parts (the caller's all-reduce), and write the sums back. Afterwards every
-  local row, owned or ghost, equals the row of the whole mesh's RHS.
+  local row, owned or ghost, equals the row of the whole mesh's RHS;
+* exchange_neighbours: the same result from point-to-point messages between
+  the parts that share nodes (for slabs, one face per neighbour), which moves
+  the shared rows only.
 
 Host-side numpy for the partition; the exchange helpers are torch indexing
 on whatever device the local RHS lives on.
@@ -47,6 +50,8 @@ class Part:
     iface_local: np.ndarray  # [I_p] int64 local indices of the part's interface nodes
     iface_slot: np.ndarray   # [I_p] int64 their slots in the interface vector
     n_iface: int             # length of the interface vector (all parts)
+    shared: dict             # q -> [S_pq] int64 local indices of the nodes shared with
+                             # part q, in ascending global id (aligned on both sides)
 
     @property
     def n_nodes(self) -> int:
@@ -104,8 +109,16 @@ def slab_partition(coords: np.ndarray, conn: np.ndarray, n_parts: int,
         lconn = g2l[conn[:, el]].astype(np.int32)
         ifl = np.flatnonzero(touched_by[nodes] > 1).astype(np.int64)
         slot = np.searchsorted(iface, nodes[ifl]).astype(np.int64)
+        shared = {}
+        gif = np.sort(nodes[ifl])
+        mif = mask[gif]
+        for q in range(n_parts):
+            if q != p:
+                sel = ((mif >> np.uint64(q)) & np.uint64(1)) == 1
+                if sel.any():
+                    shared[q] = g2l[gif[sel]]
         parts.append(Part(p, n_parts, el, nodes, int(mine.size), np.ascontiguousarray(lconn),
-                          ifl, slot, int(iface.size)))
+                          ifl, slot, int(iface.size), shared))
     return parts
 
 
@@ -139,3 +152,38 @@ def exchange_interface(rhs_local, part: Part, all_reduce):
     buf = interface_rows(rhs_local, part)
     all_reduce(buf)
     return apply_interface(rhs_local, part, buf)
+
+
+def exchange_neighbours(rhs_local, part: Part, sendrecv):
+    """The exchange as point-to-point messages: to every part q it shares
+    nodes with, this part sends its own rows of those nodes and receives q's
+    ([k, S_pq] each, in ascending global id), then adds what it received.
+    sendrecv(sends) takes {q: tensor to send to q} and returns {q: tensor
+    received from q} (see torch_sendrecv). The bytes moved are the shared
+    faces only, not the whole interface vector."""
+    import torch
+    idx = {q: torch.as_tensor(loc, device=rhs_local.device) for q, loc in part.shared.items()}
+    sends = {q: rhs_local[:, i].contiguous() for q, i in idx.items()}
+    recvs = sendrecv(sends)
+    for q, i in idx.items():
+        rhs_local[:, i] += recvs[q]
+    return rhs_local
+
+
+def torch_sendrecv(group=None):
+    """A sendrecv for exchange_neighbours over torch.distributed: every
+    message posted as a non-blocking send and receive, then all awaited."""
+    import torch
+    import torch.distributed as dist
+
+    def run(sends):
+        recvs = {q: torch.empty_like(t) for q, t in sends.items()}
+        reqs = []
+        for q in sorted(sends):
+            reqs.append(dist.isend(sends[q], q, group=group))
+            reqs.append(dist.irecv(recvs[q], q, group=group))
+        for r in reqs:
+            r.wait()
+        return recvs
+
+    return run

@@ -8,8 +8,9 @@
   Checked with the oracle.
 * The same with the package's slab partition: every rank assembles its
   sub-mesh over its owned and ghost nodes only, and one all-reduce of the
-  interface rows (exchange_interface) makes every local row equal to the
-  whole mesh's, for the RHS and the VJP.
+  interface rows (exchange_interface), or point-to-point messages with the
+  ranks it shares nodes with (exchange_neighbours), make every local row
+  equal to the whole mesh's, for the RHS and the VJP.
 """
 import multiprocessing as mp
 import os
@@ -40,7 +41,7 @@ def _worker(rank, world, port, task, q):
             t = bench.max_over_ranks(10.0 + 5.0 * rank, world, torch.device("cpu"))
             rate = bench.whole_job_rate(1000, world, t / 1e3)
             q.put((rank, t, rate))
-        elif task == "slab":
+        elif task in ("slab", "slab_p2p"):
             import meshgen as mg
             import oracle
             from paper_2403_08777_gb300 import partition as pt
@@ -50,8 +51,12 @@ def _worker(rank, world, port, task, q):
             lc, lu = part.local(w.coords), part.local(w.up)
             r = torch.from_numpy(oracle.assemble(lc, part.conn, lu, w.rho, w.mu))
             g = torch.from_numpy(oracle.vjp(lc, part.conn, lu, part.local(cot), w.rho, w.mu))
-            pt.exchange_interface(r, part, dist.all_reduce)
-            pt.exchange_interface(g, part, dist.all_reduce)
+            if task == "slab":
+                pt.exchange_interface(r, part, dist.all_reduce)
+                pt.exchange_interface(g, part, dist.all_reduce)
+            else:  # point-to-point between the parts sharing nodes
+                pt.exchange_neighbours(r, part, pt.torch_sendrecv())
+                pt.exchange_neighbours(g, part, pt.torch_sendrecv())
             full = oracle.assemble(w.coords, w.conn, w.up, w.rho, w.mu)[:, part.nodes]
             gfull = oracle.vjp(w.coords, w.conn, w.up, cot, w.rho, w.mu)[:, part.nodes]
             err = max(float(np.abs(r.numpy() - full).max() / np.abs(full).max()),
@@ -100,9 +105,10 @@ def test_partitioned_assembly_interface_sum_gloo():
         assert err <= 1e-14 * scale
 
 
+@pytest.mark.parametrize("task", ["slab", "slab_p2p"])
 @pytest.mark.parametrize("world", [2, 3])
-def test_slab_partition_exchange_gloo(world):
-    out = _run("slab", world)
+def test_slab_partition_exchange_gloo(world, task):
+    out = _run(task, world)
     for _, err, n_iface in out:
         assert n_iface > 0
         assert err <= 1e-13

@@ -92,6 +92,35 @@ def test_local_assembly_and_exchange_give_the_global_rhs(kind, n_parts):
             assert np.abs(l.numpy() - ref[:, p.nodes]).max() <= 1e-13 * scale
 
 
+@pytest.mark.parametrize("kind", ["kuhn", "delaunay"])
+@pytest.mark.parametrize("n_parts", [2, 3, 5])
+def test_neighbour_exchange_gives_the_global_rhs(kind, n_parts):
+    """Point-to-point exchange between parts sharing nodes, routed in
+    process: the shared lists of two parts name the same nodes in the same
+    order, and after the exchange every local row equals the whole mesh's.
+    The messages carry the shared rows only: fewer than the all-reduce's
+    n_parts copies of the whole interface vector."""
+    w = _mesh(kind)
+    full = oracle.assemble(w.coords, w.conn, w.up, w.rho, w.mu)
+    parts = pt.slab_partition(w.coords, w.conn, n_parts)
+    for a in parts:
+        for q, loc in a.shared.items():
+            b = parts[q]
+            assert np.array_equal(a.nodes[loc], b.nodes[b.shared[a.index]])
+            assert np.all(np.diff(a.nodes[loc]) > 0)
+    loc = [torch.from_numpy(oracle.assemble(p.local(w.coords), p.conn, p.local(w.up), w.rho, w.mu))
+           for p in parts]
+    sent = {p.index: {q: loc[p.index][:, torch.from_numpy(i)].clone() for q, i in p.shared.items()}
+            for p in parts}
+    for p in parts:
+        pt.exchange_neighbours(loc[p.index], p, lambda sends, me=p.index: {q: sent[q][me] for q in sends})
+    scale = np.abs(full).max()
+    for l, p in zip(loc, parts):
+        assert np.abs(l.numpy() - full[:, p.nodes]).max() <= 1e-13 * scale
+    p2p = sum(len(i) for p in parts for i in p.shared.values())
+    assert 0 < p2p <= n_parts * parts[0].n_iface
+
+
 def test_exchange_with_a_summing_all_reduce():
     """exchange_interface calls the all-reduce once on a [4, n_iface] buffer
     holding only the part's rows."""
