@@ -629,6 +629,11 @@ def run_ours(args):
     if args.locality > 0:
         forms["locality"] = time_locality(args.locality, dev, stream, args)
     forms["vjp_64cube"] = time_vjp_64(dev, stream, args)
+    if args.locality > 0:
+        try:
+            forms["partitioned_one_gpu"] = time_partitioned(args.locality, 8, dev, stream, args)
+        except Exception as exc:  # an auxiliary form must not cost the bench line
+            forms["partitioned_one_gpu"] = {"error": repr(exc)}
 
     dom = "vjp_fp64" if vjp_med >= fwd_med else "fwd_fp64"
     dom_ms = vjp_med if dom == "vjp_fp64" else fwd_med
@@ -866,6 +871,51 @@ def time_locality(n, dev, stream, args):
         m.close()
     out["workload"] = f"kuhn{n}^3 (random vs rcm)"
     return out
+
+
+def time_partitioned(n, n_parts, dev, stream, args):
+    """The n^3-hex mesh (paper-scale fields) cut into n_parts z-slabs
+    (partition.slab_partition), each part its own library mesh on this GPU:
+    the whole mesh's forward against each part's (what one rank of a sharded
+    run assembles), the ghost-node overhead, the bytes one rank moves in
+    either interface exchange, and the exchanged parts against the whole
+    mesh's RHS."""
+    import torch
+    import paper_2403_08777_gb300 as ns
+    from paper_2403_08777_gb300 import partition as pt
+    w = mg.paper_scale(n=n, order="rcm")
+    p = ns.Params(rho=w.rho, mu=w.mu)
+    whole = ns.Mesh(torch.from_numpy(w.coords).to(dev), torch.from_numpy(w.conn).to(dev))
+    up = torch.from_numpy(w.up).to(dev)
+    o = torch.empty_like(up)
+    t_whole = _timed(lambda: whole.assemble(up, p, out=o), dev, stream, args)
+    ref = o.clone()
+    whole.close()
+    parts = pt.slab_partition(w.coords, w.conn, n_parts)
+    t_parts, outs = [], []
+    for part in parts:
+        m = ns.Mesh(torch.from_numpy(part.local(w.coords)).to(dev),
+                    torch.from_numpy(part.conn).to(dev))
+        u = torch.from_numpy(part.local(w.up)).to(dev)
+        op = torch.empty_like(u)
+        t_parts.append(_timed(lambda: m.assemble(u, p, out=op), dev, stream, args))
+        outs.append(op)
+        m.close()
+    total = sum(pt.interface_rows(l, q) for l, q in zip(outs, parts))
+    err = 0.0
+    scale = float(ref.abs().max())
+    for l, q in zip(outs, parts):
+        pt.apply_interface(l, q, total)
+        idx = torch.as_tensor(q.nodes, device=dev)
+        err = max(err, float((l - ref[:, idx]).abs().max()) / scale)
+    return {"workload": w.name, "n_parts": n_parts, "partition": "z slabs, equal element counts",
+            "whole_fwd_ms": t_whole, "part_fwd_ms_max": max(t_parts),
+            "part_fwd_ms_sum": sum(t_parts), "per_rank_speedup": t_whole / max(t_parts),
+            "ghost_node_overhead": sum(q.n_nodes for q in parts) / w.n_nodes - 1,
+            "exchange_bytes_per_rank_allreduce": 4 * 8 * parts[0].n_iface,
+            "exchange_bytes_per_rank_p2p_max": max(4 * 8 * sum(len(i) for i in q.shared.values())
+                                                   for q in parts),
+            "max_rel_diff_vs_whole_mesh": err}
 
 
 def time_vjp_64(dev, stream, args):
