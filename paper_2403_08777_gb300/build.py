@@ -30,6 +30,8 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(s) <= t for s in sources())
 
 
+# One nvcc invocation without --split-compile: that option halves the build
+# time, but the kernels it produced ran 0.5-3.5 % slower (measured on GB300).
 def build(force: bool = False, verbose: bool = False) -> str:
     if not force and up_to_date():
         return LIB
