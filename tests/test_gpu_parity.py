@@ -673,3 +673,33 @@ def test_adjoint_at_zero_velocity_matches_central_differences(dev):
         ad = float(np.sum(g * d))
         assert abs(fd - ad) <= TOL_VJP_FD * max(abs(ad), 1e-30), (fd, ad)
     m.close()
+
+
+def test_calls_run_on_the_callers_stream(dev):
+    """Every call is issued on the caller's current stream: inputs produced on
+    a side stream, the calls issued there and only that stream synchronised
+    give the default stream's results (no call synchronises the device or
+    falls back to the default stream)."""
+    w = mg.make_workload(10, jitter=0.2, order="rcm", mu=1e-3, mag_max=2.0)
+    coords, conn, up, cot = on_dev(dev, w.coords, w.conn, w.up, mg.normal((4, w.n_nodes), seed=5))
+    m = ns.Mesh(coords, conn, colour=True)
+    p = ns.Params(rho=w.rho, mu=w.mu)
+    ref = m.assemble(up, p).cpu().numpy()
+    gref = m.assemble_vjp(up, cot, p).cpu().numpy()
+    pm = ns.Params(rho=w.rho, mu=w.mu, precision="mixed")
+    mref = m.assemble(up.float(), pm).cpu().numpy()
+    torch.cuda.synchronize(dev)
+    s = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(s):
+        u2 = up * 1.0          # produced on the side stream
+        c2 = cot * 1.0
+        x = m.assemble(u2, p)
+        g = m.assemble_vjp(u2, c2, p)
+        r1, g1 = m.assemble_rhs_vjp(u2, c2, p)
+        xm = m.assemble(u2.float(), pm)
+        xc = m.assemble(u2, ns.Params(rho=w.rho, mu=w.mu, scatter="colour"))
+    s.synchronize()
+    for a, b in ((x, ref), (g, gref), (r1, ref), (g1, gref), (xc, ref)):
+        assert relerr(a.cpu().numpy(), b) <= 1e-13
+    assert relerr(xm.cpu().numpy(), mref) <= 1e-6
+    m.close()
